@@ -1,0 +1,154 @@
+"""Dense FP64 boundary-element system of Eq. (integral_eq) and its solution.
+
+Unknowns: piecewise-constant phi_j and psi_j = dphi_1/dn on each panel j,
+collocated at the panel centroids x_i.  Rows, for each target i:
+
+    phi_i / 2 + sum_j K_L[i, j] phi_j - sum_j V_L[i, j] psi_j          = RHS_i
+    phi_i / 2 - sum_j K_Y[i, j] phi_j + (eps1 / eps2) sum_j V_Y[i, j] psi_j = 0
+
+with V = int_Tj G dS and K = int_Tj dG/dn_y dS (Eq. layers; n_y the outward
+normal of the source panel).  Entries use the panel integrals of ``panel.py``
+when the pair is near (``geometry.near_pairs``) and the K-node Gauss rule
+otherwise (Sec. "The boundary element method").
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.linalg
+
+from . import geometry, panel
+
+
+@dataclass
+class Mesh:
+    verts: np.ndarray
+    tris: np.ndarray
+    cen: np.ndarray
+    normal: np.ndarray
+    area: np.ndarray
+    ygauss: np.ndarray     # [N, K, 3]
+    wgauss: np.ndarray     # [N, K]
+    near_ptr: np.ndarray
+    near_cols: np.ndarray
+
+    @property
+    def n(self):
+        return int(self.tris.shape[0])
+
+
+def build_mesh(verts, tris, gauss_k=4, near_factor=2.0) -> Mesh:
+    cen, normal, area = geometry.panel_geometry(verts, tris)
+    y, w = geometry.gauss_points(verts, tris, gauss_k)
+    ptr, cols = geometry.near_pairs(cen, area, near_factor)
+    return Mesh(verts, tris, cen, normal, area, y, w, ptr, cols)
+
+
+def near_rows_cols(mesh: Mesh):
+    rows = np.repeat(np.arange(mesh.n), np.diff(mesh.near_ptr))
+    return rows, mesh.near_cols.astype(np.int64)
+
+
+def near_exact(mesh: Mesh, kappa: float):
+    """Accurate panel integrals for every near pair, in CSR order: (VL, KL, VY, KY)."""
+    rows, cols = near_rows_cols(mesh)
+    t = mesh.tris[cols]
+    return panel.panel_integrals(mesh.cen[rows], mesh.verts[t[:, 0]], mesh.verts[t[:, 1]],
+                                 mesh.verts[t[:, 2]], kappa, self_panel=(rows == cols))
+
+
+def near_kpoint(mesh: Mesh, kappa: float):
+    """K-node Gauss sums for every near pair, in CSR order: (VL, KL, VY, KY)."""
+    rows, cols = near_rows_cols(mesh)
+    return panel.kpoint_sums(mesh.cen[rows], mesh.ygauss[cols], mesh.wgauss[cols],
+                             mesh.normal[cols], kappa)
+
+
+def near_correction(mesh: Mesh, kappa: float):
+    """Accurate minus K-node value of each near pair (what a Gauss-node matvec must add)."""
+    ex = near_exact(mesh, kappa)
+    kp = near_kpoint(mesh, kappa)
+    return tuple(e - k for e, k in zip(ex, kp))
+
+
+def assemble_layers(mesh: Mesh, kappa: float, row_chunk: int = 256):
+    """Dense [N, N] matrices VL, KL, VY, KY (far: K-node rule, near: accurate integrals)."""
+    n = mesh.n
+    VL = np.empty((n, n))
+    KL = np.empty((n, n))
+    VY = np.empty((n, n))
+    KY = np.empty((n, n))
+    for s in range(0, n, row_chunk):
+        e = min(n, s + row_chunk)
+        m = e - s
+        x = np.repeat(mesh.cen[s:e], n, axis=0)
+        yg = np.tile(mesh.ygauss, (m, 1, 1))
+        wg = np.tile(mesh.wgauss, (m, 1))
+        nr = np.tile(mesh.normal, (m, 1))
+        vl, kl, vy, ky = panel.kpoint_sums(x, yg, wg, nr, kappa)
+        VL[s:e] = vl.reshape(m, n)
+        KL[s:e] = kl.reshape(m, n)
+        VY[s:e] = vy.reshape(m, n)
+        KY[s:e] = ky.reshape(m, n)
+    rows, cols = near_rows_cols(mesh)
+    vl, kl, vy, ky = near_exact(mesh, kappa)
+    VL[rows, cols] = vl
+    KL[rows, cols] = kl
+    VY[rows, cols] = vy
+    KY[rows, cols] = ky
+    return VL, KL, VY, KY
+
+
+def system_matrix(layers, eps_in: float, eps_out: float):
+    """The 2N x 2N matrix of Eq. (integral_eq) acting on x = [phi; psi]."""
+    VL, KL, VY, KY = layers
+    n = VL.shape[0]
+    I = np.eye(n)
+    A = np.empty((2 * n, 2 * n))
+    A[:n, :n] = 0.5 * I + KL
+    A[:n, n:] = -VL
+    A[n:, :n] = 0.5 * I - KY
+    A[n:, n:] = (eps_in / eps_out) * VY
+    return A
+
+
+class DenseSolver:
+    """LU factors of the system matrix; ``solve(b)`` returns the exact discrete solution."""
+
+    def __init__(self, mesh: Mesh, eps_in, eps_out, kappa):
+        self.layers = assemble_layers(mesh, kappa)
+        self.A = system_matrix(self.layers, eps_in, eps_out)
+        self.lu = scipy.linalg.lu_factor(self.A)
+
+    def solve(self, b):
+        return scipy.linalg.lu_solve(self.lu, b)
+
+    def matvec(self, x):
+        return self.A @ x
+
+
+def matvec_rows(mesh: Mesh, x: np.ndarray, rows: np.ndarray, eps_in, eps_out, kappa):
+    """Rows ``rows`` of both blocks of A x without forming A (for large meshes).
+
+    Returns (y1[rows], y2[rows]) where y1 is the Laplace row and y2 the Yukawa row.
+    """
+    n = mesh.n
+    phi = x[:n]
+    psi = x[n:]
+    y1 = np.empty(rows.size)
+    y2 = np.empty(rows.size)
+    for t, i in enumerate(rows):
+        xi = np.repeat(mesh.cen[i][None], n, axis=0)
+        vl, kl, vy, ky = panel.kpoint_sums(xi, mesh.ygauss, mesh.wgauss, mesh.normal, kappa)
+        cols = mesh.near_cols[mesh.near_ptr[i]:mesh.near_ptr[i + 1]].astype(np.int64)
+        tv = mesh.tris[cols]
+        ex = panel.panel_integrals(np.repeat(mesh.cen[i][None], cols.size, axis=0),
+                                   mesh.verts[tv[:, 0]], mesh.verts[tv[:, 1]], mesh.verts[tv[:, 2]],
+                                   kappa, self_panel=(cols == i))
+        vl[cols], kl[cols], vy[cols], ky[cols] = ex
+        y1[t] = 0.5 * phi[i] + kl @ phi - vl @ psi
+        y2[t] = 0.5 * phi[i] - ky @ phi + (eps_in / eps_out) * (vy @ psi)
+    return y1, y2

@@ -1,0 +1,95 @@
+"""Panel geometry and quadrature rules (Sec. "The boundary element method").
+
+The surface is discretised into flat triangles with piecewise-constant phi and
+dphi/dn, collocated at the panel centroids.  Far-away panels are integrated
+with 1, 3 or 4 Gauss nodes; panels closer than ``near_factor * sqrt(A_i)`` to
+the collocation point x_i (A_i the area of the collocation point's own panel)
+are integrated accurately (see ``panel.py``).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def panel_geometry(verts: np.ndarray, tris: np.ndarray):
+    """Centroid x_i, unit outward normal n_i and area A_i of every triangle.
+
+    Written with separate products and sums (no fused operations), in the order
+    centroid = (v0 + v1 + v2) / 3, cross = (v1 - v0) x (v2 - v0), A = |cross| / 2.
+    """
+    v0 = verts[tris[:, 0]]
+    v1 = verts[tris[:, 1]]
+    v2 = verts[tris[:, 2]]
+    cen = (v0 + v1 + v2) / 3.0
+    e1 = v1 - v0
+    e2 = v2 - v0
+    cr = np.empty_like(e1)
+    cr[:, 0] = e1[:, 1] * e2[:, 2] - e1[:, 2] * e2[:, 1]
+    cr[:, 1] = e1[:, 2] * e2[:, 0] - e1[:, 0] * e2[:, 2]
+    cr[:, 2] = e1[:, 0] * e2[:, 1] - e1[:, 1] * e2[:, 0]
+    nrm = np.sqrt(cr[:, 0] * cr[:, 0] + cr[:, 1] * cr[:, 1] + cr[:, 2] * cr[:, 2])
+    area = 0.5 * nrm
+    normal = cr / nrm[:, None]
+    return cen, normal, area
+
+
+def gauss_rule(k: int):
+    """Barycentric nodes and weights (summing to 1) of the K-node triangle rule.
+
+    K=1: centroid.  K=3: (2/3, 1/6, 1/6) and permutations, degree 2.
+    K=4: centroid with weight -27/48 and (3/5, 1/5, 1/5) permutations with
+    weight 25/48, degree 3.  The paper names 1, 3 or 4 nodes without giving the
+    rules; these are the classical Strang-Fix rules.
+    """
+    if k == 1:
+        lam = np.array([[1 / 3, 1 / 3, 1 / 3]])
+        w = np.array([1.0])
+    elif k == 3:
+        lam = np.array([[2 / 3, 1 / 6, 1 / 6], [1 / 6, 2 / 3, 1 / 6], [1 / 6, 1 / 6, 2 / 3]])
+        w = np.array([1 / 3, 1 / 3, 1 / 3])
+    elif k == 4:
+        lam = np.array([[1 / 3, 1 / 3, 1 / 3], [0.6, 0.2, 0.2], [0.2, 0.6, 0.2], [0.2, 0.2, 0.6]])
+        w = np.array([-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0])
+    else:
+        raise ValueError("gauss_k must be 1, 3 or 4")
+    return lam, w
+
+
+def gauss_points(verts: np.ndarray, tris: np.ndarray, k: int):
+    """Gauss-node positions y_jg [N, K, 3] and weights W_jg = w_g * A_j [N, K]."""
+    lam, w = gauss_rule(k)
+    v0 = verts[tris[:, 0]]
+    v1 = verts[tris[:, 1]]
+    v2 = verts[tris[:, 2]]
+    y = (lam[None, :, 0, None] * v0[:, None, :] + lam[None, :, 1, None] * v1[:, None, :]
+         + lam[None, :, 2, None] * v2[:, None, :])
+    _, _, area = panel_geometry(verts, tris)
+    return y, w[None, :] * area[:, None]
+
+
+def near_pairs(cen: np.ndarray, area: np.ndarray, near_factor: float):
+    """CSR of near pairs: j is near target i when |x_i - c_j|^2 < near_factor^2 * A_i.
+
+    The comparison is made on squared distances in FP64, with the squared
+    distance summed as dx*dx + dy*dy + dz*dz in that order.  Includes j = i.
+    Returns (row_ptr [N+1] int64, cols int32 sorted ascending per row).
+    """
+    n = cen.shape[0]
+    thr = (near_factor * near_factor) * area
+    rows = [np.zeros(0, dtype=np.int32)] * n
+    chunk = 512
+    for s in range(0, n, chunk):
+        e = min(n, s + chunk)
+        dx = cen[s:e, None, 0] - cen[None, :, 0]
+        dy = cen[s:e, None, 1] - cen[None, :, 1]
+        dz = cen[s:e, None, 2] - cen[None, :, 2]
+        d2 = dx * dx + dy * dy + dz * dz
+        m = d2 < thr[s:e, None]
+        for i in range(s, e):
+            rows[i] = np.nonzero(m[i - s])[0].astype(np.int32)
+    ptr = np.zeros(n + 1, dtype=np.int64)
+    ptr[1:] = np.cumsum([r.size for r in rows])
+    cols = np.concatenate(rows) if n else np.zeros(0, dtype=np.int32)
+    return ptr, cols

@@ -1,0 +1,143 @@
+"""Pins for the closed-form sphere solution and, through it, the whole oracle chain.
+
+The Kirkwood series is checked against scipy's Bessel functions, the Born and
+centred-dipole closed forms, finite differences of a directly summed Legendre
+series, and reciprocity.  The discrete BEM solution of the oracle must then
+converge to it at the rate of a piecewise-constant method (error ~ mean panel
+area, Sec. "Spherical cavity"), and Richardson extrapolation over three meshes
+must land on it.
+"""
+import numpy as np
+import pytest
+from scipy import special
+
+import gen
+from oracle import kirkwood as kw, multipole as mp
+
+FOUR_PI = 4.0 * np.pi
+
+
+def test_g_coefficients_vs_scipy():
+    for x in (0.05, 0.5, 1.0, 3.0):
+        g = kw.g_coeffs(30, x)
+        n = np.arange(31)
+        ref = x * special.spherical_kn(n, x, derivative=True) / special.spherical_kn(n, x)
+        assert np.allclose(g, ref, rtol=1e-12)
+    g0 = kw.g_coeffs(5, 0.0)
+    assert np.array_equal(g0, -(np.arange(6) + 1.0))
+
+
+def test_born_and_centred_dipole():
+    for eps1, eps2, kappa, a in ((1.0, 80.0, 0.125, 4.0), (2.0, 78.3, 0.0, 3.0)):
+        s = gen.Sites(pos=np.zeros((1, 3)), q=np.array([1.3]), d=np.zeros((1, 3)), Q=np.zeros((1, 3, 3)),
+                      alpha=np.zeros(1))
+        got, _, _ = kw.solvation(s, a, eps1, eps2, kappa, 0.39)
+        assert abs(got - kw.born(1.3, a, eps1, eps2, kappa)) < 1e-12 * abs(got)
+        p = np.array([0.2, -0.4, 0.3])
+        s = gen.Sites(pos=np.zeros((1, 3)), q=np.zeros(1), d=p[None], Q=np.zeros((1, 3, 3)), alpha=np.zeros(1))
+        got, _, _ = kw.solvation(s, a, eps1, eps2, kappa, 0.39)
+        f1 = kw.f_coeffs(1, eps1, eps2, kappa, a)[1]
+        ref = 0.5 * f1 * (p @ p) / (FOUR_PI * a ** 3) * mp.KCAL_PER_UNIT
+        assert abs(got - ref) < 1e-12 * abs(ref)
+    # Born example: q = 1, a = 4 A, eps 1/80, no salt -> -40.99 kcal/mol
+    assert abs(kw.born(1.0, 4.0, 1.0, 80.0, 0.0) + 40.99) < 0.01
+
+
+def _series(r, s, f, a):
+    rn, sn = np.linalg.norm(r), np.linalg.norm(s)
+    c = r @ s / (rn * sn)
+    n = np.arange(f.size)
+    return np.sum(f * (rn * sn / a ** 2) ** n * special.eval_legendre(n, c)) / (FOUR_PI * a)
+
+
+def test_reaction_jets_vs_fd_and_reciprocity():
+    a = 4.0
+    f = kw.f_coeffs(120, 1.0, 80.0, 0.125, a)
+    rng = np.random.default_rng(8)
+    r0 = rng.normal(size=3) * 1.2
+    s0 = rng.normal(size=3) * 1.1
+    u = rng.normal(size=3)
+    v = rng.normal(size=3)
+    J = kw.reaction_jets(r0[None], u[None], s0[None], v[None], f, a)[0]
+    assert abs(J[0, 0] - _series(r0, s0, f, a)) < 1e-14
+    assert abs(J[0, 0] - _series(s0, r0, f, a)) < 1e-14
+    h = 1e-4
+    G = lambda e, d: _series(r0 + e * u, s0 + d * v, f, a)
+    d10 = (G(h, 0) - G(-h, 0)) / (2 * h)
+    d01 = (G(0, h) - G(0, -h)) / (2 * h)
+    d11 = (G(h, h) - G(h, -h) - G(-h, h) + G(-h, -h)) / (4 * h * h)
+    d20 = (G(h, 0) - 2 * G(0, 0) + G(-h, 0)) / (h * h)
+    assert abs(J[1, 0] - d10) < 1e-9
+    assert abs(J[0, 1] - d01) < 1e-9
+    assert abs(J[1, 1] - d11) < 1e-7
+    assert abs(2 * J[2, 0] - d20) < 1e-6
+
+
+def _problem_on(sub, sites, params, radius=4.0):
+    v, f = gen.icosphere(radius, sub)
+    return gen.Problem("sphere", v, f, sites, params)
+
+
+@pytest.mark.slow
+def test_oracle_bem_converges_to_kirkwood_config1():
+    """Config-1 sites: error ~ A (ratio ~4 per subdivision), Richardson within 1e-4."""
+    pr = gen.config1()
+    exact, _, _ = kw.solvation(pr.sites, 4.0, 1.0, 80.0, 0.125, 0.39)
+    vals = [mp.solvation(_problem_on(s, pr.sites, pr.params)).dG_kcal for s in (2, 3, 4)]
+    e = np.abs(np.array(vals) - exact)
+    assert 3.5 < e[0] / e[1] < 4.5 and 3.5 < e[1] / e[2] < 4.5
+    rich = vals[2] + (vals[2] - vals[1]) / 3.0
+    assert abs(rich - exact) < 1e-4 * abs(exact)
+
+
+def test_oracle_bem_random_multipoles_vs_kirkwood():
+    """Random charges, dipoles, traceless quadrupoles and Thole-damped polarizable sites."""
+    pr = gen.sphere_random(4.0, 2, 5, 2.2, 1.2, 11)
+    exact, mu_ex, _ = kw.solvation(pr.sites, 4.0, 1.0, 80.0, 0.125, 0.39)
+    vals = []
+    for s in (2, 3):
+        r = mp.solvation(_problem_on(s, pr.sites, pr.params), direct_polarization=True)
+        vals.append(r.dG_kcal)
+    e = np.abs(np.array(vals) - exact)
+    assert e[1] < e[0] / 3.0
+    rich = vals[1] + (vals[1] - vals[0]) / 3.0
+    assert abs(rich - exact) < 2e-3 * abs(exact)
+    assert abs(vals[1] - exact) < 1e-2 * abs(exact)
+
+
+def test_equal_permittivity_no_salt_has_no_reaction():
+    """eps1 = eps2, kappa = 0: the medium is homogeneous, so Delta G_solv -> 0 with refinement."""
+    pr = gen.sphere_random(4.0, 2, 4, 2.0, 1.2, 12)
+    pr.params.eps_out = 1.0
+    pr.params.kappa = 0.0
+    g = [mp.solvation(_problem_on(s, pr.sites, pr.params), direct_polarization=True).dG_kcal for s in (2, 3)]
+    assert abs(g[1]) < abs(g[0]) / 3.0
+    pr2 = gen.sphere_random(4.0, 2, 4, 2.0, 1.2, 12)
+    ref = abs(mp.solvation(_problem_on(3, pr2.sites, pr2.params), direct_polarization=True).dG_kcal)
+    assert abs(g[1]) < 1e-2 * ref
+
+
+@pytest.mark.parametrize("kind", ["quadrupole", "dipole", "charge"])
+def test_single_moment_off_centre_vs_kirkwood(kind):
+    """One off-centre site carrying only one kind of moment, so that moment's reaction
+    energy is the whole of Delta G: checks each term of Eqs. rhs_multipole and
+    energy_multipole_polarizable in isolation (O(A) convergence, Richardson)."""
+    rng = np.random.default_rng(21)
+    q = np.zeros(1)
+    d = np.zeros((1, 3))
+    Q = np.zeros((1, 3, 3))
+    if kind == "quadrupole":
+        A = rng.normal(size=(3, 3))
+        A = A + A.T
+        Q[0] = A - np.trace(A) / 3 * np.eye(3)
+    elif kind == "dipole":
+        d[0] = rng.normal(size=3)
+    else:
+        q[0] = 0.7
+    s = gen.Sites(pos=np.array([[0.9, -0.6, 1.1]]), q=q, d=d, Q=Q, alpha=np.zeros(1))
+    exact, _, _ = kw.solvation(s, 4.0, 1.0, 80.0, 0.125, 0.39)
+    vals = [mp.solvation(_problem_on(sub, s, gen.Params())).dG_kcal for sub in (2, 3)]
+    e = np.abs(np.array(vals) - exact)
+    assert 3.0 < e[0] / e[1] < 5.0
+    rich = vals[1] + (vals[1] - vals[0]) / 3.0
+    assert abs(rich - exact) < 3e-3 * abs(exact)
