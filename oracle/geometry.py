@@ -58,13 +58,22 @@ def gauss_rule(k: int):
 
 
 def gauss_points(verts: np.ndarray, tris: np.ndarray, k: int):
-    """Gauss-node positions y_jg [N, K, 3] and weights W_jg = w_g * A_j [N, K]."""
+    """Gauss-node positions y_jg [N, K, 3] and weights W_jg = w_g * A_j [N, K].
+
+    The centroid node of the K=1 and K=4 rules is placed at the panel centroid
+    itself, computed exactly as the collocation point ((v0 + v1) + v2) / 3: the
+    node then coincides with its own panel's collocation point to the last bit,
+    so that pair has r = 0 and contributes nothing (a product form
+    v0/3 + v1/3 + v2/3 would miss the centroid by rounding and leave a spurious
+    1/r ~ 1e16 term)."""
     lam, w = gauss_rule(k)
     v0 = verts[tris[:, 0]]
     v1 = verts[tris[:, 1]]
     v2 = verts[tris[:, 2]]
     y = (lam[None, :, 0, None] * v0[:, None, :] + lam[None, :, 1, None] * v1[:, None, :]
          + lam[None, :, 2, None] * v2[:, None, :])
+    if k in (1, 4):
+        y[:, 0, :] = (v0 + v1 + v2) / 3.0
     _, _, area = panel_geometry(verts, tris)
     return y, w[None, :] * area[:, None]
 
