@@ -1,0 +1,352 @@
+#!/usr/bin/env python
+"""Benchmark: time per Delta G_solv and matrix-vector interactions/s at 81,920 panels.
+
+Workload (one "step" = one pass of the whole path): bumpy star surface R = 14 A
+mapped from icosphere subdivision 6 (81,920 flat panels, K = 4 Gauss nodes each),
+2,000 AMOEBA-like multipole sites; eps 1/80, kappa 0.125 1/A; GMRES tol 1e-6, SCF
+tol 1e-6 e*A.  Each step sets the mesh and sites from device-resident arrays
+(geometry, Morton order, near-field tables, tree), runs the vacuum and dissolved
+self-consistent loops (RHS, GMRES with the chosen operator, reaction fields,
+Thole fields, SOR) and the energy.  Inputs are seeded synthetic data.
+
+Also measured: the matvec alone for the chosen operator and for the FP64 direct
+operator (effective interactions/s = N * N * K / t), the end-to-end step through
+the C ABI from pinned host buffers, and the FP64 oracle on the host cores on a
+bounded sample (the CPU baseline).
+
+Launch: python bench.py [--gpus N --steps K --warmup W] ; for N > 1 under
+torch.distributed.run each rank solves its own replica (independent problems, no
+collective in the data path: weak scaling).  --impl reference times the oracle.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("time per ΔG_solv + matvec Ginter/s, FP32-tree vs FP64-direct, 81,920 panels")
+UNIT = "s/ΔG_solv"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+FLOPS_PER_PAIR = 28   # FP32 flops (FMA = 2) of one Gauss-node/target pair in the pair kernel
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--op", default="fp32_direct")
+    ap.add_argument("--residual-op", default=None)
+    ap.add_argument("--matvec-reps", type=int, default=10)
+    ap.add_argument("--fp64-reps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-rows", type=int, default=384)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread is not None:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx.append(float(r[1]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 3 + k and r[3 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- helpers
+def build_library():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bempol_build", os.path.join(ROOT, "paper_1810_03698_gb300",
+                                                                               "build.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+
+
+def workload():
+    import gen
+    return gen.config3()
+
+
+def solver_kwargs(pr, op, residual_op):
+    p = pr.params
+    return dict(eps_in=p.eps_in, eps_out=p.eps_out, kappa=p.kappa, gauss_k=p.gauss_k, near_factor=p.near_factor,
+                theta=p.theta, order=p.order, leaf=p.leaf, gmres_tol=p.gmres_tol, gmres_restart=p.gmres_restart,
+                gmres_maxit=p.gmres_maxit, scf_tol=p.scf_tol, sor_omega=p.sor_omega, scf_maxit=p.scf_maxit,
+                thole_a=p.thole_a, op=op, residual_op=residual_op)
+
+
+def cpu_baseline(pr, rows_n, matvecs_per_solve):
+    """FP64 oracle on a bounded sample: rows of the FP64 matvec, extrapolated per Delta G."""
+    from oracle import bem
+    t0 = time.time()
+    par = pr.params
+    mesh = bem.build_mesh(pr.verts, pr.tris, par.gauss_k, par.near_factor)
+    t_mesh = time.time() - t0
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=2 * mesh.n)
+    rows = np.sort(rng.choice(mesh.n, size=min(rows_n, mesh.n), replace=False))
+    t0 = time.time()
+    bem.matvec_rows(mesh, x, rows, par.eps_in, par.eps_out, par.kappa)
+    t_rows = time.time() - t0
+    t_matvec = t_rows * mesh.n / rows.size
+    pairs_per_s = rows.size * mesh.n * par.gauss_k / t_rows
+    return {
+        "value": t_matvec * matvecs_per_solve + t_mesh, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "sample": (f"FP64 oracle matvec on {rows.size} of {mesh.n} target rows ({t_rows:.1f} s), extrapolated to a "
+                   f"full matvec ({t_matvec:.1f} s) x {matvecs_per_solve} matvecs per Delta G (the count the GPU "
+                   f"solve used) + oracle mesh set-up ({t_mesh:.1f} s); numpy elementwise, one core"),
+        "matvec_pairs_per_s": pairs_per_s,
+    }
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    pr = workload()
+    matvecs = 400   # matvecs of one FP32-direct Delta G solve on this workload (from the native arm)
+    times = []
+    for k in range(args.warmup + args.steps):
+        t0 = time.time()
+        cb = cpu_baseline(pr, 64, matvecs)
+        if k >= args.warmup:
+            times.append(cb["value"])
+    v = float(np.mean(times))
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": pr.name, "panels": pr.n_panels, "sites": pr.sites.n},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- native arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    build_library()
+    import paper_1810_03698_gb300 as bp
+
+    pr = workload()
+    res_op = args.residual_op or args.op
+    s = bp.Solver(device=local, **solver_kwargs(pr, args.op, res_op))
+    dev = f"cuda:{local}"
+    st = pr.sites
+    d_verts = torch.tensor(pr.verts, dtype=torch.float64, device=dev)
+    d_tris = torch.tensor(pr.tris, dtype=torch.int32, device=dev)
+    d_site = [torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device=dev)
+              for a in (st.pos, st.q, st.d, st.Q.reshape(-1, 9), st.alpha)]
+    d_group = torch.tensor(st.group, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        s.set_mesh(d_verts, d_tris)
+        s.set_sites(*d_site, group=d_group)
+        return s.solve()
+
+    for _ in range(args.warmup):
+        out = step()
+    s.stats_enable(True)
+    s.stats(reset=True)
+    sampler = ClockSampler(local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall0 = time.time()
+    step_ms = []
+    outs = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)            # evict L2 between timed steps (not timed)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall = time.time() - t_wall0
+    clocks = sampler.stop()
+    stats = s.stats(reset=True)
+    total_ms = float(np.sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = total_ms / 1e3 / (args.steps * world)
+    out = outs[-1]
+
+    # ---- matvec alone: chosen operator and FP64 direct
+    n = pr.n_panels
+    K = pr.params.gauss_k
+    x = torch.randn(2 * n, dtype=torch.float64, device=dev)
+    y = torch.empty_like(x)
+
+    def time_matvec(op, reps):
+        s.matvec(x, y, op=op)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            s.matvec(x, y, op=op)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    s.stats(reset=True)
+    mv_ms = time_matvec(args.op, args.matvec_reps)
+    mv_stats = s.stats(reset=True)
+    f64_ms = time_matvec("fp64_direct", args.fp64_reps) if args.fp64_reps > 0 else None
+    s.stats(reset=True)
+    inter = float(n) * n * K
+
+    # ---- roofline of the dominant kernel (pair kernel), live CUDA-event durations inside the timed steps
+    pair_launch_ms = stats["pair_ms"] / max(1, stats["pair_launches"])
+    pairs_per_launch = stats["pair_interactions"] / max(1, stats["pair_launches"])
+    achieved = pairs_per_launch * FLOPS_PER_PAIR / (pair_launch_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "kernel": "p2p_f32_kernel" if args.op == "fp32_direct" else "pair kernel",
+                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                "traffic": None, "flops_per_pair": FLOPS_PER_PAIR, "pairs_per_launch": pairs_per_launch,
+                "avg_launch_ms": pair_launch_ms,
+                "share_of_step": stats["pair_ms"] / max(total_ms, 1e-9)}
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a, dt: torch.tensor(np.ascontiguousarray(a), dtype=dt).pin_memory()
+        h_verts = pin(pr.verts, torch.float64)
+        h_tris = pin(pr.tris, torch.int32)
+        h_site = [pin(a, torch.float64) for a in (st.pos, st.q, st.d, st.Q.reshape(-1, 9), st.alpha)]
+        h_group = pin(st.group, torch.int32)
+        h2d = sum(t.numel() * t.element_size() for t in [h_verts, h_tris, h_group] + h_site)
+        e2e_ms = []
+        d2h = 0
+        for k in range(args.steps + 1):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.set_mesh(h_verts, h_tris)
+            s.set_sites(*h_site, group=h_group)
+            o = s.solve(outputs=True, where="host")
+            t1 = time.perf_counter()
+            d2h = sum(o[k2].nbytes for k2 in ("phi", "dphidn", "site_reaction", "mu_diss", "mu_vac")) + 8 * 3
+            if k > 0:
+                e2e_ms.append((t1 - t0) * 1e3)
+        e2e = {"value": float(np.mean(e2e_ms)) / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    cpu = None
+    if not args.no_cpu:
+        cpu = cpu_baseline(pr, args.cpu_rows, int(out["matvecs_total"]))
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if "fp32" in args.op else "f64",
+        "data": "synthetic",
+        "config": {"workload": pr.name, "panels": n, "gauss_k": K, "sites": st.n, "op": args.op,
+                   "residual_op": res_op, "theta": pr.params.theta, "order": pr.params.order,
+                   "gmres_tol": pr.params.gmres_tol, "scf_tol": pr.params.scf_tol,
+                   "l2": "flushed (512 MiB write) between timed steps, flush not timed"},
+        "solve": {"dG_solv_kcal": out["dG_solv_kcal"], "scf_iters_diss": out["scf_iters_diss"],
+                  "scf_iters_vac": out["scf_iters_vac"], "gmres_iters": out["gmres_iters_total"],
+                  "matvecs": out["matvecs_total"], "bem_solves": out["n_solves"],
+                  "last_rel_residual": out["last_rel_residual"], "t_setup_ms": out["t_setup_ms"],
+                  "t_scf_ms": out["t_scf_ms"], "wall_s_timed_region": wall},
+        "matvec": {"op": args.op, "ms": mv_ms, "effective_ginter_s": inter / (mv_ms * 1e-3) / 1e9,
+                   "performed_pairs": mv_stats["pair_interactions"] / max(1, args.matvec_reps),
+                   "fp64_direct_ms": f64_ms,
+                   "fp64_direct_ginter_s": (inter / (f64_ms * 1e-3) / 1e9) if f64_ms else None,
+                   "interactions_per_matvec": inter},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(stats["kernel_launches"]),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -18,7 +18,7 @@ from dataclasses import dataclass, field, replace
 
 import numpy as np
 
-from .surfaces import icosphere, bumpy_surface
+from .surfaces import icosphere, bumpy_surface, mesh_stats
 from .sites import Sites, random_multipoles, sample_ball, sample_inside, StarSurfaceInside
 
 SEED_BASE = 1810036980
@@ -96,6 +96,9 @@ def bumpy_problem(radius: float, subdiv: int, n_sites: int, seed_index: int,
     rng = np.random.default_rng(SEED_BASE + seed_index)
     v, f, coeffs = bumpy_surface(radius, subdiv, rng)
     surf = StarSurfaceInside(v, f, subdiv)
+    # sites must also clear the near-singular radius 2 sqrt(A) of every panel
+    _, area, _ = mesh_stats(v, f)
+    min_surface = max(min_surface, 2.0 * float(np.sqrt(area.max())) + 0.2)
     rmax = radius * 1.12 - min_surface
     pos = sample_inside(rng, surf, n_sites, rmax, min_surface, min_sep)
     q, d, Q, alpha = random_multipoles(rng, n_sites)

@@ -1,0 +1,241 @@
+/*
+ * bempol.h -- C ABI of a GB300 (sm_103a) boundary-integral Poisson-Boltzmann solver
+ * with polarizable point multipoles (Cooper, "A boundary-integral approach for the
+ * Poisson-Boltzmann equation with polarizable force fields", arXiv:1810.03698).
+ *
+ * Model (Sec. "The boundary integral formulation", Eqs. pde, green_identity,
+ * layers, free-space, integral_eq): solute region Omega_1 (permittivity eps_in,
+ * point multipoles), solvent Omega_2 (eps_out, inverse Debye length kappa), interface
+ * Gamma given as a closed triangle mesh.  Unknowns are phi and psi = dphi_1/dn on
+ * Gamma, piecewise constant per flat panel, collocated at the panel centroids
+ * (Sec. "The boundary element method"):
+ *
+ *   phi_i/2 + K_L[phi]_i - V_L[psi]_i                    = RHS_i   (Eq. rhs_multipole)
+ *   phi_i/2 - K_Y[phi]_i + (eps_in/eps_out) V_Y[psi]_i   = 0
+ *
+ * with G_L = 1/(4 pi r), G_Y = e^{-kappa r}/(4 pi r), V = int G, K = int dG/dn_y
+ * (n the outward normal of the source panel).  Far-away panels use a K-node
+ * Gauss rule; panels within near_factor*sqrt(A_i) of collocation point i use
+ * FP64 semi-analytical integrals.
+ *
+ * Units: angstrom, elementary charge; potentials q/(4 pi eps r) (vacuum
+ * permittivity 1); polarizabilities are polarizability volumes (A^3), so an
+ * induced dipole is mu = 4 pi alpha E in these units (Eq. induced_dipole);
+ * energies are reported in kcal/mol (1 e^2/A in these units = 4 pi * 332.0637).
+ *
+ * Conventions common to every entry point
+ *  - Every function returns a bempol_status; on error the context keeps a
+ *    message readable with bempol_last_error().  Nothing aborts the process.
+ *  - Pointers marked "host or device" are read or written according to the
+ *    `where` argument (BEMPOL_HOST or BEMPOL_DEVICE).  Device pointers belong to
+ *    the current CUDA context of the device given to bempol_create.
+ *  - Pointers marked "device" must be device memory; "host" must be host memory.
+ *  - The caller owns every buffer it passes; the library owns its internal
+ *    geometry, tree, near-field tables and solver workspaces (allocated by
+ *    bempol_set_mesh / bempol_set_sites / first solve, freed by bempol_destroy).
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Compute entry
+ *    points enqueue their work on that stream; solver entry points also
+ *    synchronise it to read convergence scalars.
+ *  - Panel-indexed arrays at the ABI are in the caller's triangle order
+ *    (the library reorders internally and maps back).
+ *  - Double-precision is used at the ABI throughout.
+ */
+#ifndef BEMPOL_H
+#define BEMPOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bempol_ctx bempol_ctx;
+
+typedef enum {
+  BEMPOL_OK = 0,
+  BEMPOL_ERR_ARG = 1,             /* bad argument (NULL, size, enum, parameter range) */
+  BEMPOL_ERR_MESH = 2,            /* mesh fails validation (index range, degenerate or inverted panel, not closed) */
+  BEMPOL_ERR_SITES = 3,           /* sites fail validation (outside or within the near radius of a panel, alpha < 0, Q not symmetric traceless) */
+  BEMPOL_ERR_NOT_CONVERGED = 4,   /* GMRES or SCF hit its iteration limit; results hold the last iterate */
+  BEMPOL_ERR_CUDA = 5,            /* a CUDA runtime call failed (message has the CUDA error string) */
+  BEMPOL_ERR_TIMEOUT = 6,         /* a bounded device-side wait expired */
+  BEMPOL_ERR_OOM = 7,             /* device allocation failed */
+  BEMPOL_ERR_STATE = 8            /* call out of order (e.g. solve before set_mesh) */
+} bempol_status;
+
+enum { BEMPOL_HOST = 0, BEMPOL_DEVICE = 1 };
+
+/* Matrix-vector product / operator forms. */
+enum {
+  BEMPOL_OP_FP64_DIRECT = 0,   /* every Gauss-node pair in FP64, FP64 sums */
+  BEMPOL_OP_FP32_DIRECT = 1,   /* every pair in FP32, FP32 tile sums, FP64 per-target sums */
+  BEMPOL_OP_FP32_TREE = 2,     /* treecode (Taylor far field, theta, order) in FP32, FP64 per-target sums */
+  BEMPOL_OP_FP64_TREE = 3      /* treecode in FP64 */
+};
+
+typedef struct {
+  double eps_in, eps_out;      /* relative permittivities of solute and solvent */
+  double kappa;                /* inverse Debye length, 1/A (>= 0) */
+  int gauss_k;                 /* Gauss nodes per far panel: 1, 3 or 4 */
+  double near_factor;          /* near-singular threshold: |x_i - c_j| < near_factor*sqrt(A_i) */
+  double theta;                /* treecode multipole acceptance: cell accepted if R_cell / dist < theta */
+  int order;                   /* treecode Taylor order P (1..10) */
+  int leaf;                    /* treecode maximum panels per leaf */
+  double gmres_tol;            /* stop when ||b - A x||_2 / ||b||_2 < gmres_tol */
+  int gmres_restart;           /* Krylov basis size before a restart */
+  int gmres_maxit;             /* total GMRES iterations per solve */
+  double scf_tol;              /* SCF stop: sqrt(sum_i |mu_new - mu_old|^2 / Ns) < scf_tol (e*A) */
+  double sor_omega;            /* SOR coefficient (paper: 0.7) */
+  int scf_maxit;
+  int op;                      /* operator used inside GMRES: BEMPOL_OP_* */
+  int residual_op;             /* operator for the outer FP64 residual of iterative refinement
+                                  (BEMPOL_OP_*; equal to `op` = plain GMRES, no refinement) */
+  double inner_tol;            /* relative tolerance of each inner solve under refinement */
+  int refine_maxit;            /* maximum refinement (outer) steps */
+  double thole_a;              /* Thole damping parameter (AMOEBA: 0.39) */
+} bempol_params;
+
+typedef struct {
+  /* scalars, always written (host memory inside this struct) */
+  double dG_solv_kcal;         /* G_diss - G_vac in kcal/mol (Eqs. deltaG_aux2, energy_multipole_polarizable) */
+  double G_diss, G_vac;        /* the two energies in the paper's units (e^2/A, vacuum permittivity 1) */
+  int scf_iters_diss, scf_iters_vac;
+  int gmres_iters_total;       /* GMRES iterations summed over all solves */
+  int matvecs_total;           /* operator applications (inner + residual) */
+  int n_solves;                /* BEM solves performed */
+  double last_rel_residual;    /* ||b - A x|| / ||b|| of the final BEM solve (with residual_op) */
+  double t_setup_ms, t_scf_ms, t_total_ms;   /* wall time of the phases, measured on the stream */
+  /* optional outputs (NULL to skip), in the caller's order; host or device per `where` */
+  double* phi;                 /* [N]   potential on the panels */
+  double* dphidn;              /* [N]   dphi_1/dn on the panels */
+  double* site_reaction;       /* [Ns*10] per site: phi_solv, grad phi_solv (3), Hessian xx,xy,xz,yy,yz,zz */
+  double* mu_diss;             /* [Ns*3] induced dipoles, dissolved state */
+  double* mu_vac;              /* [Ns*3] induced dipoles, vacuum state */
+  int where;                   /* BEMPOL_HOST or BEMPOL_DEVICE for the optional outputs */
+} bempol_result;
+
+/* Fill `p` with the defaults: eps 1/80, kappa 0.125, K=4, near 2.0, theta 0.5,
+ * P=5, leaf 256, GMRES 1e-8/100/500, SCF 1e-8/omega 0.7/200, op FP64 direct,
+ * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39. */
+void bempol_default_params(bempol_params* p);
+
+/* Create a context on CUDA device `device`.  Validates `p` (ranges above);
+ * BEMPOL_ERR_ARG on a bad value, BEMPOL_ERR_CUDA if the device cannot be used.
+ * *out is NULL on failure. */
+bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out);
+
+/* Replace the parameters of an existing context (same validation as create).
+ * Geometry-dependent tables are rebuilt on the next call that needs them when
+ * gauss_k, near_factor, kappa or leaf change. */
+bempol_status bempol_set_params(bempol_ctx* c, const bempol_params* p);
+
+/* Release everything the context owns.  NULL is a no-op. */
+void bempol_destroy(bempol_ctx* c);
+
+/* Message of the last error on this context ("" when none); owned by the context. */
+const char* bempol_last_error(const bempol_ctx* c);
+
+/* Set the surface (Sec. "The boundary element method": flat triangles).
+ *   verts [nv*3] float64 (x,y,z per vertex), host or device per `where`
+ *   tris  [nt*3] int32, counter-clockwise seen from the solvent side (so
+ *         (v1-v0)x(v2-v0) is the outward normal n of Eq. pde), host or device
+ * Validates index range, zero-area panels and closedness (every edge shared by
+ * exactly two panels with opposite orientation), then builds on `stream`: panel
+ * centroids/normals/areas, Gauss nodes, the Morton-ordered panel permutation and
+ * treecode cells, the near-pair list and its FP64 semi-analytical corrections
+ * (exact minus K-node value for each near pair).  Synchronises `stream`.
+ * Errors: BEMPOL_ERR_ARG, BEMPOL_ERR_MESH, BEMPOL_ERR_OOM, BEMPOL_ERR_CUDA. */
+bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt,
+                              const int32_t* tris, int where, void* stream);
+
+/* Set the point multipoles (Eqs. pot_multipole, induced_dipole).
+ *   pos   [ns*3] A;  q [ns] e;  d [ns*3] permanent dipoles e*A;
+ *   Q     [ns*9] e*A^2, row-major 3x3, symmetric and traceless in the paper's
+ *         convention Q = int rho (3 r r - r^2 I) (a trace below 1e-9 |Q| is
+ *         removed, a larger one or asymmetry is rejected);
+ *   alpha [ns] polarizability volumes A^3 (>= 0);
+ *   group [ns] int32 polarisation group (NULL = every site its own group).
+ * All host or device per `where`.  Validation: every site strictly inside the
+ * surface and farther than near_factor*sqrt(A_j) from every panel centroid j
+ * (BEMPOL_ERR_SITES).  Requires bempol_set_mesh first (BEMPOL_ERR_STATE). */
+bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, const double* q,
+                               const double* d, const double* Q, const double* alpha,
+                               const int32_t* group, int where, void* stream);
+
+/* Solvation free energy Delta G_solv = G_diss - G_vac (Sec. "Calculation of the
+ * solvation energy") with the self-consistent induced dipoles of Sec.
+ * "Self-consistent induced field": vacuum SCF; then mu = 0, repeat { solve the
+ * BEM system with RHS from p = d + mu (GMRES with params.op, warm-started, FP64
+ * Krylov basis, optional FP64 iterative refinement with params.residual_op);
+ * E = E_solv + E_mult; mu <- (1-omega) mu + omega 4 pi alpha E } until the RMS
+ * change < scf_tol; one more solve with the converged mu; energy of Eq.
+ * energy_multipole_polarizable.  Fills `out` (scalars always, arrays if non-NULL).
+ * Returns BEMPOL_ERR_NOT_CONVERGED (with `out` filled) if GMRES or the SCF hit
+ * their limits.  Synchronises `stream`. */
+bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out);
+
+/* y = A x for the operator form `op` (BEMPOL_OP_*), one matrix-vector product of
+ * Eq. integral_eq.  x, y: device float64 [2N] = [phi; psi] in the caller's panel
+ * order (y may not alias x).  Enqueued on `stream`, no synchronisation. */
+bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, void* stream);
+
+/* Right-hand side of Eq. rhs_multipole at every collocation point, with the
+ * sites' q and Q and the total dipoles p (device float64 [ns*3]; NULL = the
+ * permanent d).  b: device float64 [N] (caller order).  `op` selects FP64
+ * (BEMPOL_OP_FP64_*) or FP32-pair/FP64-sum arithmetic.  Enqueued on `stream`. */
+bempol_status bempol_rhs(bempol_ctx* c, const double* p, double* b, int op, void* stream);
+
+/* Reaction potential, field gradient and Hessian at the sites from a surface
+ * solution x = [phi; psi] (device float64 [2N], caller order) (Eqs. pot_solvent,
+ * Efield_solv, ddphi): out [ns*10] device float64, per site phi_solv,
+ * dphi/dx,dy,dz, then d2phi xx,xy,xz,yy,yz,zz.  K-node quadrature over every
+ * panel (sites are validated to be far from the surface).  Enqueued on `stream`. */
+bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, int op, void* stream);
+
+/* Multipole-multipole potentials at the sites (Eqs. Efield_mult,
+ * second_derivative) with induced dipoles mu (device float64 [ns*3], NULL = 0):
+ *   mode 0 (polarising field): permanent moments of the same polarisation group
+ *          are masked, induced dipoles Thole-damped; out [ns*3] = E (field).
+ *   mode 1 (energy): permanent moments unmasked, induced dipoles damped;
+ *          out [ns*10] = phi, grad phi (3), Hessian (6) as in bempol_site_reaction.
+ * FP64.  Enqueued on `stream`. */
+bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, double* out, void* stream);
+
+/* Sizes of the library's tables: number of panels, Gauss nodes per panel,
+ * sites, near pairs, treecode cells and leaves (any pointer may be NULL). */
+bempol_status bempol_sizes(const bempol_ctx* c, int64_t* n_panels, int32_t* gauss_k, int64_t* n_sites,
+                           int64_t* n_near, int64_t* n_cells, int64_t* n_leaves);
+
+/* Kernel accounting (not part of the method; for measurement).  When enabled,
+ * the pair kernels (direct or treecode near field) and the treecode far-field
+ * kernel are bracketed by CUDA events on their launch stream; bempol_stats_read
+ * synchronises the device and reports the summed event times. */
+typedef struct {
+  int64_t kernel_launches;     /* kernels this library launched (all contexts) since the last reset */
+  int64_t pair_launches;       /* launches of the pair kernel */
+  double pair_ms;              /* summed CUDA-event time of those launches (0 unless enabled) */
+  int64_t far_launches;        /* launches of the treecode far-field kernel */
+  double far_ms;
+  int64_t pair_interactions;   /* (target, Gauss node) pairs evaluated by the pair kernels */
+  int64_t far_evaluations;     /* (target, cell) Taylor evaluations of the far-field kernel */
+} bempol_stats;
+
+/* Turn event timing on (1) or off (0).  Counting is always on. */
+bempol_status bempol_stats_enable(bempol_ctx* c, int enable);
+
+/* Read the counters (host struct); reset = 1 zeroes them afterwards. */
+bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset);
+
+/* Copy out the geometry and the near-field table, in the caller's order (host
+ * pointers, any may be NULL): centroid [N*3], normal [N*3], area [N];
+ * near_ptr [N+1] int64 (CSR rows), near_col [n_near] int32 (ascending per row),
+ * near_corr [n_near*4] float64 per pair (V_L, K_L, V_Y, K_Y) of
+ * (semi-analytical - K-node) integrals including 1/(4 pi).  Synchronises. */
+bempol_status bempol_get_geometry(bempol_ctx* c, double* centroid, double* normal, double* area,
+                                  int64_t* near_ptr, int32_t* near_col, double* near_corr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BEMPOL_H */

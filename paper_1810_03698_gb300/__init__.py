@@ -1,0 +1,268 @@
+"""GB300 boundary-integral Poisson-Boltzmann solver with polarizable multipoles.
+
+A thin binding over the C ABI of ``libbempol.so`` (see ``include/bempol.h``):
+argument marshalling only, every step of the computation runs in the library's
+CUDA kernels.  PyTorch supplies device memory and streams.
+
+The shared library is built in-tree by ``paper_1810_03698_gb300.build``; importing
+this package without it raises ImportError (there is no CPU fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libbempol.so")
+
+HOST, DEVICE = 0, 1
+OP_FP64_DIRECT, OP_FP32_DIRECT, OP_FP32_TREE, OP_FP64_TREE = 0, 1, 2, 3
+OP_NAMES = {"fp64_direct": 0, "fp32_direct": 1, "fp32_tree": 2, "fp64_tree": 3}
+
+STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_SITES", 4: "ERR_NOT_CONVERGED", 5: "ERR_CUDA",
+          6: "ERR_TIMEOUT", 7: "ERR_OOM", 8: "ERR_STATE"}
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("eps_in", C.c_double), ("eps_out", C.c_double), ("kappa", C.c_double),
+        ("gauss_k", C.c_int), ("near_factor", C.c_double),
+        ("theta", C.c_double), ("order", C.c_int), ("leaf", C.c_int),
+        ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
+        ("scf_tol", C.c_double), ("sor_omega", C.c_double), ("scf_maxit", C.c_int),
+        ("op", C.c_int), ("residual_op", C.c_int), ("inner_tol", C.c_double), ("refine_maxit", C.c_int),
+        ("thole_a", C.c_double),
+    ]
+
+
+class Result(C.Structure):
+    _fields_ = [
+        ("dG_solv_kcal", C.c_double), ("G_diss", C.c_double), ("G_vac", C.c_double),
+        ("scf_iters_diss", C.c_int), ("scf_iters_vac", C.c_int), ("gmres_iters_total", C.c_int),
+        ("matvecs_total", C.c_int), ("n_solves", C.c_int), ("last_rel_residual", C.c_double),
+        ("t_setup_ms", C.c_double), ("t_scf_ms", C.c_double), ("t_total_ms", C.c_double),
+        ("phi", C.c_void_p), ("dphidn", C.c_void_p), ("site_reaction", C.c_void_p),
+        ("mu_diss", C.c_void_p), ("mu_vac", C.c_void_p), ("where", C.c_int),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("kernel_launches", C.c_int64), ("pair_launches", C.c_int64), ("pair_ms", C.c_double),
+        ("far_launches", C.c_int64), ("far_ms", C.c_double), ("pair_interactions", C.c_int64),
+        ("far_evaluations", C.c_int64),
+    ]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1810_03698_gb300.build`")
+    lib = C.CDLL(LIB_PATH)
+    vp, i64, i32, dp = C.c_void_p, C.c_int64, C.c_int, C.c_double
+    sig = {
+        "bempol_default_params": (None, [C.POINTER(Params)]),
+        "bempol_create": (i32, [C.POINTER(Params), i32, C.POINTER(vp)]),
+        "bempol_set_params": (i32, [vp, C.POINTER(Params)]),
+        "bempol_destroy": (None, [vp]),
+        "bempol_last_error": (C.c_char_p, [vp]),
+        "bempol_set_mesh": (i32, [vp, i64, vp, i64, vp, i32, vp]),
+        "bempol_set_sites": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
+        "bempol_solve": (i32, [vp, vp, C.POINTER(Result)]),
+        "bempol_matvec": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_rhs": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_site_reaction": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_multipole_field": (i32, [vp, vp, i32, vp, vp]),
+        "bempol_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(C.c_int32), C.POINTER(i64), C.POINTER(i64),
+                               C.POINTER(i64), C.POINTER(i64)]),
+        "bempol_get_geometry": (i32, [vp, vp, vp, vp, vp, vp, vp]),
+        "bempol_stats_enable": (i32, [vp, i32]),
+        "bempol_stats_read": (i32, [vp, C.POINTER(Stats), i32]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+lib = _lib
+
+
+class BempolError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def default_params(**kw) -> Params:
+    p = Params()
+    _lib.bempol_default_params(C.byref(p))
+    for k, v in kw.items():
+        if k in ("op", "residual_op") and isinstance(v, str):
+            v = OP_NAMES[v]
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(a):
+    """(pointer, where) of a numpy array (host) or torch tensor (host or device)."""
+    if a is None:
+        return None, HOST
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, HOST
+    if not a.is_contiguous():
+        raise ValueError("tensors must be contiguous")
+    return a.data_ptr(), (DEVICE if a.is_cuda else HOST)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Solver:
+    """One context of the library: a mesh, its sites and the solver parameters."""
+
+    def __init__(self, params: Params | None = None, device: int = 0, **kw):
+        self.params = params if params is not None else default_params(**kw)
+        h = C.c_void_p()
+        st = _lib.bempol_create(C.byref(self.params), device, C.byref(h))
+        if st != 0:
+            raise BempolError(st, "bempol_create failed")
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.bempol_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _chk(self, st):
+        if st != 0:
+            raise BempolError(st, _lib.bempol_last_error(self._h).decode())
+
+    def set_params(self, **kw):
+        for k, v in kw.items():
+            if k in ("op", "residual_op") and isinstance(v, str):
+                v = OP_NAMES[v]
+            setattr(self.params, k, v)
+        self._chk(_lib.bempol_set_params(self._h, C.byref(self.params)))
+
+    def set_mesh(self, verts, tris, stream=None):
+        pv, wv = _ptr(verts)
+        pt, wt = _ptr(tris)
+        if wv != wt:
+            raise ValueError("verts and tris must both be host or both be device arrays")
+        self._chk(_lib.bempol_set_mesh(self._h, verts.shape[0], pv, tris.shape[0], pt, wv, _stream(stream)))
+
+    def set_sites(self, pos, q, d, Q, alpha, group=None, stream=None):
+        arrs = [pos, q, d, Q, alpha] + ([group] if group is not None else [])
+        ptrs = [_ptr(a) for a in arrs]
+        where = {w for _, w in ptrs}
+        if len(where) != 1:
+            raise ValueError("site arrays must all be host or all be device")
+        pg = ptrs[5][0] if group is not None else None
+        self._chk(_lib.bempol_set_sites(self._h, pos.shape[0], ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0],
+                                        ptrs[4][0], pg, where.pop(), _stream(stream)))
+
+    def sizes(self):
+        v = [C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()]
+        self._chk(_lib.bempol_sizes(self._h, *[C.byref(x) for x in v]))
+        return dict(zip(["n_panels", "gauss_k", "n_sites", "n_near", "n_cells", "n_leaves"], [x.value for x in v]))
+
+    def solve(self, stream=None, outputs=False, where="host", allow_unconverged=False):
+        """Run the SCF + BEM solve; returns a dict of scalars (and arrays if ``outputs``)."""
+        r = Result()
+        arrays = {}
+        if outputs:
+            sz = self.sizes()
+            n, ns = sz["n_panels"], sz["n_sites"]
+            if where == "host":
+                mk = lambda k: np.zeros(k)
+                r.where = HOST
+            else:
+                import torch
+                mk = lambda k: torch.zeros(k, dtype=torch.float64, device=f"cuda:{self.device}")
+                r.where = DEVICE
+            arrays = {"phi": mk(n), "dphidn": mk(n), "site_reaction": mk(ns * 10), "mu_diss": mk(ns * 3),
+                      "mu_vac": mk(ns * 3)}
+            for k, a in arrays.items():
+                setattr(r, k, _ptr(a)[0])
+        st = _lib.bempol_solve(self._h, _stream(stream), C.byref(r))
+        if st != 0 and not (allow_unconverged and st == 4):
+            self._chk(st)
+        out = {k: getattr(r, k) for k, _ in Result._fields_ if k not in arrays and k != "where"}
+        out["status"] = st
+        for k, a in arrays.items():
+            out[k] = a
+        return out
+
+    def matvec(self, x, y, op=OP_FP64_DIRECT, stream=None):
+        self._chk(_lib.bempol_matvec(self._h, _ptr(x)[0], _ptr(y)[0], OP_NAMES.get(op, op), _stream(stream)))
+
+    def rhs(self, b, p=None, op=OP_FP64_DIRECT, stream=None):
+        self._chk(_lib.bempol_rhs(self._h, _ptr(p)[0], _ptr(b)[0], OP_NAMES.get(op, op), _stream(stream)))
+
+    def site_reaction(self, x, out, op=OP_FP64_DIRECT, stream=None):
+        self._chk(_lib.bempol_site_reaction(self._h, _ptr(x)[0], _ptr(out)[0], OP_NAMES.get(op, op),
+                                            _stream(stream)))
+
+    def multipole_field(self, out, mu=None, mode=0, stream=None):
+        self._chk(_lib.bempol_multipole_field(self._h, _ptr(mu)[0], mode, _ptr(out)[0], _stream(stream)))
+
+    def stats_enable(self, on=True):
+        self._chk(_lib.bempol_stats_enable(self._h, 1 if on else 0))
+
+    def stats(self, reset=False):
+        st = Stats()
+        self._chk(_lib.bempol_stats_read(self._h, C.byref(st), 1 if reset else 0))
+        return {k: getattr(st, k) for k, _ in Stats._fields_}
+
+    def geometry(self):
+        sz = self.sizes()
+        n, nnz = sz["n_panels"], sz["n_near"]
+        out = {"centroid": np.zeros((n, 3)), "normal": np.zeros((n, 3)), "area": np.zeros(n),
+               "near_ptr": np.zeros(n + 1, dtype=np.int64), "near_col": np.zeros(max(nnz, 1), dtype=np.int32),
+               "near_corr": np.zeros((max(nnz, 1), 4))}
+        self._chk(_lib.bempol_get_geometry(self._h, *[out[k].ctypes.data for k in
+                                                      ("centroid", "normal", "area", "near_ptr", "near_col",
+                                                       "near_corr")]))
+        out["near_col"] = out["near_col"][:nnz]
+        out["near_corr"] = out["near_corr"][:nnz]
+        return out
+
+
+def problem_solver(problem, device: int = 0, stream=None, **overrides) -> Solver:
+    """A Solver loaded with a ``gen.Problem`` (mesh and sites from host arrays)."""
+    par = problem.params
+    kw = dict(eps_in=par.eps_in, eps_out=par.eps_out, kappa=par.kappa, gauss_k=par.gauss_k,
+              near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,
+              gmres_tol=par.gmres_tol, gmres_restart=par.gmres_restart, gmres_maxit=par.gmres_maxit,
+              scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a)
+    kw.update(overrides)
+    s = Solver(device=device, **kw)
+    s.set_mesh(np.ascontiguousarray(problem.verts, dtype=np.float64),
+               np.ascontiguousarray(problem.tris, dtype=np.int32), stream=stream)
+    st = problem.sites
+    s.set_sites(np.ascontiguousarray(st.pos), np.ascontiguousarray(st.q), np.ascontiguousarray(st.d),
+                np.ascontiguousarray(st.Q.reshape(-1, 9)), np.ascontiguousarray(st.alpha),
+                np.ascontiguousarray(st.group, dtype=np.int32), stream=stream)
+    return s

@@ -1,0 +1,581 @@
+// C ABI of the library (declared in include/bempol.h): context lifecycle,
+// validation, data marshalling and the self-consistent solvation driver.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "internal.h"
+
+struct bempol_ctx : public bp::Ctx {};
+
+namespace bp {
+
+static std::atomic<long long> g_launches{0};
+
+void note_launch() {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  BP_CUDA(cudaGetLastError());
+}
+
+void Ctx::time_begin(int kind, cudaStream_t s, Timed& t) {
+  t.kind = kind;
+  ++stat_launches[kind];
+  if (!stats_on) return;
+  BP_CUDA(cudaEventCreate(&t.a));
+  BP_CUDA(cudaEventCreate(&t.b));
+  BP_CUDA(cudaEventRecord(t.a, s));
+}
+
+void Ctx::time_end(cudaStream_t s, Timed& t) {
+  if (!stats_on) return;
+  BP_CUDA(cudaEventRecord(t.b, s));
+  timed.push_back(t);
+}
+
+void Ctx::collect_timers() {
+  for (auto& t : timed) {
+    float ms = 0;
+    cudaEventSynchronize(t.b);
+    cudaEventElapsedTime(&ms, t.a, t.b);
+    stat_ms[t.kind] += ms;
+    cudaEventDestroy(t.a);
+    cudaEventDestroy(t.b);
+  }
+  timed.clear();
+}
+
+Ctx::~Ctx() {
+  collect_timers();
+  if (h_pinned) cudaFreeHost(h_pinned);
+}
+
+int num_sms(int device) {
+  static int cache[64] = {0};
+  if (device < 0 || device >= 64) device = 0;
+  if (!cache[device]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v <= 0) v = 148;
+    cache[device] = v;
+  }
+  return cache[device];
+}
+
+namespace {
+
+// e^2/(4 pi eps0 A) per mole in kcal/mol from the SI-defined e, eps0 (CODATA 2018), N_A and 4184 J/kcal
+constexpr double COULOMB_KCAL = 332.0637132991921;
+constexpr double KCAL_PER_UNIT = 4.0 * M_PI * COULOMB_KCAL;
+
+void check_params(const bempol_params* p) {
+  if (!p) fail(BEMPOL_ERR_ARG, "params is NULL");
+  auto bad = [](const char* m) { fail(BEMPOL_ERR_ARG, m); };
+  if (!(p->eps_in > 0) || !(p->eps_out > 0)) bad("eps_in and eps_out must be > 0");
+  if (!(p->kappa >= 0)) bad("kappa must be >= 0");
+  if (p->gauss_k != 1 && p->gauss_k != 3 && p->gauss_k != 4) bad("gauss_k must be 1, 3 or 4");
+  if (!(p->near_factor >= 0)) bad("near_factor must be >= 0");
+  if (!(p->theta > 0 && p->theta < 1.5)) bad("theta must be in (0, 1.5)");
+  if (p->order < 1 || p->order > 10) bad("order must be in 1..10");
+  if (p->leaf < 8 || p->leaf > 4096) bad("leaf must be in 8..4096");
+  if (!(p->gmres_tol > 0)) bad("gmres_tol must be > 0");
+  if (p->gmres_restart < 1 || p->gmres_restart > 1000) bad("gmres_restart must be in 1..1000");
+  if (p->gmres_maxit < 1) bad("gmres_maxit must be >= 1");
+  if (!(p->scf_tol > 0)) bad("scf_tol must be > 0");
+  if (!(p->sor_omega > 0 && p->sor_omega <= 1.0)) bad("sor_omega must be in (0, 1]");
+  if (p->scf_maxit < 1) bad("scf_maxit must be >= 1");
+  if (p->op < 0 || p->op > 3 || p->residual_op < 0 || p->residual_op > 3) bad("op/residual_op out of range");
+  if (!(p->inner_tol > 0 && p->inner_tol < 1)) bad("inner_tol must be in (0, 1)");
+  if (p->refine_maxit < 0) bad("refine_maxit must be >= 0");
+  if (!(p->thole_a >= 0)) bad("thole_a must be >= 0");
+}
+
+bool op_fp32(int op) { return op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE; }
+bool op_tree(int op) { return op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE; }
+
+template <typename F>
+bempol_status guard(bempol_ctx* c, F&& f) {
+  if (!c) return BEMPOL_ERR_ARG;
+  try {
+    if (cudaSetDevice(c->device) != cudaSuccess) fail(BEMPOL_ERR_CUDA, "cudaSetDevice failed");
+    f();
+    c->err.clear();
+    return BEMPOL_OK;
+  } catch (const Error& e) {
+    c->err = e.msg;
+    return e.st;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return BEMPOL_ERR_ARG;
+  }
+}
+
+template <typename T>
+void to_device(DBuf<T>& dst, const T* src, size_t count, int where, cudaStream_t s) {
+  dst.alloc(std::max<size_t>(1, count));
+  if (count == 0) return;
+  BP_CUDA(cudaMemcpyAsync(dst.p, src, count * sizeof(T),
+                          where == BEMPOL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+}
+
+template <typename T>
+std::vector<T> to_host(const T* src, size_t count, int where, cudaStream_t s) {
+  std::vector<T> h(count);
+  if (count == 0) return h;
+  if (where == BEMPOL_DEVICE) {
+    BP_CUDA(cudaMemcpyAsync(h.data(), src, count * sizeof(T), cudaMemcpyDeviceToHost, s));
+    BP_CUDA(cudaStreamSynchronize(s));
+  } else {
+    std::memcpy(h.data(), src, count * sizeof(T));
+  }
+  return h;
+}
+
+void ensure_tree(Ctx& c, int op, cudaStream_t s) {
+  if (op_tree(op) && !c.tree_ready) build_tree(c, s);
+}
+
+__global__ void add_vec(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = a[i] + (b ? b[i] : 0.0);
+}
+
+__global__ void pack_sites(const double* __restrict__ pos, const double* __restrict__ alpha, int ns,
+                           double4* __restrict__ out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ns) out[i] = make_double4(pos[3 * i], pos[3 * i + 1], pos[3 * i + 2], alpha[i]);
+}
+
+struct EventTimer {
+  cudaEvent_t a, b;
+  cudaStream_t s;
+  explicit EventTimer(cudaStream_t st) : s(st) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, s);
+  }
+  double ms() {
+    float t = 0;
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    cudaEventElapsedTime(&t, a, b);
+    return t;
+  }
+  ~EventTimer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+}  // namespace
+}  // namespace bp
+
+using namespace bp;
+
+extern "C" {
+
+void bempol_default_params(bempol_params* p) {
+  if (!p) return;
+  p->eps_in = 1.0;
+  p->eps_out = 80.0;
+  p->kappa = 0.125;
+  p->gauss_k = 4;
+  p->near_factor = 2.0;
+  p->theta = 0.5;
+  p->order = 5;
+  p->leaf = 256;
+  p->gmres_tol = 1e-8;
+  p->gmres_restart = 100;
+  p->gmres_maxit = 500;
+  p->scf_tol = 1e-8;
+  p->sor_omega = 0.7;
+  p->scf_maxit = 200;
+  p->op = BEMPOL_OP_FP64_DIRECT;
+  p->residual_op = BEMPOL_OP_FP64_DIRECT;
+  p->inner_tol = 1e-3;
+  p->refine_maxit = 20;
+  p->thole_a = 0.39;
+}
+
+bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out) {
+  if (!out) return BEMPOL_ERR_ARG;
+  *out = nullptr;
+  bempol_ctx* c = nullptr;
+  try {
+    check_params(p);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+      (void)cudaGetLastError();
+      return BEMPOL_ERR_CUDA;
+    }
+    BP_CUDA(cudaSetDevice(device));
+    c = new bempol_ctx();
+    c->par = *p;
+    c->device = device;
+    init_gauss_legendre();
+    c->scal.alloc(16);
+    BP_CUDA(cudaMallocHost(&c->h_pinned, 16 * sizeof(double)));
+  } catch (const Error& e) {
+    delete c;
+    return e.st;
+  }
+  *out = c;
+  return BEMPOL_OK;
+}
+
+bempol_status bempol_set_params(bempol_ctx* c, const bempol_params* p) {
+  return guard(c, [&] {
+    check_params(p);
+    bool geo = p->gauss_k != c->par.gauss_k || p->near_factor != c->par.near_factor || p->kappa != c->par.kappa;
+    bool tree = p->leaf != c->par.leaf || geo;
+    if (geo && c->have_mesh) fail(BEMPOL_ERR_STATE, "gauss_k, near_factor and kappa are fixed once a mesh is set");
+    c->par = *p;
+    if (tree) c->tree_ready = false;
+  });
+}
+
+void bempol_destroy(bempol_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  delete c;
+}
+
+const char* bempol_last_error(const bempol_ctx* c) { return c ? c->err.c_str() : "NULL context"; }
+
+bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt, const int32_t* tris,
+                              int where, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nv < 4 || nt < 4 || !verts || !tris) fail(BEMPOL_ERR_ARG, "need nv >= 4, nt >= 4 and non-NULL arrays");
+    if (nt > (int64_t)1 << 28) fail(BEMPOL_ERR_ARG, "too many triangles");
+    if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
+    c->have_mesh = false;
+    c->have_sites = false;
+    c->tree_ready = false;
+    c->n = (int)nt;
+    c->nv = (int)nv;
+    c->K = c->par.gauss_k;
+    std::vector<int32_t> ht = to_host(tris, 3 * (size_t)nt, where, s);
+    DBuf<double> dv;
+    to_device(dv, verts, 3 * (size_t)nv, where, s);
+    build_geometry(*c, dv.p, ht.data(), s);
+    build_near(*c, s);
+    build_block_centers(*c, s);
+    size_t len = 2 * (size_t)c->n;
+    c->vec_a.alloc(len);
+    c->vec_b.alloc(len);
+    c->vec_c.alloc(len);
+    c->vec_d.alloc(len);
+    c->have_mesh = true;
+  });
+}
+
+bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, const double* q, const double* d,
+                               const double* Q, const double* alpha, const int32_t* group, int where,
+                               void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "set_mesh must come before set_sites");
+    if (ns < 1 || ns > (1 << 24) || !pos || !q || !d || !Q || !alpha) fail(BEMPOL_ERR_ARG, "bad site arrays");
+    if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
+    c->have_sites = false;
+    // host-side checks of the moments (small arrays)
+    std::vector<double> hQ = to_host(Q, 9 * (size_t)ns, where, s);
+    std::vector<double> ha = to_host(alpha, (size_t)ns, where, s);
+    std::vector<double> Q6(6 * (size_t)ns);
+    for (int64_t l = 0; l < ns; ++l) {
+      const double* m = hQ.data() + 9 * l;
+      double mx = 0;
+      for (int k = 0; k < 9; ++k) mx = std::max(mx, std::fabs(m[k]));
+      if (!std::isfinite(mx)) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " has a non-finite quadrupole");
+      double asym = std::max(std::fabs(m[1] - m[3]), std::max(std::fabs(m[2] - m[6]), std::fabs(m[5] - m[7])));
+      double tr = m[0] + m[4] + m[8];
+      if (asym > 1e-9 * mx || std::fabs(tr) > 1e-9 * mx)
+        fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": Q must be symmetric and traceless");
+      double t3 = tr / 3.0;
+      double* o = Q6.data() + 6 * l;
+      o[0] = m[0] - t3;
+      o[1] = m[1];
+      o[2] = m[2];
+      o[3] = m[4] - t3;
+      o[4] = m[5];
+      o[5] = m[8] - t3;
+      if (!(ha[l] >= 0.0) || !std::isfinite(ha[l]))
+        fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": alpha must be finite and >= 0");
+    }
+    c->ns = (int)ns;
+    DBuf<double> dpos, dal;
+    to_device(dpos, pos, 3 * (size_t)ns, where, s);
+    to_device(dal, alpha, (size_t)ns, where, s);
+    c->site_pos.alloc(ns);
+    launch(pack_sites, cdiv(ns, 256), 256, 0, s, dpos.p, dal.p, (int)ns, c->site_pos.p);
+    BP_CHECK_LAUNCH();
+    to_device(c->site_q, q, (size_t)ns, where, s);
+    to_device(c->site_d, d, 3 * (size_t)ns, where, s);
+    to_device(c->site_Q, Q6.data(), 6 * (size_t)ns, BEMPOL_HOST, s);
+    std::vector<int32_t> g(ns);
+    if (group) {
+      g = to_host(group, (size_t)ns, where, s);
+    } else {
+      for (int64_t l = 0; l < ns; ++l) g[l] = (int32_t)l;
+    }
+    to_device(c->site_group, g.data(), (size_t)ns, BEMPOL_HOST, s);
+    site_validation(*c, s);
+    BP_CUDA(cudaStreamSynchronize(s));
+    c->have_sites = true;
+  });
+}
+
+bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "no mesh");
+    if (!x || !y || x == y) fail(BEMPOL_ERR_ARG, "x and y must be distinct device arrays");
+    if (op < 0 || op > 3) fail(BEMPOL_ERR_ARG, "bad op");
+    ensure_tree(*c, op, s);
+    permute_to_internal(*c, x, c->vec_a.p, 2, s);
+    matvec_internal(*c, c->vec_a.p, c->vec_b.p, op, s);
+    permute_to_caller(*c, c->vec_b.p, y, 2, s);
+  });
+}
+
+bempol_status bempol_rhs(bempol_ctx* c, const double* p, double* b, int op, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
+    if (!b) fail(BEMPOL_ERR_ARG, "b is NULL");
+    rhs_internal(*c, p, c->vec_a.p, op_fp32(op), s);
+    permute_to_caller(*c, c->vec_a.p, b, 1, s);
+  });
+}
+
+bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, int op, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
+    if (!x || !out) fail(BEMPOL_ERR_ARG, "NULL array");
+    permute_to_internal(*c, x, c->vec_a.p, 2, s);
+    site_reaction_internal(*c, c->vec_a.p, out, op_fp32(op), true, s);
+  });
+}
+
+bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, double* out, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
+    if (!out || (mode != 0 && mode != 1)) fail(BEMPOL_ERR_ARG, "bad arguments");
+    DBuf<double> zero;
+    const double* m = mu;
+    if (!m) {
+      zero.alloc(3 * (size_t)c->ns);
+      zero.zero(s);
+      m = zero.p;
+    }
+    multipole_internal(*c, m, mode, out, s);
+    if (!mu) BP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+bempol_status bempol_sizes(const bempol_ctx* cc, int64_t* n_panels, int32_t* gauss_k, int64_t* n_sites,
+                           int64_t* n_near, int64_t* n_cells, int64_t* n_leaves) {
+  if (!cc) return BEMPOL_ERR_ARG;
+  if (n_panels) *n_panels = cc->have_mesh ? cc->n : 0;
+  if (gauss_k) *gauss_k = cc->K;
+  if (n_sites) *n_sites = cc->have_sites ? cc->ns : 0;
+  if (n_near) *n_near = cc->have_mesh ? cc->nnz : 0;
+  if (n_cells) *n_cells = cc->tree_ready ? cc->tree.ncell : 0;
+  if (n_leaves) *n_leaves = cc->tree_ready ? cc->tree.nleaf : 0;
+  return BEMPOL_OK;
+}
+
+bempol_status bempol_stats_enable(bempol_ctx* c, int enable) {
+  return guard(c, [&] { c->stats_on = enable != 0; });
+}
+
+bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
+  return guard(c, [&] {
+    if (!out) fail(BEMPOL_ERR_ARG, "out is NULL");
+    BP_CUDA(cudaDeviceSynchronize());
+    c->collect_timers();
+    out->kernel_launches = g_launches.load() - c->launches_at_reset;
+    out->pair_launches = c->stat_launches[0];
+    out->pair_ms = c->stat_ms[0];
+    out->far_launches = c->stat_launches[1];
+    out->far_ms = c->stat_ms[1];
+    out->pair_interactions = c->stat_pairs;
+    out->far_evaluations = c->stat_far;
+    if (reset) {
+      c->launches_at_reset = g_launches.load();
+      c->stat_launches[0] = c->stat_launches[1] = 0;
+      c->stat_ms[0] = c->stat_ms[1] = 0;
+      c->stat_pairs = c->stat_far = 0;
+    }
+  });
+}
+
+bempol_status bempol_get_geometry(bempol_ctx* c, double* centroid, double* normal, double* area,
+                                  int64_t* near_ptr, int32_t* near_col, double* near_corr) {
+  return guard(c, [&] {
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "no mesh");
+    const int n = c->n;
+    cudaStream_t s = 0;
+    std::vector<double4> t(n), nr(n);
+    std::vector<int> perm(n), ptr(n + 1), col(c->nnz);
+    std::vector<double4> corr(c->nnz);
+    BP_CUDA(cudaMemcpy(t.data(), c->tgt64.p, sizeof(double4) * n, cudaMemcpyDeviceToHost));
+    BP_CUDA(cudaMemcpy(nr.data(), c->nrm64.p, sizeof(double4) * n, cudaMemcpyDeviceToHost));
+    BP_CUDA(cudaMemcpy(perm.data(), c->perm.p, sizeof(int) * n, cudaMemcpyDeviceToHost));
+    BP_CUDA(cudaMemcpy(ptr.data(), c->near_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost));
+    if (c->nnz) {
+      BP_CUDA(cudaMemcpy(col.data(), c->near_col.p, sizeof(int) * c->nnz, cudaMemcpyDeviceToHost));
+      BP_CUDA(cudaMemcpy(corr.data(), c->near_corr.p, sizeof(double4) * c->nnz, cudaMemcpyDeviceToHost));
+    }
+    (void)s;
+    for (int i = 0; i < n; ++i) {
+      int p = perm[i];
+      if (centroid) {
+        centroid[3 * p] = t[i].x;
+        centroid[3 * p + 1] = t[i].y;
+        centroid[3 * p + 2] = t[i].z;
+      }
+      if (area) area[p] = t[i].w;
+      if (normal) {
+        normal[3 * p] = nr[i].x;
+        normal[3 * p + 1] = nr[i].y;
+        normal[3 * p + 2] = nr[i].z;
+      }
+    }
+    if (near_ptr || near_col || near_corr) {
+      // rows in caller order, columns as caller indices ascending
+      std::vector<int64_t> cptr(n + 1, 0);
+      for (int i = 0; i < n; ++i) cptr[perm[i] + 1] = ptr[i + 1] - ptr[i];
+      for (int i = 0; i < n; ++i) cptr[i + 1] += cptr[i];
+      if (near_ptr)
+        for (int i = 0; i <= n; ++i) near_ptr[i] = cptr[i];
+      std::vector<std::pair<int, int>> row;
+      for (int i = 0; i < n; ++i) {
+        int p = perm[i];
+        row.clear();
+        for (int e = ptr[i]; e < ptr[i + 1]; ++e) row.push_back({perm[col[e]], e});
+        std::sort(row.begin(), row.end());
+        int64_t o = cptr[p];
+        for (auto& r : row) {
+          if (near_col) near_col[o] = r.first;
+          if (near_corr) {
+            double4 v = corr[r.second];
+            near_corr[4 * o] = v.x;
+            near_corr[4 * o + 1] = v.y;
+            near_corr[4 * o + 2] = v.z;
+            near_corr[4 * o + 3] = v.w;
+          }
+          ++o;
+        }
+      }
+    }
+  });
+}
+
+bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_sites) fail(BEMPOL_ERR_STATE, "set_mesh and set_sites must come first");
+    if (!out) fail(BEMPOL_ERR_ARG, "out is NULL");
+    auto wall0 = std::chrono::steady_clock::now();
+    EventTimer tt(s);
+    const bempol_params& P = c->par;
+    const int n = c->n, ns = c->ns, len = 2 * n;
+    ensure_tree(*c, P.op, s);
+    ensure_tree(*c, P.residual_op, s);
+    const bool f32 = op_fp32(P.residual_op);
+    DBuf<double> mu, mu_v, emult, react, mult10, p, b, x;
+    mu.alloc(3 * ns);
+    mu_v.alloc(3 * ns);
+    emult.alloc(3 * ns);
+    react.alloc(10 * ns);
+    mult10.alloc(10 * ns);
+    p.alloc(3 * ns);
+    b.alloc(len);
+    x.alloc(len);
+    mu.zero(s);
+    mu_v.zero(s);
+    x.zero(s);
+    b.zero(s);
+    double t_setup = tt.ms();
+    EventTimer ts(s);
+    int gm_iters = 0, matvecs = 0, solves = 0;
+    double last_res = 0;
+    bool ok = true;
+    // vacuum state: multipoles only
+    int it_v = 0;
+    for (it_v = 1; it_v <= P.scf_maxit; ++it_v) {
+      multipole_internal(*c, mu_v.p, 0, emult.p, s);
+      double rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, s);
+      if (rms < P.scf_tol) break;
+    }
+    if (it_v > P.scf_maxit) {
+      ok = false;
+      it_v = P.scf_maxit;
+    }
+    auto bem = [&]() {
+      launch(add_vec, cdiv(3 * ns, 256), 256, 0, s, c->site_d.p, mu.p, p.p, 3 * ns);
+      rhs_internal(*c, p.p, b.p, f32, s);
+      GmresOut g = solve_bem(*c, b.p, x.p, s);
+      gm_iters += g.iters;
+      matvecs += g.matvecs;
+      ++solves;
+      last_res = g.rel_res;
+      if (!g.converged) ok = false;
+    };
+    int it = 0;
+    for (it = 1; it <= P.scf_maxit; ++it) {
+      bem();
+      site_reaction_internal(*c, x.p, react.p, f32, false, s);
+      multipole_internal(*c, mu.p, 0, emult.p, s);
+      double rms = sor_update(*c, mu.p, react.p, emult.p, false, s);
+      if (rms < P.scf_tol) break;
+    }
+    if (it > P.scf_maxit) {
+      ok = false;
+      it = P.scf_maxit;
+    }
+    bem();
+    site_reaction_internal(*c, x.p, react.p, f32, true, s);
+    multipole_internal(*c, mu.p, 1, mult10.p, s);
+    double G_diss = energy_internal(*c, react.p, mult10.p, s);
+    multipole_internal(*c, mu_v.p, 1, mult10.p, s);
+    double G_vac = energy_internal(*c, nullptr, mult10.p, s);
+    double t_scf = ts.ms();
+    out->G_diss = G_diss;
+    out->G_vac = G_vac;
+    out->dG_solv_kcal = (G_diss - G_vac) * KCAL_PER_UNIT;
+    out->scf_iters_diss = it;
+    out->scf_iters_vac = it_v;
+    out->gmres_iters_total = gm_iters;
+    out->matvecs_total = matvecs;
+    out->n_solves = solves;
+    out->last_rel_residual = last_res;
+    out->t_setup_ms = t_setup;
+    out->t_scf_ms = t_scf;
+    // optional arrays
+    auto put = [&](double* dst, const double* src_dev, size_t count) {
+      if (!dst) return;
+      BP_CUDA(cudaMemcpyAsync(dst, src_dev, count * sizeof(double),
+                              out->where == BEMPOL_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    };
+    if (out->phi || out->dphidn) {
+      permute_to_caller(*c, x.p, c->vec_d.p, 2, s);
+      put(out->phi, c->vec_d.p, n);
+      put(out->dphidn, c->vec_d.p + n, n);
+    }
+    put(out->site_reaction, react.p, 10 * (size_t)ns);
+    put(out->mu_diss, mu.p, 3 * (size_t)ns);
+    put(out->mu_vac, mu_v.p, 3 * (size_t)ns);
+    BP_CUDA(cudaStreamSynchronize(s));
+    out->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    if (!ok) fail(BEMPOL_ERR_NOT_CONVERGED, "GMRES or SCF reached its iteration limit");
+  });
+}
+
+}  // extern "C"

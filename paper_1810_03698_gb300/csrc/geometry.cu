@@ -1,0 +1,228 @@
+// Panel geometry, Morton ordering and Gauss nodes (Sec. "The boundary element method":
+// flat triangles, piecewise-constant unknowns collocated at centroids, 1/3/4-node
+// Gauss rules for far-away panels).
+//
+// This file is compiled with -fmad=false: centroids, normals and areas are formed
+// with separately rounded products and sums in a fixed order, so they are
+// reproducible bit for bit by any FP64 implementation that follows the same order
+// (centroid = ((v0 + v1) + v2) / 3, cross = (v1 - v0) x (v2 - v0), area = |cross| / 2).
+#include <algorithm>
+#include <cstring>
+#include <unordered_map>
+
+#include "internal.h"
+
+namespace bp {
+
+namespace {
+
+__global__ void panel_geom_kernel(const double* __restrict__ verts, const int* __restrict__ tris, int n,
+                                  double4* __restrict__ cen_area, double4* __restrict__ nrm,
+                                  double* __restrict__ vert9) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int a = tris[3 * t], b = tris[3 * t + 1], c = tris[3 * t + 2];
+  double ax = verts[3 * a], ay = verts[3 * a + 1], az = verts[3 * a + 2];
+  double bx = verts[3 * b], by = verts[3 * b + 1], bz = verts[3 * b + 2];
+  double cx = verts[3 * c], cy = verts[3 * c + 1], cz = verts[3 * c + 2];
+  double e1x = bx - ax, e1y = by - ay, e1z = bz - az;
+  double e2x = cx - ax, e2y = cy - ay, e2z = cz - az;
+  double crx = e1y * e2z - e1z * e2y;
+  double cry = e1z * e2x - e1x * e2z;
+  double crz = e1x * e2y - e1y * e2x;
+  double nn = sqrt(crx * crx + cry * cry + crz * crz);
+  double area = 0.5 * nn;
+  cen_area[t] = make_double4((ax + bx + cx) / 3.0, (ay + by + cy) / 3.0, (az + bz + cz) / 3.0, area);
+  nrm[t] = make_double4(crx / nn, cry / nn, crz / nn, 0.0);
+  double* v = vert9 + 9 * (size_t)t;
+  v[0] = ax; v[1] = ay; v[2] = az;
+  v[3] = bx; v[4] = by; v[5] = bz;
+  v[6] = cx; v[7] = cy; v[8] = cz;
+}
+
+__global__ void morton_kernel(const double4* __restrict__ cen, int n, int npad, double lox, double loy,
+                              double loz, double inv, unsigned long long* __restrict__ keys) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= npad) return;
+  if (t >= n) {
+    keys[t] = ~0ull;
+    return;
+  }
+  double4 c = cen[t];
+  auto q = [&](double v, double lo) {
+    double s = (v - lo) * inv;
+    int iv = (int)(s * 1024.0);
+    return (unsigned)min(1023, max(0, iv));
+  };
+  auto spread = [](unsigned x) {
+    x &= 0x3ffu;
+    x = (x | (x << 16)) & 0x030000FFu;
+    x = (x | (x << 8)) & 0x0300F00Fu;
+    x = (x | (x << 4)) & 0x030C30C3u;
+    x = (x | (x << 2)) & 0x09249249u;
+    return x;
+  };
+  unsigned m = (spread(q(c.x, lox)) << 2) | (spread(q(c.y, loy)) << 1) | spread(q(c.z, loz));
+  keys[t] = ((unsigned long long)m << 32) | (unsigned)t;
+}
+
+// one compare-exchange stage of a bitonic sort (ascending)
+__global__ void bitonic_step(unsigned long long* __restrict__ keys, int npad, int j, int k) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npad) return;
+  int l = i ^ j;
+  if (l > i) {
+    unsigned long long a = keys[i], b = keys[l];
+    bool up = (i & k) == 0;
+    if ((a > b) == up) {
+      keys[i] = b;
+      keys[l] = a;
+    }
+  }
+}
+
+__global__ void perm_from_keys(const unsigned long long* __restrict__ keys, int n, int* __restrict__ perm,
+                               int* __restrict__ iperm) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int p = (int)(keys[i] & 0xffffffffu);
+  perm[i] = p;
+  iperm[p] = i;
+}
+
+__global__ void gather_geometry(const int* __restrict__ perm, int n, int K, const double4* __restrict__ cen_c,
+                                const double4* __restrict__ nrm_c, const double* __restrict__ v9_c,
+                                double4* __restrict__ tgt64, float4* __restrict__ tgt32,
+                                double4* __restrict__ nrm64, double* __restrict__ v9,
+                                double4* __restrict__ src64, float4* __restrict__ src32) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int p = perm[i];
+  double4 c = cen_c[p];
+  tgt64[i] = c;
+  tgt32[i] = make_float4((float)c.x, (float)c.y, (float)c.z, 0.f);
+  nrm64[i] = nrm_c[p];
+  const double* a = v9_c + 9 * (size_t)p;
+  double* o = v9 + 9 * (size_t)i;
+  for (int k = 0; k < 9; ++k) o[k] = a[k];
+  // barycentric nodes and weights of the K-node rule
+  double lam[4][3], w[4];
+  if (K == 1) {
+    lam[0][0] = lam[0][1] = lam[0][2] = 1.0 / 3.0;
+    w[0] = 1.0;
+  } else if (K == 3) {
+    const double hi = 2.0 / 3.0, lo = 1.0 / 6.0;
+    for (int g = 0; g < 3; ++g) {
+      for (int d = 0; d < 3; ++d) lam[g][d] = (g == d) ? hi : lo;
+      w[g] = 1.0 / 3.0;
+    }
+  } else {
+    lam[0][0] = lam[0][1] = lam[0][2] = 1.0 / 3.0;
+    w[0] = -27.0 / 48.0;
+    for (int g = 1; g < 4; ++g) {
+      for (int d = 0; d < 3; ++d) lam[g][d] = (g - 1 == d) ? 0.6 : 0.2;
+      w[g] = 25.0 / 48.0;
+    }
+  }
+  for (int g = 0; g < K; ++g) {
+    double x = lam[g][0] * a[0] + lam[g][1] * a[3] + lam[g][2] * a[6];
+    double y = lam[g][0] * a[1] + lam[g][1] * a[4] + lam[g][2] * a[7];
+    double z = lam[g][0] * a[2] + lam[g][1] * a[5] + lam[g][2] * a[8];
+    if (K != 3 && g == 0) {
+      // the centroid node is the collocation point itself (bit for bit), so the
+      // self pair has r = 0 and drops out instead of leaving a rounding-sized r
+      x = c.x;
+      y = c.y;
+      z = c.z;
+    }
+    double W = w[g] * c.w;
+    src64[(size_t)K * i + g] = make_double4(x, y, z, W);
+    src32[(size_t)K * i + g] = make_float4((float)x, (float)y, (float)z, (float)W);
+  }
+}
+
+void validate_closed(const int* tris, int n, int nv) {
+  // every directed edge must appear once and its reverse once (closed, consistently oriented)
+  std::vector<unsigned long long> e;
+  e.reserve(3 * (size_t)n);
+  for (int t = 0; t < n; ++t) {
+    for (int k = 0; k < 3; ++k) {
+      int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+      if (a < 0 || a >= nv || b < 0 || b >= nv)
+        fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has a vertex index out of range");
+      if (a == b) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " repeats a vertex");
+      e.push_back(((unsigned long long)(unsigned)a << 32) | (unsigned)b);
+    }
+  }
+  std::sort(e.begin(), e.end());
+  for (size_t i = 1; i < e.size(); ++i)
+    if (e[i] == e[i - 1]) fail(BEMPOL_ERR_MESH, "a directed edge is used twice (inconsistent orientation or non-manifold mesh)");
+  for (auto k : e) {
+    unsigned long long r = ((k & 0xffffffffull) << 32) | (k >> 32);
+    if (!std::binary_search(e.begin(), e.end(), r))
+      fail(BEMPOL_ERR_MESH, "the mesh is not closed: an edge has no opposite neighbour");
+  }
+}
+
+}  // namespace
+
+void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, cudaStream_t s) {
+  const int n = c.n;
+  validate_closed(h_tris_for_check, n, c.nv);
+  DBuf<int> d_tris;
+  d_tris.alloc(3 * (size_t)n);
+  BP_CUDA(cudaMemcpyAsync(d_tris.p, h_tris_for_check, 3 * sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s));
+  DBuf<double4> cen_c, nrm_c;
+  DBuf<double> v9_c;
+  cen_c.alloc(n);
+  nrm_c.alloc(n);
+  v9_c.alloc(9 * (size_t)n);
+  launch(panel_geom_kernel, cdiv(n, 256), 256, 0, s, d_verts, d_tris.p, n, cen_c.p, nrm_c.p, v9_c.p);
+  BP_CHECK_LAUNCH();
+  // areas and the centroid bounding box on the host (validation, Morton normalisation)
+  std::vector<double4> h(n);
+  BP_CUDA(cudaMemcpyAsync(h.data(), cen_c.p, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int t = 0; t < n; ++t) {
+    if (!(h[t].w > 0.0)) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has zero or invalid area");
+    double v[3] = {h[t].x, h[t].y, h[t].z};
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], v[d]);
+      hi[d] = std::max(hi[d], v[d]);
+    }
+  }
+  double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
+  if (!(ext > 0.0)) ext = 1.0;
+  for (int d = 0; d < 3; ++d) {
+    c.bbox_lo[d] = lo[d];
+    c.bbox_hi[d] = hi[d];
+  }
+  int npad = 1;
+  while (npad < n) npad <<= 1;
+  DBuf<unsigned long long> keys;
+  keys.alloc(npad);
+  launch(morton_kernel, cdiv(npad, 256), 256, 0, s, cen_c.p, n, npad, lo[0], lo[1], lo[2], 1.0 / ext, keys.p);
+  BP_CHECK_LAUNCH();
+  for (int k = 2; k <= npad; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) launch(bitonic_step, cdiv(npad, 256), 256, 0, s, keys.p, npad, j, k);
+  BP_CHECK_LAUNCH();
+  c.perm.alloc(n);
+  c.iperm.alloc(n);
+  launch(perm_from_keys, cdiv(n, 256), 256, 0, s, keys.p, n, c.perm.p, c.iperm.p);
+  BP_CHECK_LAUNCH();
+  c.tgt64.alloc(n);
+  c.tgt32.alloc(n);
+  c.nrm64.alloc(n);
+  c.vert9.alloc(9 * (size_t)n);
+  c.src64.alloc((size_t)c.K * n);
+  c.src32.alloc((size_t)c.K * n);
+  c.str64.alloc((size_t)c.K * n);
+  c.str32.alloc((size_t)c.K * n);
+  launch(gather_geometry, cdiv(n, 128), 128, 0, s, c.perm.p, n, c.K, cen_c.p, nrm_c.p, v9_c.p, c.tgt64.p,
+                                                c.tgt32.p, c.nrm64.p, c.vert9.p, c.src64.p, c.src32.p);
+  BP_CHECK_LAUNCH();
+  BP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace bp

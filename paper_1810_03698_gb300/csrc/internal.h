@@ -1,0 +1,196 @@
+// Internal declarations of the bempol library (not part of the ABI).
+//
+// Internal order: panels are stored in Morton order of their centroids
+// (perm[i] = caller index of internal panel i).  Gauss node g of internal
+// panel j is source K*j + g.  Every device array below is in internal order.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bempol.h"
+
+namespace bp {
+
+// ---------------------------------------------------------------- errors
+struct Error {
+  bempol_status st;
+  std::string msg;
+};
+
+#define BP_CUDA(call)                                                                     \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      throw ::bp::Error{BEMPOL_ERR_CUDA, std::string(#call " failed: ") + cudaGetErrorString(e_)}; \
+  } while (0)
+
+#define BP_CHECK_LAUNCH() BP_CUDA(cudaGetLastError())
+
+inline void fail(bempol_status st, const std::string& m) { throw Error{st, m}; }
+
+// Every kernel of the library is launched through launch(): it counts launches
+// (reported by bempol_stats_read) and checks the launch status.
+void note_launch();
+template <typename... KArgs, typename... Args>
+inline void launch(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                   Args&&... args) {
+  if (grid.x == 0 || grid.y == 0 || grid.z == 0) return;
+  kernel<<<grid, block, smem, s>>>(static_cast<KArgs>(args)...);
+  note_launch();
+}
+
+// ---------------------------------------------------------------- device buffer
+template <typename T>
+struct DBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count == n && p) return;
+    release();
+    if (count == 0) return;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      (void)cudaGetLastError();
+      fail(e == cudaErrorMemoryAllocation ? BEMPOL_ERR_OOM : BEMPOL_ERR_CUDA,
+           std::string("cudaMalloc of ") + std::to_string(count * sizeof(T)) + " bytes failed: " +
+               cudaGetErrorString(e));
+    }
+    n = count;
+  }
+  void zero(cudaStream_t s) {
+    if (p) BP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), s));
+  }
+};
+
+// ---------------------------------------------------------------- tree
+struct Tree {
+  int ncell = 0, nleaf = 0, depth = 0;
+  DBuf<int> cell_begin, cell_end;      // panel range [begin, end) of each cell
+  DBuf<int> cell_child;                // first child index (-1 leaf), children contiguous
+  DBuf<int> cell_nchild;
+  DBuf<double4> cell_center;           // x, y, z, radius (covers every Gauss node in the cell)
+  DBuf<int> leaves;                    // cell indices of leaves
+  std::vector<int> h_level_begin;      // cells of level l: [h_level_begin[l], h_level_begin[l+1])
+};
+
+// ---------------------------------------------------------------- context
+struct Ctx {
+  bempol_params par;
+  int device = 0;
+  std::string err;
+
+  // geometry
+  int n = 0;                 // panels
+  int K = 0;                 // Gauss nodes per panel
+  int nv = 0;
+  bool have_mesh = false;
+  DBuf<int> perm, iperm;     // internal -> caller, caller -> internal
+  DBuf<double> vert9;        // [n][9] triangle vertices (internal order)
+  DBuf<double4> tgt64;       // centroid x,y,z, area
+  DBuf<float4> tgt32;        // centroid x,y,z, 0
+  DBuf<double4> nrm64;       // unit normal, 0
+  DBuf<double4> blk_center;  // FP64 centre of each block of 128 consecutive targets
+  DBuf<double4> src64;       // Gauss node x,y,z, weight w_g*A_j   [n*K]
+  DBuf<float4> src32;
+  DBuf<double4> str64;       // per-matvec strengths m, d (x,y,z)  [n*K]
+  DBuf<float4> str32;
+  DBuf<int> near_ptr;        // [n+1]
+  DBuf<int> near_col;        // [nnz]
+  DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections
+  int64_t nnz = 0;
+  double bbox_lo[3], bbox_hi[3];
+  Tree tree;
+  bool tree_ready = false;
+
+  // sites
+  int ns = 0;
+  bool have_sites = false;
+  DBuf<double4> site_pos;    // x, y, z, alpha
+  DBuf<double> site_q;       // [ns]
+  DBuf<double> site_d;       // [ns*3]
+  DBuf<double> site_Q;       // [ns*6] xx xy xz yy yz zz
+  DBuf<int> site_group;      // [ns]
+
+  // matvec / solver workspaces
+  DBuf<double> part;         // P2P partial sums [S][4][n]
+  int part_splits = 0;
+  DBuf<double> site_part;    // site partial sums
+  DBuf<double> gm_V, gm_H, gm_small, gm_dots;
+  DBuf<double> vec_a, vec_b, vec_c, vec_d;   // [2n] scratch vectors
+  DBuf<double> scal;         // device scalars
+  double* h_pinned = nullptr;  // pinned host scalars
+  int gm_m = 0;
+
+  // optional CUDA-event timing of the pair (direct / near-field) and far-field kernels
+  bool stats_on = false;
+  struct Timed {
+    cudaEvent_t a, b;
+    int kind;  // 0 pair kernel, 1 far-field kernel
+  };
+  std::vector<Timed> timed;
+  double stat_ms[2] = {0, 0};
+  long long stat_launches[2] = {0, 0};
+  long long stat_pairs = 0, stat_far = 0;
+  long long launches_at_reset = 0;
+  void time_begin(int kind, cudaStream_t s, Timed& t);
+  void time_end(cudaStream_t s, Timed& t);
+  void collect_timers();
+
+  Ctx() = default;
+  ~Ctx();
+};
+
+// ---------------------------------------------------------------- launch helpers
+inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
+int num_sms(int device);
+
+// geometry.cu
+void build_geometry(Ctx& c, const double* h_verts, const int* h_tris, cudaStream_t s);
+// near.cu
+void build_near(Ctx& c, cudaStream_t s);
+void init_gauss_legendre();
+// p2p.cu
+void build_block_centers(Ctx& c, cudaStream_t s);
+void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s);
+void p2p_direct(Ctx& c, bool fp32, cudaStream_t s);
+void combine(Ctx& c, const double* x, double* y, cudaStream_t s);
+void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s);
+// tree.cu
+void build_tree(Ctx& c, cudaStream_t s);
+void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
+// sites.cu
+void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s);
+void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s);
+void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s);
+double energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s);
+double sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
+                  cudaStream_t s);
+void site_validation(Ctx& c, cudaStream_t s);
+// gmres.cu
+struct GmresOut {
+  int iters = 0;
+  int matvecs = 0;
+  double rel_res = 0;
+  bool converged = false;
+};
+GmresOut solve_bem(Ctx& c, const double* b, double* x, cudaStream_t s);
+// vector helpers (gmres.cu)
+double dot_dev(Ctx& c, const double* a, const double* b, int len, cudaStream_t s);
+void permute_to_internal(const Ctx& c, const double* src, double* dst, int blocks_of_n, cudaStream_t s);
+void permute_to_caller(const Ctx& c, const double* src, double* dst, int blocks_of_n, cudaStream_t s);
+
+}  // namespace bp

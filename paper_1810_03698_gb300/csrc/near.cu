@@ -1,0 +1,253 @@
+// Near-singular and singular panel integrals (Sec. "The boundary element method").
+//
+// Near pairs: panel j is near collocation point i when |x_i - c_j|^2 < nf^2 * A_i
+// (nf = near_factor, A_i the area of the collocation point's own panel).  The
+// decision is taken in FP64 with explicitly rounded operations in the order
+// ((dx*dx + dy*dy) + dz*dz) < (nf*nf)*A_i; an FP32 pass with a safety margin only
+// skips pairs that are certainly far.
+//
+// For every near pair the FP64 correction (accurate integral - K-node sum) of the
+// four kernels V_L, K_L, V_Y, K_Y is stored, so that a matvec over all Gauss
+// nodes plus this sparse correction equals the discrete operator.
+//
+// Accurate integrals (semi-analytical; the paper cites Hess-Smith and Zhu et al.
+// without formulas, this is the reading used):
+//   * foot point p of x on the panel plane, signed height h = n.(x - v0)
+//     (h = 0 exactly when x is the centroid of the same panel);
+//   * three signed sub-triangles (p, v_a, v_b), sign = orientation along n;
+//   * radial integrals in closed form with s = sqrt(rho^2 + h^2):
+//       G_L: s - |h|;  G_Y: (e^{-k|h|} - e^{-k s})/k;
+//       dG_L/dn_y: sgn(h)(1 - |h|/s);  dG_Y/dn_y: sgn(h)(e^{-k|h|} - |h| e^{-k s}/s)
+//     (all over 4 pi), written without cancellation (s - |h| = rho^2/(s + |h|),
+//     expm1 for the exponential differences);
+//   * angular integral along each edge in the variable u with t = d sinh(u)
+//     (d = distance from p to the edge line, t = position along it), so
+//     dpsi = du/cosh(u) and rho_max = d cosh(u); every singularity of the
+//     integrand then lies at |Im u| >= pi/2, and composite 10-node
+//     Gauss-Legendre on pieces of length <= 1 converges to ~1e-16.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace bp {
+
+namespace {
+
+constexpr int GL_N = 10;
+__constant__ double c_gl_x[GL_N];
+__constant__ double c_gl_w[GL_N];
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n (host).
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+__device__ __forceinline__ double dsq3(double dx, double dy, double dz) {
+  return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+}
+
+// pass 1/2: count, then fill, the near columns of every target (ascending j)
+template <bool FILL>
+__global__ void near_list_kernel(const double4* __restrict__ tgt64, const float4* __restrict__ tgt32, int n,
+                                 double nf2, float abs_margin, const int* __restrict__ ptr,
+                                 int* __restrict__ out) {
+  __shared__ float4 tile[256];
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double4 xi = i < n ? tgt64[i] : make_double4(0, 0, 0, 0);
+  float4 xf = i < n ? tgt32[i] : make_float4(0, 0, 0, 0);
+  double thr = __dmul_rn(nf2, xi.w);
+  float rf = sqrtf((float)thr) + abs_margin;
+  float thrf = rf * rf;
+  int cnt = 0;
+  int base = (FILL && i < n) ? ptr[i] : 0;
+  for (int t0 = 0; t0 < n; t0 += 256) {
+    int j = t0 + threadIdx.x;
+    tile[threadIdx.x] = j < n ? tgt32[j] : make_float4(3e30f, 3e30f, 3e30f, 0.f);
+    __syncthreads();
+    int lim = min(256, n - t0);
+    for (int k = 0; k < lim; ++k) {
+      float4 c = tile[k];
+      float dx = xf.x - c.x, dy = xf.y - c.y, dz = xf.z - c.z;
+      float d2 = dx * dx + dy * dy + dz * dz;
+      if (d2 <= thrf && i < n) {
+        double4 cj = tgt64[t0 + k];
+        double e2 = dsq3(__dsub_rn(xi.x, cj.x), __dsub_rn(xi.y, cj.y), __dsub_rn(xi.z, cj.z));
+        if (e2 < thr) {
+          if (FILL) out[base + cnt] = t0 + k;
+          ++cnt;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (!FILL && i < n) out[i] = cnt;
+}
+
+__device__ void panel_exact(double xx, double xy, double xz, const double* __restrict__ v, bool self,
+                            double kappa, double out[4]) {
+  const double v0x = v[0], v0y = v[1], v0z = v[2];
+  double e1x = v[3] - v0x, e1y = v[4] - v0y, e1z = v[5] - v0z;
+  double e2x = v[6] - v0x, e2y = v[7] - v0y, e2z = v[8] - v0z;
+  double nx = e1y * e2z - e1z * e2y, ny = e1z * e2x - e1x * e2z, nz = e1x * e2y - e1y * e2x;
+  double nn = sqrt(nx * nx + ny * ny + nz * nz);
+  nx /= nn;
+  ny /= nn;
+  nz /= nn;
+  double h = self ? 0.0 : nx * (xx - v0x) + ny * (xy - v0y) + nz * (xz - v0z);
+  double px = xx - h * nx, py = xy - h * ny, pz = xz - h * nz;
+  double ah = fabs(h);
+  double sh = h > 0.0 ? 1.0 : (h < 0.0 ? -1.0 : 0.0);
+  double eh = exp(-kappa * ah);
+  double acc0 = 0, acc1 = 0, acc2 = 0, acc3 = 0;
+  for (int e = 0; e < 3; ++e) {
+    const double* A = v + 3 * e;
+    const double* B = v + 3 * ((e + 1) % 3);
+    double apx = A[0] - px, apy = A[1] - py, apz = A[2] - pz;
+    double bpx = B[0] - px, bpy = B[1] - py, bpz = B[2] - pz;
+    double abx = B[0] - A[0], aby = B[1] - A[1], abz = B[2] - A[2];
+    double L = sqrt(abx * abx + aby * aby + abz * abz);
+    double ux = abx / L, uy = aby / L, uz = abz / L;
+    double cx = apy * bpz - apz * bpy, cy = apz * bpx - apx * bpz, cz = apx * bpy - apy * bpx;
+    double nc = nx * cx + ny * cy + nz * cz;
+    double d = fabs(nc) / L;
+    if (!(d > 1e-14 * L)) continue;
+    double sig = nc > 0.0 ? 1.0 : -1.0;
+    double ta = apx * ux + apy * uy + apz * uz;
+    double tb = bpx * ux + bpy * uy + bpz * uz;
+    double ua = asinh(ta / d), ub = asinh(tb / d);
+    int np = max(1, (int)ceil(ub - ua));
+    double du = (ub - ua) / np;
+    for (int pc = 0; pc < np; ++pc) {
+      double u0 = ua + pc * du;
+      for (int q = 0; q < GL_N; ++q) {
+        double u = u0 + 0.5 * du * (c_gl_x[q] + 1.0);
+        double wq = 0.5 * du * c_gl_w[q];
+        double ch = cosh(u);
+        double rho = d * ch;
+        double s = sqrt(rho * rho + h * h);
+        double sm = rho * rho / (s + ah);
+        double fvl = sm, fkl = sh * sm / s, fvy, fky;
+        if (kappa > 0.0) {
+          double em = -expm1(-kappa * sm);
+          fvy = eh * em / kappa;
+          fky = sh * (eh * sm / s + (ah / s) * eh * em);
+        } else {
+          fvy = fvl;
+          fky = fkl;
+        }
+        double wt = sig * wq / ch;
+        acc0 += wt * fvl;
+        acc1 += wt * fkl;
+        acc2 += wt * fvy;
+        acc3 += wt * fky;
+      }
+    }
+  }
+  const double inv4pi = 0.25 / M_PI;
+  out[0] = acc0 * inv4pi;
+  out[1] = acc1 * inv4pi;
+  out[2] = acc2 * inv4pi;
+  out[3] = acc3 * inv4pi;
+}
+
+__global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n,
+                                 const double4* __restrict__ tgt64, const double* __restrict__ vert9,
+                                 const double4* __restrict__ src64, const double4* __restrict__ nrm64, int K,
+                                 double kappa, double4* __restrict__ corr) {
+  int i = blockIdx.x;  // one block per target row; threads over its near columns
+  if (i >= n) return;
+  int b = ptr[i], e = ptr[i + 1];
+  double4 x = tgt64[i];
+  for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+    int j = col[k];
+    double ex[4];
+    panel_exact(x.x, x.y, x.z, vert9 + 9 * (size_t)j, i == j, kappa, ex);
+    double4 nj = nrm64[j];
+    double vl = 0, kl = 0, vy = 0, ky = 0;
+    for (int g = 0; g < K; ++g) {
+      double4 y = src64[(size_t)K * j + g];
+      double rx = x.x - y.x, ry = x.y - y.y, rz = x.z - y.z;
+      double r2 = rx * rx + ry * ry + rz * rz;
+      if (r2 == 0.0) continue;
+      double R = sqrt(r2);
+      double inv = 1.0 / R;
+      double nr = nj.x * rx + nj.y * ry + nj.z * rz;
+      double ek = exp(-kappa * R);
+      double inv3 = inv * inv * inv;
+      vl += y.w * inv;
+      kl += y.w * nr * inv3;
+      vy += y.w * ek * inv;
+      ky += y.w * nr * (1.0 + kappa * R) * ek * inv3;
+    }
+    const double inv4pi = 0.25 / M_PI;
+    corr[k] = make_double4(ex[0] - vl * inv4pi, ex[1] - kl * inv4pi, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
+  }
+}
+
+}  // namespace
+
+void init_gauss_legendre() {
+  double x[GL_N], w[GL_N];
+  gauss_legendre(GL_N, x, w);
+  BP_CUDA(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
+  BP_CUDA(cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
+}
+
+void build_near(Ctx& c, cudaStream_t s) {
+  const int n = c.n;
+  double nf2 = c.par.near_factor * c.par.near_factor;
+  // FP32 prefilter margin: coordinates are rounded to FP32 (relative 2^-24), so the
+  // FP32 distance is within a few ulps of max|coordinate| of the FP64 one.
+  double cmax = 0;
+  for (int d = 0; d < 3; ++d) cmax = std::max(cmax, std::max(std::fabs(c.bbox_lo[d]), std::fabs(c.bbox_hi[d])));
+  float margin = (float)(64.0 * cmax * 5.9604644775390625e-08 + 1e-30);
+  DBuf<int> cnt;
+  cnt.alloc(n);
+  int tb = 256;
+  launch(near_list_kernel<false>, cdiv(n, tb), tb, 0, s, c.tgt64.p, c.tgt32.p, n, nf2, margin, nullptr, cnt.p);
+  BP_CHECK_LAUNCH();
+  std::vector<int> h(n);
+  BP_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  std::vector<int> ptr(n + 1, 0);
+  for (int i = 0; i < n; ++i) ptr[i + 1] = ptr[i] + h[i];
+  c.nnz = ptr[n];
+  c.near_ptr.alloc(n + 1);
+  c.near_col.alloc(std::max<int64_t>(1, c.nnz));
+  c.near_corr.alloc(std::max<int64_t>(1, c.nnz));
+  BP_CUDA(cudaMemcpyAsync(c.near_ptr.p, ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
+  launch(near_list_kernel<true>, cdiv(n, tb), tb, 0, s, c.tgt64.p, c.tgt32.p, n, nf2, margin, c.near_ptr.p,
+                                                     c.near_col.p);
+  BP_CHECK_LAUNCH();
+  launch(near_corr_kernel, n, 32, 0, s, c.near_ptr.p, c.near_col.p, n, c.tgt64.p, c.vert9.p, c.src64.p, c.nrm64.p,
+                                    c.K, c.par.kappa, c.near_corr.p);
+  BP_CHECK_LAUNCH();
+  BP_CUDA(cudaStreamSynchronize(s));
+}
+
+}  // namespace bp

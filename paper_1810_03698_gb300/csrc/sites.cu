@@ -1,0 +1,426 @@
+// Site-side kernels: multipole right-hand side (Eq. rhs_multipole), reaction
+// potential/field/Hessian at the sites (Eqs. pot_solvent, Efield_solv, ddphi),
+// multipole-multipole fields with Thole damping (Eqs. Efield_mult,
+// derivatives_Emult, second_derivative), the SOR update of the induced dipoles
+// (Sec. "Self-consistent induced field") and the energy of Eq.
+// energy_multipole_polarizable.
+//
+// Tensor conventions: R = r_field - r_source, r = |R|.  A site with charge q,
+// dipole p and traceless quadrupole Q (Eq. pot_multipole) has potential
+//   q/r + p.R/r^3 + R.Q.R/(2 r^5)        (times 1/(4 pi eps_in))
+// gradient
+//   -q R/r^3 + p/r^3 - 3 (p.R) R/r^5 + Q R/r^5 - (5/2)(R.Q.R) R/r^7
+// and Hessian
+//   q (3 R R/r^5 - I/r^3) + 15 (p.R) R R/r^7 - 3 ((p.R) I + p R + R p)/r^5
+//   + (35/2)(R.Q.R) R R/r^9 - (5/2)((R.Q.R) I + 2 (Q R) R + 2 R (Q R))/r^7 + Q/r^5.
+// Induced dipoles mu use the Thole-damped forms (AMOEBA reading of the paper's
+// "Thole-like" damping): u^3 = r^3 / sqrt(alpha_l alpha_m), e = exp(-a u^3),
+// lambda3 = 1 - e, lambda5 = 1 - (1 + a u^3) e, lambda7 = 1 - (1 + a u^3 + 0.6 (a u^3)^2) e:
+//   potential lambda3 mu.R/r^3, gradient lambda3 mu/r^3 - 3 lambda5 (mu.R) R/r^5,
+//   Hessian 15 lambda7 (mu.R) R R/r^7 - 3 lambda5 ((mu.R) I + mu R + R mu)/r^5.
+// Induced dipoles: mu = 4 pi alpha E (alpha a polarizability volume, potentials
+// in units with vacuum permittivity 1).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace bp {
+
+namespace {
+
+constexpr double INV4PI = 0.07957747154594767;  // 1/(4 pi)
+
+struct SiteSrc {   // one multipole, 13 values
+  double x, y, z, q, px, py, pz, qxx, qxy, qxz, qyy, qyz, qzz;
+};
+
+// ---------------------------------------------------------------- RHS
+template <typename Real>
+__global__ void rhs_kernel(const double4* __restrict__ tgt, int n, const double4* __restrict__ spos,
+                           const double* __restrict__ sq, const double* __restrict__ sp,
+                           const double* __restrict__ sQ, int ns, double scale, double* __restrict__ b) {
+  constexpr int T = 128;
+  __shared__ Real sh[13][T];
+  int i = blockIdx.x * T + threadIdx.x;
+  double4 xd = i < n ? tgt[i] : make_double4(0, 0, 0, 0);
+  Real x = (Real)xd.x, y = (Real)xd.y, z = (Real)xd.z;
+  double acc = 0.0;
+  for (int t0 = 0; t0 < ns; t0 += T) {
+    int k = t0 + threadIdx.x;
+    if (k < ns) {
+      double4 p = spos[k];
+      sh[0][threadIdx.x] = (Real)p.x;
+      sh[1][threadIdx.x] = (Real)p.y;
+      sh[2][threadIdx.x] = (Real)p.z;
+      sh[3][threadIdx.x] = (Real)sq[k];
+      sh[4][threadIdx.x] = (Real)sp[3 * k];
+      sh[5][threadIdx.x] = (Real)sp[3 * k + 1];
+      sh[6][threadIdx.x] = (Real)sp[3 * k + 2];
+      for (int c = 0; c < 6; ++c) sh[7 + c][threadIdx.x] = (Real)sQ[6 * k + c];
+    }
+    __syncthreads();
+    int lim = min(T, ns - t0);
+    Real a = 0;
+    for (int kk = 0; kk < lim; ++kk) {
+      Real Rx = x - sh[0][kk], Ry = y - sh[1][kk], Rz = z - sh[2][kk];
+      Real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+      Real rinv = (Real)1 / sqrt(r2);
+      Real rinv2 = rinv * rinv;
+      Real rinv3 = rinv2 * rinv;
+      Real pR = sh[4][kk] * Rx + sh[5][kk] * Ry + sh[6][kk] * Rz;
+      Real RQR = sh[7][kk] * Rx * Rx + sh[10][kk] * Ry * Ry + sh[12][kk] * Rz * Rz +
+                 (Real)2 * (sh[8][kk] * Rx * Ry + sh[9][kk] * Rx * Rz + sh[11][kk] * Ry * Rz);
+      a += sh[3][kk] * rinv + pR * rinv3 + (Real)0.5 * RQR * rinv3 * rinv2;
+    }
+    acc += (double)a;
+    __syncthreads();
+  }
+  if (i < n) b[i] = acc * scale;
+}
+
+// ---------------------------------------------------------------- reaction at sites
+// warp per site; the block's 8 warps share source tiles staged in shared memory.
+template <typename Real, typename R4, bool HESS>
+__global__ void __launch_bounds__(256) site_reaction_kernel(const double4* __restrict__ spos_site, int ns,
+                                                            const R4* __restrict__ src, const R4* __restrict__ str,
+                                                            int nsrc, int per_split, double* __restrict__ part) {
+  constexpr int T = 256;
+  __shared__ R4 tp[T];
+  __shared__ R4 ts[T];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int site = blockIdx.x * 8 + warp;
+  const int s0 = blockIdx.y * per_split, s1 = min(nsrc, s0 + per_split);
+  double4 sd = site < ns ? spos_site[site] : make_double4(0, 0, 0, 0);
+  const Real X = (Real)sd.x, Y = (Real)sd.y, Z = (Real)sd.z;
+  double acc[10];
+#pragma unroll
+  for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+  for (int t0 = s0; t0 < s1; t0 += T) {
+    int j = t0 + threadIdx.x;
+    if (j < s1) {
+      tp[threadIdx.x] = src[j];
+      ts[threadIdx.x] = str[j];
+    }
+    __syncthreads();
+    int lim = min(T, s1 - t0);
+    Real a[10];
+#pragma unroll
+    for (int c = 0; c < 10; ++c) a[c] = 0;
+    for (int k = lane; k < lim; k += 32) {
+      R4 p = tp[k], s = ts[k];
+      Real Rx = X - p.x, Ry = Y - p.y, Rz = Z - p.z;
+      Real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+      Real rinv = (Real)1 / sqrt(r2);
+      Real rinv2 = rinv * rinv;
+      Real A3 = rinv2 * rinv;             // 1/r^3
+      Real B5 = (Real)3 * A3 * rinv2;      // 3/r^5
+      Real m = s.x;
+      Real dR = s.y * Rx + s.z * Ry + s.w * Rz;
+      a[0] += m * rinv - dR * A3;
+      Real gc = -m * A3 + dR * B5;
+      a[1] += gc * Rx - s.y * A3;
+      a[2] += gc * Ry - s.z * A3;
+      a[3] += gc * Rz - s.w * A3;
+      if (HESS) {
+        Real C7 = (Real)5 * B5 * rinv2;    // 15/r^7
+        Real hc = m * B5 - dR * C7;
+        Real hd = dR * B5 - m * A3;
+        a[4] += hc * Rx * Rx + hd + (Real)2 * B5 * Rx * s.y;
+        a[5] += hc * Rx * Ry + B5 * (Rx * s.z + Ry * s.y);
+        a[6] += hc * Rx * Rz + B5 * (Rx * s.w + Rz * s.y);
+        a[7] += hc * Ry * Ry + hd + (Real)2 * B5 * Ry * s.z;
+        a[8] += hc * Ry * Rz + B5 * (Ry * s.w + Rz * s.z);
+        a[9] += hc * Rz * Rz + hd + (Real)2 * B5 * Rz * s.w;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 10; ++c) acc[c] += (double)a[c];
+    __syncthreads();
+  }
+  const int nc = HESS ? 10 : 4;
+#pragma unroll
+  for (int c = 0; c < 10; ++c) {
+    if (c >= nc) break;
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    acc[c] = v;
+  }
+  if (lane == 0 && site < ns) {
+    double* o = part + ((size_t)blockIdx.y * ns + site) * 10;
+    for (int c = 0; c < 10; ++c) o[c] = c < nc ? acc[c] : 0.0;
+  }
+}
+
+__global__ void site_reduce_kernel(const double* __restrict__ part, int S, int ns, double* __restrict__ out) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ns * 10) return;
+  double v = 0;
+  for (int s = 0; s < S; ++s) v += part[(size_t)s * ns * 10 + t];
+  out[t] = v * INV4PI;
+}
+
+// ---------------------------------------------------------------- multipole-multipole
+// mode 0: polarising field E (3 per site): permanent masked by group, induced damped.
+// mode 1: energy potentials (10 per site): permanent unmasked, induced damped.
+__global__ void __launch_bounds__(256) multipole_kernel(const double4* __restrict__ pos, const double* __restrict__ q,
+                                                        const double* __restrict__ d, const double* __restrict__ Q,
+                                                        const double* __restrict__ mu, const int* __restrict__ group,
+                                                        int ns, int mode, double thole_a, double scale,
+                                                        double* __restrict__ out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * 8 + warp;
+  if (l >= ns) return;
+  const double4 pl = pos[l];
+  const int gl = group[l];
+  double acc[10];
+  for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+  for (int m = lane; m < ns; m += 32) {
+    if (m == l) continue;
+    double4 pm = pos[m];
+    double Rx = pl.x - pm.x, Ry = pl.y - pm.y, Rz = pl.z - pm.z;
+    double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    double rinv = 1.0 / sqrt(r2);
+    double i2 = rinv * rinv, i3 = i2 * rinv, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
+    double R[3] = {Rx, Ry, Rz};
+    double g[3] = {0, 0, 0}, H[6] = {0, 0, 0, 0, 0, 0}, P = 0;
+    bool perm = (mode == 1) || (group[m] != gl);
+    if (perm) {
+      double qm = q[m];
+      double pv[3] = {d[3 * m], d[3 * m + 1], d[3 * m + 2]};
+      const double* Qm = Q + 6 * m;
+      double QM[3][3] = {{Qm[0], Qm[1], Qm[2]}, {Qm[1], Qm[3], Qm[4]}, {Qm[2], Qm[4], Qm[5]}};
+      double QR[3];
+      for (int a = 0; a < 3; ++a) QR[a] = QM[a][0] * Rx + QM[a][1] * Ry + QM[a][2] * Rz;
+      double RQR = QR[0] * Rx + QR[1] * Ry + QR[2] * Rz;
+      double pR = pv[0] * Rx + pv[1] * Ry + pv[2] * Rz;
+      P = qm * rinv + pR * i3 + 0.5 * RQR * i5;
+      for (int a = 0; a < 3; ++a)
+        g[a] = -qm * R[a] * i3 + pv[a] * i3 - 3.0 * pR * R[a] * i5 + QR[a] * i5 - 2.5 * RQR * R[a] * i7;
+      if (mode == 1) {
+        int k = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = a; b < 3; ++b, ++k) {
+            double dab = a == b ? 1.0 : 0.0;
+            H[k] = qm * (3.0 * R[a] * R[b] * i5 - dab * i3) + 15.0 * pR * R[a] * R[b] * i7 -
+                   3.0 * (pR * dab + pv[a] * R[b] + pv[b] * R[a]) * i5 + 17.5 * RQR * R[a] * R[b] * i9 -
+                   2.5 * (RQR * dab + 2.0 * QR[a] * R[b] + 2.0 * QR[b] * R[a]) * i7 + QM[a][b] * i5;
+          }
+      }
+    }
+    // induced dipole, Thole damped
+    double mv[3] = {mu[3 * m], mu[3 * m + 1], mu[3 * m + 2]};
+    double aa = pl.w * pm.w;
+    double l3 = 1.0, l5 = 1.0, l7 = 1.0;
+    if (aa > 0.0) {
+      double au3 = thole_a * r2 * sqrt(r2) / sqrt(aa);
+      double e = exp(-au3);
+      l3 = 1.0 - e;
+      l5 = 1.0 - (1.0 + au3) * e;
+      l7 = 1.0 - (1.0 + au3 + 0.6 * au3 * au3) * e;
+    }
+    double mR = mv[0] * Rx + mv[1] * Ry + mv[2] * Rz;
+    P += l3 * mR * i3;
+    for (int a = 0; a < 3; ++a) g[a] += l3 * mv[a] * i3 - 3.0 * l5 * mR * R[a] * i5;
+    if (mode == 1) {
+      int k = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = a; b < 3; ++b, ++k) {
+          double dab = a == b ? 1.0 : 0.0;
+          H[k] += 15.0 * l7 * mR * R[a] * R[b] * i7 - 3.0 * l5 * (mR * dab + mv[a] * R[b] + mv[b] * R[a]) * i5;
+        }
+    }
+    acc[0] += P;
+    for (int a = 0; a < 3; ++a) acc[1 + a] += g[a];
+    for (int k = 0; k < 6; ++k) acc[4 + k] += H[k];
+  }
+  for (int c = 0; c < 10; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    acc[c] = v;
+  }
+  if (lane == 0) {
+    if (mode == 0) {
+      for (int a = 0; a < 3; ++a) out[3 * l + a] = -acc[1 + a] * scale;
+    } else {
+      for (int c = 0; c < 10; ++c) out[10 * l + c] = acc[c] * scale;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- energy and SOR
+__global__ void energy_kernel(const double* __restrict__ q, const double* __restrict__ d,
+                              const double* __restrict__ Q, const double* __restrict__ r10,
+                              const double* __restrict__ m10, int ns, double* __restrict__ outE) {
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int l = threadIdx.x; l < ns; l += 256) {
+    double f[10];
+    for (int c = 0; c < 10; ++c) f[c] = (r10 ? r10[10 * l + c] : 0.0) + (m10 ? m10[10 * l + c] : 0.0);
+    const double* Ql = Q + 6 * l;
+    double QH = Ql[0] * f[4] + Ql[3] * f[7] + Ql[5] * f[9] + 2.0 * (Ql[1] * f[5] + Ql[2] * f[6] + Ql[4] * f[8]);
+    v += q[l] * f[0] + d[3 * l] * f[1] + d[3 * l + 1] * f[2] + d[3 * l + 2] * f[3] + QH / 6.0;
+  }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *outE = 0.5 * sh[0];
+}
+
+// mu_new = (1 - w) mu + w 4 pi alpha (E_solv + E_mult); returns sum |mu_new - mu|^2
+__global__ void sor_kernel(double* __restrict__ mu, const double4* __restrict__ pos,
+                           const double* __restrict__ react10, const double* __restrict__ emult, int ns,
+                           double omega, double* __restrict__ out_sq) {
+  __shared__ double sh[256];
+  double v = 0.0;
+  for (int l = threadIdx.x; l < ns; l += 256) {
+    double fa = 4.0 * M_PI * pos[l].w;
+    for (int a = 0; a < 3; ++a) {
+      double E = emult[3 * l + a] - (react10 ? react10[10 * l + 1 + a] : 0.0);
+      double old = mu[3 * l + a];
+      double nw = (1.0 - omega) * old + omega * fa * E;
+      mu[3 * l + a] = nw;
+      v += (nw - old) * (nw - old);
+    }
+  }
+  sh[threadIdx.x] = v;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out_sq = sh[0];
+}
+
+// ---------------------------------------------------------------- validation
+// flag[l] = 1 if site l is within the near radius of a panel centroid, 2 if outside the surface
+__global__ void site_check_kernel(const double4* __restrict__ spos, int ns, const double4* __restrict__ tgt64,
+                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int n,
+                                  int K, double nf2, int* __restrict__ flag) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = blockIdx.x * 8 + warp;
+  if (l >= ns) return;
+  double4 p = spos[l];
+  int near = 0;
+  double dl = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    double4 c = tgt64[j];
+    double dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
+    if (dx * dx + dy * dy + dz * dz < nf2 * c.w) near = 1;
+    double4 nj = nrm64[j];
+    for (int g = 0; g < K; ++g) {
+      double4 y = src64[(size_t)K * j + g];
+      double rx = p.x - y.x, ry = p.y - y.y, rz = p.z - y.z;
+      double r2 = rx * rx + ry * ry + rz * rz;
+      double ri = 1.0 / sqrt(r2);
+      dl += y.w * (nj.x * rx + nj.y * ry + nj.z * rz) * ri * ri * ri;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dl += __shfl_down_sync(0xffffffffu, dl, o);
+    near |= __shfl_down_sync(0xffffffffu, near, o);
+  }
+  if (lane == 0) {
+    // -K_L[1] = 1 inside a closed surface, 0 outside
+    double inside = -dl * INV4PI;
+    flag[l] = near ? 1 : (inside > 0.5 ? 0 : 2);
+  }
+}
+
+int site_splits(Ctx& c, int ns, int nsrc) {
+  int bx = cdiv(ns, 8);
+  int want = num_sms(c.device) * 6;
+  int S = std::max(1, cdiv(want, bx));
+  S = std::min(S, std::max(1, nsrc / 1024));
+  return std::min(S, 256);
+}
+
+}  // namespace
+
+void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s) {
+  const double* pp = p ? p : c.site_d.p;
+  double scale = INV4PI / c.par.eps_in;
+  if (fp32)
+    launch(rhs_kernel<float>, cdiv(c.n, 128), 128, 0, s, c.tgt64.p, c.n, c.site_pos.p, c.site_q.p, pp, c.site_Q.p,
+                                                     c.ns, scale, b);
+  else
+    launch(rhs_kernel<double>, cdiv(c.n, 128), 128, 0, s, c.tgt64.p, c.n, c.site_pos.p, c.site_q.p, pp, c.site_Q.p,
+                                                      c.ns, scale, b);
+  BP_CHECK_LAUNCH();
+}
+
+void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s) {
+  strengths(c, x, fp32, s);
+  const int nsrc = c.n * c.K;
+  int S = site_splits(c, c.ns, nsrc);
+  int per = cdiv(cdiv(nsrc, S), 256) * 256;
+  S = cdiv(nsrc, per);
+  size_t need = (size_t)S * c.ns * 10;
+  if (c.site_part.n < need) c.site_part.alloc(need);
+  dim3 grid(cdiv(c.ns, 8), S);
+  if (fp32) {
+    if (hessian)
+      launch(site_reaction_kernel<float, float4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
+                                                                    nsrc, per, c.site_part.p);
+    else
+      launch(site_reaction_kernel<float, float4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
+                                                                     nsrc, per, c.site_part.p);
+  } else {
+    if (hessian)
+      launch(site_reaction_kernel<double, double4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p, c.str64.p,
+                                                                      nsrc, per, c.site_part.p);
+    else
+      launch(site_reaction_kernel<double, double4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
+                                                                       c.str64.p, nsrc, per, c.site_part.p);
+  }
+  BP_CHECK_LAUNCH();
+  launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, c.site_part.p, S, c.ns, out);
+  BP_CHECK_LAUNCH();
+}
+
+void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s) {
+  launch(multipole_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
+                                                  c.site_group.p, c.ns, mode, c.par.thole_a,
+                                                  INV4PI / c.par.eps_in, out);
+  BP_CHECK_LAUNCH();
+}
+
+double energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s) {
+  launch(energy_kernel, 1, 256, 0, s, c.site_q.p, c.site_d.p, c.site_Q.p, react10, mult10, c.ns, c.scal.p);
+  BP_CHECK_LAUNCH();
+  BP_CUDA(cudaMemcpyAsync(c.h_pinned, c.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  return c.h_pinned[0];
+}
+
+double sor_update(Ctx& c, double* mu, const double* react10, const double* emult3, bool vacuum, cudaStream_t s) {
+  launch(sor_kernel, 1, 256, 0, s, mu, c.site_pos.p, vacuum ? nullptr : react10, emult3, c.ns, c.par.sor_omega,
+                               c.scal.p + 1);
+  BP_CHECK_LAUNCH();
+  BP_CUDA(cudaMemcpyAsync(c.h_pinned + 1, c.scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  return std::sqrt(c.h_pinned[1] / std::max(1, c.ns));
+}
+
+void site_validation(Ctx& c, cudaStream_t s) {
+  DBuf<int> flag;
+  flag.alloc(c.ns);
+  double nf2 = c.par.near_factor * c.par.near_factor;
+  launch(site_check_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.ns, c.tgt64.p, c.src64.p, c.nrm64.p, c.n, c.K,
+                                                  nf2, flag.p);
+  BP_CHECK_LAUNCH();
+  std::vector<int> h(c.ns);
+  BP_CUDA(cudaMemcpyAsync(h.data(), flag.p, sizeof(int) * c.ns, cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  for (int l = 0; l < c.ns; ++l) {
+    if (h[l] == 1)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies within the near-singular radius of a panel");
+    if (h[l] == 2) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies outside the surface");
+  }
+}
+
+}  // namespace bp

@@ -18,6 +18,17 @@ def pytest_collection_modifyitems(config, items):
     return None
 
 
+def build_library():
+    """Compile libbempol.so if needed (the build script is loaded by path: importing the
+    package itself requires the compiled library)."""
+    import importlib.util
+    path = os.path.join(ROOT, "paper_1810_03698_gb300", "build.py")
+    spec = importlib.util.spec_from_file_location("bempol_build", path)
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod.build()
+
+
 @pytest.fixture(scope="session")
 def cuda_available():
     try:
