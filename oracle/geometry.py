@@ -84,21 +84,25 @@ def near_pairs(cen: np.ndarray, area: np.ndarray, near_factor: float):
     The comparison is made on squared distances in FP64, with the squared
     distance summed as dx*dx + dy*dy + dz*dz in that order.  Includes j = i.
     Returns (row_ptr [N+1] int64, cols int32 sorted ascending per row).
+    Candidates come from a k-d tree ball query with a radius above every
+    threshold (so no near pair is missed); each candidate then gets the exact test.
     """
+    from scipy.spatial import cKDTree
+
     n = cen.shape[0]
     thr = (near_factor * near_factor) * area
-    rows = [np.zeros(0, dtype=np.int32)] * n
-    chunk = 512
-    for s in range(0, n, chunk):
-        e = min(n, s + chunk)
-        dx = cen[s:e, None, 0] - cen[None, :, 0]
-        dy = cen[s:e, None, 1] - cen[None, :, 1]
-        dz = cen[s:e, None, 2] - cen[None, :, 2]
-        d2 = dx * dx + dy * dy + dz * dz
-        m = d2 < thr[s:e, None]
-        for i in range(s, e):
-            rows[i] = np.nonzero(m[i - s])[0].astype(np.int32)
+    radius = float(np.sqrt(thr.max())) * (1.0 + 1e-6) + 1e-12
+    cand = cKDTree(cen).query_ball_point(cen, radius)
+    counts = np.array([len(c) for c in cand], dtype=np.int64)
+    ci = np.repeat(np.arange(n), counts)
+    cj = np.concatenate([np.asarray(c, dtype=np.int64) for c in cand]) if n else np.zeros(0, np.int64)
+    dx = cen[ci, 0] - cen[cj, 0]
+    dy = cen[ci, 1] - cen[cj, 1]
+    dz = cen[ci, 2] - cen[cj, 2]
+    keep = (dx * dx + dy * dy + dz * dz) < thr[ci]
+    ci, cj = ci[keep], cj[keep]
+    order = np.lexsort((cj, ci))
+    ci, cj = ci[order], cj[order]
     ptr = np.zeros(n + 1, dtype=np.int64)
-    ptr[1:] = np.cumsum([r.size for r in rows])
-    cols = np.concatenate(rows) if n else np.zeros(0, dtype=np.int32)
-    return ptr, cols
+    ptr[1:] = np.cumsum(np.bincount(ci, minlength=n))
+    return ptr, cj.astype(np.int32)
