@@ -79,7 +79,7 @@ typedef struct {
   int gauss_k;                 /* Gauss nodes per far panel: 1, 3 or 4 */
   double near_factor;          /* near-singular threshold: |x_i - c_j| < near_factor*sqrt(A_i) */
   double theta;                /* treecode multipole acceptance: cell accepted if R_cell / dist < theta */
-  int order;                   /* treecode Taylor order P (1..10) */
+  int order;                   /* treecode Taylor order P (1..6) */
   int leaf;                    /* treecode maximum panels per leaf */
   double gmres_tol;            /* stop when ||b - A x||_2 / ||b||_2 < gmres_tol */
   int gmres_restart;           /* Krylov basis size before a restart */

@@ -78,7 +78,7 @@ void check_params(const bempol_params* p) {
   if (p->gauss_k != 1 && p->gauss_k != 3 && p->gauss_k != 4) bad("gauss_k must be 1, 3 or 4");
   if (!(p->near_factor >= 0)) bad("near_factor must be >= 0");
   if (!(p->theta > 0 && p->theta < 1.5)) bad("theta must be in (0, 1.5)");
-  if (p->order < 1 || p->order > 10) bad("order must be in 1..10");
+  if (p->order < 1 || p->order > 6) bad("order must be in 1..6");
   if (p->leaf < 8 || p->leaf > 4096) bad("leaf must be in 8..4096");
   if (!(p->gmres_tol > 0)) bad("gmres_tol must be > 0");
   if (p->gmres_restart < 1 || p->gmres_restart > 1000) bad("gmres_restart must be in 1..1000");
@@ -229,7 +229,7 @@ bempol_status bempol_set_params(bempol_ctx* c, const bempol_params* p) {
   return guard(c, [&] {
     check_params(p);
     bool geo = p->gauss_k != c->par.gauss_k || p->near_factor != c->par.near_factor || p->kappa != c->par.kappa;
-    bool tree = p->leaf != c->par.leaf || geo;
+    bool tree = p->leaf != c->par.leaf || p->theta != c->par.theta || geo;
     if (geo && c->have_mesh) fail(BEMPOL_ERR_STATE, "gauss_k, near_factor and kappa are fixed once a mesh is set");
     c->par = *p;
     if (tree) c->tree_ready = false;
@@ -507,12 +507,33 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
     int gm_iters = 0, matvecs = 0, solves = 0;
     double last_res = 0;
     bool ok = true;
+    // Divergence guard: the relaxed update converges only when every eigenvalue of
+    // 4 pi alpha T (plus the reaction coupling) exceeds 1 - 2/omega.  A change that is
+    // not finite, or that has grown 8 times in a row to more than 10x its smallest
+    // value, ends the solve with an error (stagnation at the operator's noise level
+    // instead runs to scf_maxit).
+    struct Guard {
+      double best = 1e300, prev = 1e300;
+      int grow = 0;
+      void check(double rms, const char* state) {
+        if (!std::isfinite(rms)) grow = 1000;
+        grow = (rms > prev) ? grow + 1 : 0;
+        prev = rms;
+        best = std::min(best, rms);
+        if (grow >= 1000 || (grow >= 8 && rms > 10.0 * best))
+          fail(BEMPOL_ERR_NOT_CONVERGED, std::string("induced-dipole iteration diverges in the ") + state +
+                                             " state (RMS change grows); sor_omega is outside the convergence range "
+                                             "of this polarizability coupling");
+      }
+    };
     // vacuum state: multipoles only
     int it_v = 0;
+    Guard gv;
     for (it_v = 1; it_v <= P.scf_maxit; ++it_v) {
       multipole_internal(*c, mu_v.p, 0, emult.p, s);
       double rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, s);
       if (rms < P.scf_tol) break;
+      gv.check(rms, "vacuum");
     }
     if (it_v > P.scf_maxit) {
       ok = false;
@@ -529,12 +550,14 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
       if (!g.converged) ok = false;
     };
     int it = 0;
+    Guard gd;
     for (it = 1; it <= P.scf_maxit; ++it) {
       bem();
       site_reaction_internal(*c, x.p, react.p, f32, false, s);
       multipole_internal(*c, mu.p, 0, emult.p, s);
       double rms = sor_update(*c, mu.p, react.p, emult.p, false, s);
       if (rms < P.scf_tol) break;
+      gd.check(rms, "dissolved");
     }
     if (it > P.scf_maxit) {
       ok = false;

@@ -211,6 +211,14 @@ void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, 
   c.iperm.alloc(n);
   launch(perm_from_keys, cdiv(n, 256), 256, 0, s, keys.p, n, c.perm.p, c.iperm.p);
   BP_CHECK_LAUNCH();
+  {
+    // sorted Morton codes (high 32 bits of the keys) for the host-side tree topology
+    std::vector<unsigned long long> hk(n);
+    BP_CUDA(cudaMemcpyAsync(hk.data(), keys.p, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost, s));
+    BP_CUDA(cudaStreamSynchronize(s));
+    c.h_morton.resize(n);
+    for (int i = 0; i < n; ++i) c.h_morton[i] = (unsigned)(hk[i] >> 32);
+  }
   c.tgt64.alloc(n);
   c.tgt32.alloc(n);
   c.nrm64.alloc(n);

@@ -77,14 +77,30 @@ struct DBuf {
 };
 
 // ---------------------------------------------------------------- tree
+// Octree over the Morton-ordered panels.  Cells are stored in breadth-first
+// order; cells of tree depth d are [h_depth_begin[d], h_depth_begin[d+1]).
+// A cell owns the contiguous panel range [begin, end) and its Gauss nodes
+// [K*begin, K*end).  Leaves are the target batches of the treecode.
 struct Tree {
-  int ncell = 0, nleaf = 0, depth = 0;
-  DBuf<int> cell_begin, cell_end;      // panel range [begin, end) of each cell
-  DBuf<int> cell_child;                // first child index (-1 leaf), children contiguous
-  DBuf<int> cell_nchild;
-  DBuf<double4> cell_center;           // x, y, z, radius (covers every Gauss node in the cell)
-  DBuf<int> leaves;                    // cell indices of leaves
-  std::vector<int> h_level_begin;      // cells of level l: [h_level_begin[l], h_level_begin[l+1])
+  int ncell = 0, nleaf = 0, ndepth = 0;
+  std::vector<int> h_begin, h_end, h_child0, h_nchild;   // host topology
+  std::vector<int> h_depth_begin;
+  std::vector<int> h_leaf_cell;                          // leaf number -> cell
+  std::vector<double4> h_center;                         // copy of `center`
+  DBuf<int> begin, end, child0, nchild;
+  DBuf<double4> center;                                  // x, y, z of the node bounding-box centre; w = radius
+  DBuf<int> leaf_cell;                                   // leaf number -> cell
+  // interaction lists per leaf (CSR): accepted far cells, near (direct) leaves
+  DBuf<int> far_ptr, far_list, near_ptr, near_list;
+  // target blocks: (leaf number, first panel, count <= 128)
+  int nblk = 0;
+  DBuf<int4> blk;
+  // multipole moments [ncell][2][NC]: single layer M_k, double layer D_k
+  DBuf<float> mom32;
+  DBuf<double> mom64;
+  int mom_order = -1;
+  double theta_built = -1.0;
+  long long pairs_per_matvec = 0, far_per_matvec = 0;
 };
 
 // ---------------------------------------------------------------- context
@@ -113,6 +129,7 @@ struct Ctx {
   DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections
   int64_t nnz = 0;
   double bbox_lo[3], bbox_hi[3];
+  std::vector<unsigned> h_morton;  // 30-bit Morton code of each internal panel (sorted)
   Tree tree;
   bool tree_ready = false;
 

@@ -1,19 +1,681 @@
-// Treecode matvec (Sec. "The treecode algorithm").  Placeholder until the
-// Morton-octree far field lands: the tree operators report an argument error.
+// Treecode matrix-vector product (Sec. "The treecode algorithm").
+//
+// Sources are the Gauss nodes, targets the collocation points; both live in the
+// octree over the Morton-ordered panels.  For a target batch (a leaf) and a cell
+// C with radius R_C, the cell is accepted (far field) when
+//     R_C < theta * (|c_T - c_C| - R_T),
+// i.e. the paper's acceptance criterion theta > R_b / R_tb holds for every target
+// of the batch; otherwise C is opened, and leaves that are never accepted are
+// summed directly (near field).
+//
+// Far field (Cartesian Taylor expansion about the cell centre c, order P):
+// with Delta = x - c and h = y - c,
+//     G(x - y) = sum_{|k| <= P} a_k(Delta) h^k,   a_k = (1/k!) d^k/dh^k G(Delta - h) at h = 0,
+// so  V = sum_k a_k M_k   with M_k = sum_s m_s h_s^k             (single layer),
+//     K = sum_k a_k D_k   with D_k = sum_s sum_j k_j d_sj h_s^(k - e_j)  (double layer:
+//         the moments of the dipole layer, since d . grad_y G = d . grad_h of the series).
+// Coefficients by recurrence in |k| = n, written for f(h) = e^{-kappa r}/r, r = |Delta - h|
+// (kappa = 0 gives Laplace).  From r^2 grad f = (Delta - h)(f + kappa e^{-kappa r}) and
+// grad e^{-kappa r} = kappa (Delta - h) f one gets, with b_k the coefficients of e^{-kappa r},
+//     n |Delta|^2 a_k = (2n - 1) sum_j Delta_j a_{k-e_j} - (n - 1) sum_j a_{k-2e_j}
+//                       + kappa sum_j (Delta_j b_{k-e_j} - b_{k-2e_j}),
+//     n b_k           = kappa sum_j (Delta_j a_{k-e_j} - a_{k-2e_j}),
+// a_0 = e^{-kappa|Delta|}/|Delta|, b_0 = e^{-kappa|Delta|} (terms with a negative index vanish).
+// Moments of a parent follow from its children's by the exact shift
+//     M_k(c_p) = sum_{l <= k} prod_i C(k_i, l_i) (c_c - c_p)_i^(k_i - l_i) M_l(c_c)
+// (and the same for D_k).
+//
+// Precision: the FP32 form takes every coordinate difference relative to a
+// nearby centre subtracted in FP64 (target-leaf centre for the near field,
+// Delta = (x - c_T) + (c_T - c_C) for the far field), keeps per-cell and per-tile
+// sums in FP32 and per-target sums in FP64.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
 #include "internal.h"
 
 namespace bp {
 
+namespace {
+
+constexpr int TB = 128;      // targets per block (a leaf chunk)
+constexpr int MAXP = 6;      // highest Taylor order compiled
+
+// ---------------------------------------------------------------- multi-index tables
+template <int P>
+struct MI {
+  static constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+  int k[NC][3];
+  int ord[NC];
+  int m1[NC][3];  // index of k - e_j, or -1
+  int m2[NC][3];  // index of k - 2 e_j, or -1
+  int idx[P + 1][P + 1][P + 1];
+  constexpr MI() : k{}, ord{}, m1{}, m2{}, idx{} {
+    int t = 0;
+    for (int a = 0; a <= P; ++a)
+      for (int b = 0; b <= P; ++b)
+        for (int c = 0; c <= P; ++c) idx[a][b][c] = -1;
+    for (int n = 0; n <= P; ++n)
+      for (int a = n; a >= 0; --a)
+        for (int b = n - a; b >= 0; --b) {
+          k[t][0] = a;
+          k[t][1] = b;
+          k[t][2] = n - a - b;
+          ord[t] = n;
+          idx[a][b][n - a - b] = t;
+          ++t;
+        }
+    for (int u = 0; u < NC; ++u)
+      for (int j = 0; j < 3; ++j) {
+        int q[3] = {k[u][0], k[u][1], k[u][2]};
+        m1[u][j] = -1;
+        m2[u][j] = -1;
+        if (q[j] >= 1) {
+          q[j] -= 1;
+          m1[u][j] = idx[q[0]][q[1]][q[2]];
+          q[j] += 1;
+        }
+        if (q[j] >= 2) {
+          q[j] -= 2;
+          m2[u][j] = idx[q[0]][q[1]][q[2]];
+          q[j] += 2;
+        }
+      }
+  }
+};
+
+__host__ __device__ constexpr int ncoef(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+// constant-memory copies for kernels that index the tables at run time
+template <int P>
+__constant__ MI<P> c_mi{};
+
+struct Binom {
+  int b[MAXP + 1][MAXP + 1];
+  constexpr Binom() : b{} {
+    for (int a = 0; a <= MAXP; ++a) {
+      b[a][0] = 1;
+      for (int q = 1; q <= a; ++q) b[a][q] = b[a - 1][q - 1] + (q <= a - 1 ? b[a - 1][q] : 0);
+    }
+  }
+};
+__constant__ Binom c_binom{};
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrt_approx(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float exp_neg(float kr) { return exp2_approx(-1.4426950408889634f * kr); }
+__device__ __forceinline__ double exp_neg(double kr) { return exp(-kr); }
+
+template <typename R4>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  typedef float4 T;
+};
+template <>
+struct Vec4<double> {
+  typedef double4 T;
+};
+
+// ---------------------------------------------------------------- cell geometry
+// centre = midpoint of the bounding box of the cell's Gauss nodes; radius = max distance to them
+__global__ void cell_geometry_kernel(const int* __restrict__ begin, const int* __restrict__ end, int K,
+                                     const double4* __restrict__ src64, double4* __restrict__ center) {
+  __shared__ double sh[6][256];
+  const int cidx = blockIdx.x;
+  const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int j = s0 + threadIdx.x; j < s1; j += 256) {
+    double4 y = src64[j];
+    lo[0] = fmin(lo[0], y.x); hi[0] = fmax(hi[0], y.x);
+    lo[1] = fmin(lo[1], y.y); hi[1] = fmax(hi[1], y.y);
+    lo[2] = fmin(lo[2], y.z); hi[2] = fmax(hi[2], y.z);
+  }
+  for (int d = 0; d < 3; ++d) {
+    sh[d][threadIdx.x] = lo[d];
+    sh[3 + d][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + s]);
+        sh[3 + d][threadIdx.x] = fmax(sh[3 + d][threadIdx.x], sh[3 + d][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  const double cx = 0.5 * (sh[0][0] + sh[3][0]), cy = 0.5 * (sh[1][0] + sh[4][0]), cz = 0.5 * (sh[2][0] + sh[5][0]);
+  __syncthreads();
+  double r2 = 0.0;
+  for (int j = s0 + threadIdx.x; j < s1; j += 256) {
+    double4 y = src64[j];
+    double dx = y.x - cx, dy = y.y - cy, dz = y.z - cz;
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+  }
+  sh[0][threadIdx.x] = r2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) center[cidx] = make_double4(cx, cy, cz, sqrt(sh[0][0]));
+}
+
+// ---------------------------------------------------------------- moments
+// Leaf moments from the sources: one block per leaf, thread o owns moments o, o + TB, ...
+template <int P, typename Real>
+__global__ void __launch_bounds__(TB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
+                                                          const int* __restrict__ begin, const int* __restrict__ end,
+                                                          const double4* __restrict__ center, int K,
+                                                          const double4* __restrict__ src64,
+                                                          const typename Vec4<Real>::T* __restrict__ str,
+                                                          Real* __restrict__ mom) {
+  const MI<P>& mi = c_mi<P>;
+  constexpr int NC = MI<P>::NC;
+  __shared__ Real pw[TB][3][P + 1];
+  __shared__ Real sd[TB][4];
+  const int cidx = leaf_cell[blockIdx.x];
+  const double4 c = center[cidx];
+  const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
+  Real acc[(2 * NC + TB - 1) / TB];
+  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) acc[u] = 0;
+  for (int t0 = s0; t0 < s1; t0 += TB) {
+    int j = t0 + threadIdx.x;
+    if (j < s1) {
+      double4 y = src64[j];
+      Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
+      for (int d = 0; d < 3; ++d) {
+        Real p = 1;
+        for (int e = 0; e <= P; ++e) {
+          pw[threadIdx.x][d][e] = p;
+          p *= h[d];
+        }
+      }
+      auto s = str[j];
+      sd[threadIdx.x][0] = s.x;
+      sd[threadIdx.x][1] = s.y;
+      sd[threadIdx.x][2] = s.z;
+      sd[threadIdx.x][3] = s.w;
+    }
+    __syncthreads();
+    const int lim = min(TB, s1 - t0);
+    for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
+      const int o = threadIdx.x + u * TB;
+      if (o >= 2 * NC) break;
+      const bool dbl = o >= NC;
+      const int t = dbl ? o - NC : o;
+      const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
+      Real a = 0;
+      for (int q = 0; q < lim; ++q) {
+        if (!dbl) {
+          a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
+        } else {
+          Real v = 0;
+          if (kx) v += (Real)kx * sd[q][1] * pw[q][0][kx - 1] * pw[q][1][ky] * pw[q][2][kz];
+          if (ky) v += (Real)ky * sd[q][2] * pw[q][0][kx] * pw[q][1][ky - 1] * pw[q][2][kz];
+          if (kz) v += (Real)kz * sd[q][3] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz - 1];
+          a += v;
+        }
+      }
+      acc[u] += a;
+    }
+    __syncthreads();
+  }
+  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
+    const int o = threadIdx.x + u * TB;
+    if (o < 2 * NC) mom[(size_t)cidx * 2 * NC + o] = acc[u];
+  }
+}
+
+// Parent moments by shifting the children's: one block per parent cell of one depth.
+template <int P, typename Real>
+__global__ void __launch_bounds__(TB) m2m_kernel(int first_cell, const int* __restrict__ child0,
+                                                 const int* __restrict__ nchild, const double4* __restrict__ center,
+                                                 Real* __restrict__ mom) {
+  const MI<P>& mi = c_mi<P>;
+  constexpr int NC = MI<P>::NC;
+  __shared__ Real dp[8][3][P + 1];
+  __shared__ Real cm[8][2 * NC];
+  const int pc = first_cell + blockIdx.x;
+  const int nch = nchild[pc];
+  if (nch == 0) return;  // leaf (uniform across the block)
+  const int c0 = child0[pc];
+  const double4 cp = center[pc];
+  if (threadIdx.x < nch) {
+    double4 cc = center[c0 + threadIdx.x];
+    Real dl[3] = {(Real)(cc.x - cp.x), (Real)(cc.y - cp.y), (Real)(cc.z - cp.z)};
+    for (int d = 0; d < 3; ++d) {
+      Real p = 1;
+      for (int e = 0; e <= P; ++e) {
+        dp[threadIdx.x][d][e] = p;
+        p *= dl[d];
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < nch * 2 * NC; q += TB) cm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)(c0 + q / (2 * NC)) * 2 * NC + q % (2 * NC)];
+  __syncthreads();
+  const auto& binom = c_binom.b;
+  for (int o = threadIdx.x; o < 2 * NC; o += TB) {
+    const int t = o < NC ? o : o - NC;
+    const int off = o < NC ? 0 : NC;
+    const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
+    Real a = 0;
+    for (int ch = 0; ch < nch; ++ch)
+      for (int lx = 0; lx <= kx; ++lx)
+        for (int ly = 0; ly <= ky; ++ly)
+          for (int lz = 0; lz <= kz; ++lz) {
+            const int l = mi.idx[lx][ly][lz];
+            a += (Real)(binom[kx][lx] * binom[ky][ly] * binom[kz][lz]) * dp[ch][0][kx - lx] * dp[ch][1][ky - ly] *
+                 dp[ch][2][kz - lz] * cm[ch][off + l];
+          }
+    mom[(size_t)pc * 2 * NC + o] = a;
+  }
+}
+
+// ---------------------------------------------------------------- far field
+// One (target, cell) interaction: Laplace coefficients a_k, then Yukawa a_k, b_k,
+// each dotted with the cell's single-layer (M) and double-layer (Dm) moments.
+// Fully unrolled for a compile-time order, so every table index is a constant.
+template <int P, typename Real>
+__device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict__ M, const Real* __restrict__ Dm,
+                                         Real kappa, Real& vl, Real& kl, Real& vy, Real& ky) {
+  constexpr MI<P> mi{};
+  constexpr int NC = MI<P>::NC;
+  const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+  const Real rinv = inv_sqrt(r2);
+  const Real ir2 = rinv * rinv;
+  Real a[NC];
+  a[0] = rinv;
+  Real sV = a[0] * M[0], sK = a[0] * Dm[0];
+#pragma unroll
+  for (int t = 1; t < NC; ++t) {
+    const int n = mi.ord[t];
+    Real s1 = 0, s2 = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (mi.m1[t][j] >= 0) s1 += D[j] * a[mi.m1[t][j]];
+      if (mi.m2[t][j] >= 0) s2 += a[mi.m2[t][j]];
+    }
+    a[t] = ((Real)(2 * n - 1) * s1 - (Real)(n - 1) * s2) * (ir2 * (Real)(1.0 / n));
+    sV += a[t] * M[t];
+    sK += a[t] * Dm[t];
+  }
+  vl += sV;
+  kl += sK;
+  const Real r = r2 * rinv;
+  const Real e = exp_neg(kappa * r);
+  Real A[NC], Bc[NC];
+  A[0] = e * rinv;
+  Bc[0] = e;
+  sV = A[0] * M[0];
+  sK = A[0] * Dm[0];
+#pragma unroll
+  for (int t = 1; t < NC; ++t) {
+    const int n = mi.ord[t];
+    Real s1a = 0, s2a = 0, s1b = 0, s2b = 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      if (mi.m1[t][j] >= 0) {
+        s1a += D[j] * A[mi.m1[t][j]];
+        s1b += D[j] * Bc[mi.m1[t][j]];
+      }
+      if (mi.m2[t][j] >= 0) {
+        s2a += A[mi.m2[t][j]];
+        s2b += Bc[mi.m2[t][j]];
+      }
+    }
+    Bc[t] = kappa * (Real)(1.0 / n) * (s1a - s2a);
+    A[t] = ((Real)(2 * n - 1) * s1a - (Real)(n - 1) * s2a + kappa * (s1b - s2b)) * (ir2 * (Real)(1.0 / n));
+    sV += A[t] * M[t];
+    sK += A[t] * Dm[t];
+  }
+  vy += sV;
+  ky += sK;
+}
+
+constexpr int FCH = 8;  // far cells staged in shared memory per pass
+
+// One block per target block (<= 128 targets of one leaf); loops over the leaf's far cells.
+template <int P, typename Real>
+__global__ void __launch_bounds__(TB) far_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                                 const int* __restrict__ leaf_cell, const double4* __restrict__ center,
+                                                 const int* __restrict__ far_ptr, const int* __restrict__ far_list,
+                                                 const Real* __restrict__ mom, Real kappa, int n,
+                                                 double* __restrict__ out) {
+  constexpr int NC = MI<P>::NC;
+  __shared__ Real sm[FCH][2 * NC];
+  __shared__ Real so[FCH][3];
+  const int4 B = blk[blockIdx.x];
+  const int leaf = B.x;
+  const double4 ct = center[leaf_cell[leaf]];
+  const int i = B.y + threadIdx.x;
+  const bool act = (int)threadIdx.x < B.z;
+  Real xr[3] = {0, 0, 0};
+  if (act) {
+    double4 x = tgt64[i];
+    xr[0] = (Real)(x.x - ct.x);
+    xr[1] = (Real)(x.y - ct.y);
+    xr[2] = (Real)(x.z - ct.z);
+  }
+  double aVL = 0, aKL = 0, aVY = 0, aKY = 0;
+  const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
+  for (int fb = f0; fb < f1; fb += FCH) {
+    const int cnt = min(FCH, f1 - fb);
+    for (int q = threadIdx.x; q < cnt * 2 * NC; q += TB)
+      sm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+    if ((int)threadIdx.x < cnt) {
+      double4 cc = center[far_list[fb + threadIdx.x]];
+      so[threadIdx.x][0] = (Real)(ct.x - cc.x);
+      so[threadIdx.x][1] = (Real)(ct.y - cc.y);
+      so[threadIdx.x][2] = (Real)(ct.z - cc.z);
+    }
+    __syncthreads();
+    Real vl = 0, kl = 0, vy = 0, ky = 0;
+    for (int q = 0; q < cnt; ++q) {
+      const Real D[3] = {xr[0] + so[q][0], xr[1] + so[q][1], xr[2] + so[q][2]};
+      far_eval<P, Real>(D, sm[q], sm[q] + NC, kappa, vl, kl, vy, ky);
+    }
+    aVL += (double)vl;
+    aKL += (double)kl;
+    aVY += (double)vy;
+    aKY += (double)ky;
+    __syncthreads();
+  }
+  if (act) {
+    out[i] = aVL;
+    out[n + i] = aKL;
+    out[2 * n + i] = aVY;
+    out[3 * n + i] = aKY;
+  }
+}
+
+// ---------------------------------------------------------------- near field
+__device__ __forceinline__ void pair_accum(const float x[3], float4 p, float4 s, float kappa, float nk_log2e,
+                                           float& vl, float& kl, float& vy, float& ky) {
+  float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+  float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+  float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
+  float r = r2 * rinv;
+  float e = exp2_approx(r * nk_log2e);
+  float mr = s.x * rinv;
+  vl += mr;
+  vy = fmaf(mr, e, vy);
+  float dR = fmaf(s.y, dx, fmaf(s.z, dy, s.w * dz));
+  float t = dR * (rinv * rinv) * rinv;
+  kl += t;
+  ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
+}
+
+__device__ __forceinline__ void pair_accum(const double x[3], double4 p, double4 s, double kappa, double,
+                                           double& vl, double& kl, double& vy, double& ky) {
+  double dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+  double r2 = dx * dx + dy * dy + dz * dz;
+  if (r2 == 0.0) return;
+  double R = sqrt(r2);
+  double rinv = 1.0 / R;
+  double e = exp(-kappa * R);
+  double mr = s.x * rinv;
+  vl += mr;
+  vy += mr * e;
+  double t = (s.y * dx + s.z * dy + s.w * dz) * rinv * rinv * rinv;
+  kl += t;
+  ky += t * (1.0 + kappa * R) * e;
+}
+
+// One block per target block; loops over the source leaves of the leaf's near list.
+template <typename Real>
+__global__ void __launch_bounds__(TB) near_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                                  const int* __restrict__ leaf_cell,
+                                                  const double4* __restrict__ center, const int* __restrict__ begin,
+                                                  const int* __restrict__ end, const int* __restrict__ near_ptr,
+                                                  const int* __restrict__ near_list, int K,
+                                                  const double4* __restrict__ src64,
+                                                  const typename Vec4<Real>::T* __restrict__ str, Real kappa,
+                                                  Real nk_log2e, int n, double* __restrict__ out) {
+  typedef typename Vec4<Real>::T R4;
+  __shared__ R4 sp[TB];
+  __shared__ R4 ss[TB];
+  const int4 B = blk[blockIdx.x];
+  const int leaf = B.x;
+  const double4 ct = center[leaf_cell[leaf]];
+  const int i = B.y + threadIdx.x;
+  const bool act = (int)threadIdx.x < B.z;
+  Real xr[3] = {0, 0, 0};
+  if (act) {
+    double4 x = tgt64[i];
+    xr[0] = (Real)(x.x - ct.x);
+    xr[1] = (Real)(x.y - ct.y);
+    xr[2] = (Real)(x.z - ct.z);
+  }
+  double acc[4] = {0, 0, 0, 0};
+  for (int e = near_ptr[leaf]; e < near_ptr[leaf + 1]; ++e) {
+    const int cl = leaf_cell[near_list[e]];
+    const int s0 = begin[cl] * K, s1 = end[cl] * K;
+    for (int t0 = s0; t0 < s1; t0 += TB) {
+      const int j = t0 + threadIdx.x;
+      R4 pz, sz;
+      pz.x = pz.y = pz.z = pz.w = 0;
+      sz = pz;
+      if (j < s1) {
+        double4 y = src64[j];
+        pz.x = (Real)(y.x - ct.x);
+        pz.y = (Real)(y.y - ct.y);
+        pz.z = (Real)(y.z - ct.z);
+        sz = str[j];
+      }
+      sp[threadIdx.x] = pz;
+      ss[threadIdx.x] = sz;
+      __syncthreads();
+      Real vl = 0, kl = 0, vy = 0, ky = 0;
+      const int lim = min(TB, s1 - t0);
+      for (int k = 0; k < lim; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
+      acc[0] += (double)vl;
+      acc[1] += (double)kl;
+      acc[2] += (double)vy;
+      acc[3] += (double)ky;
+      __syncthreads();
+    }
+  }
+  if (act) {
+    out[i] = acc[0];
+    out[n + i] = acc[1];
+    out[2 * n + i] = acc[2];
+    out[3 * n + i] = acc[3];
+  }
+}
+
+}  // namespace
+
+namespace {
+
+// Octree topology from the sorted 30-bit Morton codes (10 levels of 3 bits).
+// A cell with more than `leaf` panels is split by the next Morton digit; digits
+// shared by every panel of the cell are skipped, so no cell has a single child.
+void build_topology(Ctx& c) {
+  Tree& T = c.tree;
+  const int n = c.n;
+  const std::vector<unsigned>& m = c.h_morton;
+  T.h_begin.assign(1, 0);
+  T.h_end.assign(1, n);
+  T.h_child0.assign(1, -1);
+  T.h_nchild.assign(1, 0);
+  std::vector<int> lev(1, 0), depth(1, 0);
+  for (size_t q = 0; q < T.h_begin.size(); ++q) {
+    const int b = T.h_begin[q], e = T.h_end[q];
+    if (e - b <= c.par.leaf) continue;
+    int l = lev[q];
+    auto digit = [&](int i, int L) { return (int)((m[i] >> (27 - 3 * L)) & 7u); };
+    while (l < 10 && digit(b, l) == digit(e - 1, l)) ++l;
+    if (l >= 10) continue;  // identical codes: keep as an oversized leaf
+    T.h_child0[q] = (int)T.h_begin.size();
+    int start = b;
+    for (int i = b + 1; i <= e; ++i) {
+      if (i == e || digit(i, l) != digit(start, l)) {
+        T.h_begin.push_back(start);
+        T.h_end.push_back(i);
+        T.h_child0.push_back(-1);
+        T.h_nchild.push_back(0);
+        lev.push_back(l + 1);
+        depth.push_back(depth[q] + 1);
+        ++T.h_nchild[q];
+        start = i;
+      }
+    }
+  }
+  T.ncell = (int)T.h_begin.size();
+  T.h_depth_begin.clear();
+  for (int q = 0; q < T.ncell; ++q)
+    while ((int)T.h_depth_begin.size() <= depth[q]) T.h_depth_begin.push_back(q);
+  T.ndepth = (int)T.h_depth_begin.size();
+  T.h_depth_begin.push_back(T.ncell);
+  T.h_leaf_cell.clear();
+  for (int q = 0; q < T.ncell; ++q)
+    if (T.h_nchild[q] == 0) T.h_leaf_cell.push_back(q);
+  T.nleaf = (int)T.h_leaf_cell.size();
+}
+
+template <typename V>
+void upload(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
+  d.alloc(std::max<size_t>(1, h.size()));
+  if (!h.empty()) BP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s));
+}
+
+// Interaction lists of every leaf under the batch acceptance criterion.
+void build_lists(Ctx& c, cudaStream_t s) {
+  Tree& T = c.tree;
+  const double theta = c.par.theta;
+  std::vector<int> leaf_of(T.ncell, -1);
+  for (int l = 0; l < T.nleaf; ++l) leaf_of[T.h_leaf_cell[l]] = l;
+  std::vector<int> fptr(T.nleaf + 1, 0), nptr(T.nleaf + 1, 0), flist, nlist;
+  std::vector<int4> blk;
+  std::vector<int> stack;
+  long long pairs = 0, fars = 0;
+  for (int l = 0; l < T.nleaf; ++l) {
+    const int ct = T.h_leaf_cell[l];
+    const double4 a = T.h_center[ct];
+    const int ntgt = T.h_end[ct] - T.h_begin[ct];
+    stack.assign(1, 0);
+    while (!stack.empty()) {
+      const int q = stack.back();
+      stack.pop_back();
+      const double4 b = T.h_center[q];
+      const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+      const double gap = std::sqrt(dx * dx + dy * dy + dz * dz) - a.w;
+      if (q != ct && gap > 0.0 && b.w < theta * gap) {
+        flist.push_back(q);
+        fars += ntgt;
+      } else if (T.h_nchild[q] == 0) {
+        nlist.push_back(leaf_of[q]);
+        pairs += (long long)ntgt * (T.h_end[q] - T.h_begin[q]) * c.K;
+      } else {
+        for (int k = T.h_nchild[q] - 1; k >= 0; --k) stack.push_back(T.h_child0[q] + k);
+      }
+    }
+    fptr[l + 1] = (int)flist.size();
+    nptr[l + 1] = (int)nlist.size();
+    for (int off = 0; off < ntgt; off += TB) blk.push_back(make_int4(l, T.h_begin[ct] + off, std::min(TB, ntgt - off), 0));
+  }
+  T.nblk = (int)blk.size();
+  T.pairs_per_matvec = pairs;
+  T.far_per_matvec = fars;
+  upload(T.far_ptr, fptr, s);
+  upload(T.far_list, flist, s);
+  upload(T.near_ptr, nptr, s);
+  upload(T.near_list, nlist, s);
+  upload(T.blk, blk, s);
+  T.theta_built = theta;
+}
+
+template <int P, typename Real>
+void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
+  Tree& T = c.tree;
+  constexpr int NC = MI<P>::NC;
+  if (T.mom_order != P || mom.n < (size_t)T.ncell * 2 * NC) {
+    mom.alloc((size_t)T.ncell * 2 * NC);
+    T.mom_order = P;
+  }
+  typedef typename Vec4<Real>::T R4;
+  const R4* str = nullptr;
+  if (sizeof(Real) == 4)
+    str = reinterpret_cast<const R4*>(c.str32.p);
+  else
+    str = reinterpret_cast<const R4*>(c.str64.p);
+  launch(leaf_moments_kernel<P, Real>, T.nleaf, TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
+         c.src64.p, str, mom.p);
+  for (int d = T.ndepth - 2; d >= 0; --d) {
+    const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
+    launch(m2m_kernel<P, Real>, cnt, TB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
+  }
+  const size_t need = (size_t)8 * c.n;
+  if (c.part.n < need) c.part.alloc(need);
+  const Real kappa = (Real)c.par.kappa;
+  const Real nk = (Real)(-c.par.kappa * 1.4426950408889634);
+  Ctx::Timed tm;
+  c.time_begin(0, s, tm);
+  c.stat_pairs += T.pairs_per_matvec;
+  launch(near_kernel<Real>, T.nblk, TB, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.begin.p, T.end.p,
+         T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, c.part.p);
+  c.time_end(s, tm);
+  Ctx::Timed tf;
+  c.time_begin(1, s, tf);
+  c.stat_far += T.far_per_matvec;
+  launch(far_kernel<P, Real>, T.nblk, TB, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
+         T.far_list.p, mom.p, kappa, c.n, c.part.p + 4 * (size_t)c.n);
+  c.time_end(s, tf);
+  c.part_splits = 2;
+}
+
+template <typename Real>
+void dispatch(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
+  switch (c.par.order) {
+    case 1: run_tree<1, Real>(c, mom, s); break;
+    case 2: run_tree<2, Real>(c, mom, s); break;
+    case 3: run_tree<3, Real>(c, mom, s); break;
+    case 4: run_tree<4, Real>(c, mom, s); break;
+    case 5: run_tree<5, Real>(c, mom, s); break;
+    case 6: run_tree<6, Real>(c, mom, s); break;
+    default: fail(BEMPOL_ERR_ARG, "treecode order must be in 1..6");
+  }
+}
+
+}  // namespace
+
 void build_tree(Ctx& c, cudaStream_t s) {
-  (void)s;
-  c.tree_ready = false;
+  Tree& T = c.tree;
+  build_topology(c);
+  upload(T.begin, T.h_begin, s);
+  upload(T.end, T.h_end, s);
+  upload(T.child0, T.h_child0, s);
+  upload(T.nchild, T.h_nchild, s);
+  upload(T.leaf_cell, T.h_leaf_cell, s);
+  T.center.alloc(T.ncell);
+  launch(cell_geometry_kernel, T.ncell, 256, 0, s, T.begin.p, T.end.p, c.K, c.src64.p, T.center.p);
+  T.h_center.resize(T.ncell);
+  BP_CUDA(cudaMemcpyAsync(T.h_center.data(), T.center.p, sizeof(double4) * T.ncell, cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  build_lists(c, s);
+  BP_CUDA(cudaStreamSynchronize(s));
+  T.mom_order = -1;
+  c.tree_ready = true;
 }
 
 void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s) {
-  (void)c;
-  (void)fp32;
-  (void)s;
-  fail(BEMPOL_ERR_ARG, "treecode operators are not available in this build");
+  if (!c.tree_ready) build_tree(c, s);
+  if (fp32)
+    dispatch<float>(c, c.tree.mom32, s);
+  else
+    dispatch<double>(c, c.tree.mom64, s);
 }
 
 }  // namespace bp
