@@ -82,7 +82,7 @@ def test_small_theta_is_the_direct_sum(mid):
     pr, mesh, A, s, xs = mid
     x = xs["random"]
     ref = A @ x
-    s.set_params(order=3, theta=0.02)
+    s.set_params(order=3, theta=1e-3)
     assert _relmax(_apply(s, x, "fp64_tree"), ref) < 1e-12
     assert s.sizes()["n_leaves"] > 8
     assert _relmax(_apply(s, x, "fp32_tree"), ref) < 2e-5
