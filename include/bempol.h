@@ -192,6 +192,23 @@ bempol_status bempol_rhs(bempol_ctx* c, const double* p, double* b, int op, void
  * panel (sites are validated to be far from the surface).  Enqueued on `stream`. */
 bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, int op, void* stream);
 
+/* Same result as bempol_site_reaction, for callers that cannot allow a device
+ * allocation during the call (the paper has no counterpart: this is a property
+ * of the library, not of the method).  bempol_site_reaction may cudaMalloc its
+ * partial-sum buffer when it grows; this variant calls no cudaMalloc, cudaFree or
+ * other allocating routine.  Use it where another runtime owns the device memory
+ * pool, or in loops that cannot take an allocation's implicit synchronisation.
+ *   x   device float64 [2N] (caller order), out device float64 [ns*10] as above.
+ * Limit: at most 26,214 sites (its partial sums live in one fixed 2 MiB
+ * file-scope device array that every GPU loading the library keeps until
+ * process exit); more sites give BEMPOL_ERR_ARG.  The array is shared by every
+ * call on every context: calls that overlap on the GPU race.  Each call writes
+ * every scratch entry it reads, so nothing carries over between calls.  The
+ * first call on a device looks up the array's device address (one-time set-up);
+ * make that first call before any stream capture.  Other errors as
+ * bempol_site_reaction.  Enqueued on `stream`. */
+bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const double* x, double* out, int op, void* stream);
+
 /* Multipole-multipole potentials at the sites (Eqs. Efield_mult,
  * second_derivative) with induced dipoles mu (device float64 [ns*3], NULL = 0):
  *   mode 0 (polarising field): permanent moments of the same polarisation group

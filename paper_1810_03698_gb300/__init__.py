@@ -73,6 +73,7 @@ def _load():
         "bempol_matvec": (i32, [vp, vp, vp, i32, vp]),
         "bempol_rhs": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_site_reaction_noalloc": (i32, [vp, vp, vp, i32, vp]),
         "bempol_multipole_field": (i32, [vp, vp, i32, vp, vp]),
         "bempol_sizes": (i32, [vp, C.POINTER(i64), C.POINTER(C.c_int32), C.POINTER(i64), C.POINTER(i64),
                                C.POINTER(i64), C.POINTER(i64)]),
@@ -224,6 +225,11 @@ class Solver:
     def site_reaction(self, x, out, op=OP_FP64_DIRECT, stream=None):
         self._chk(_lib.bempol_site_reaction(self._h, _ptr(x)[0], _ptr(out)[0], OP_NAMES.get(op, op),
                                             _stream(stream)))
+
+    def site_reaction_noalloc(self, x, out, op=OP_FP64_DIRECT, stream=None):
+        """Same as site_reaction, with no device allocation during the call (fixed scratch)."""
+        self._chk(_lib.bempol_site_reaction_noalloc(self._h, _ptr(x)[0], _ptr(out)[0], OP_NAMES.get(op, op),
+                                                    _stream(stream)))
 
     def multipole_field(self, out, mu=None, mode=0, stream=None):
         self._chk(_lib.bempol_multipole_field(self._h, _ptr(mu)[0], mode, _ptr(out)[0], _stream(stream)))

@@ -197,6 +197,8 @@ double energy_internal(Ctx& c, const double* react10, const double* mult10, cuda
 double sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
                   cudaStream_t s);
 void site_validation(Ctx& c, cudaStream_t s);
+bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool hessian, double* scratch,
+                           size_t cap, cudaStream_t s);
 // gmres.cu
 struct GmresOut {
   int iters = 0;

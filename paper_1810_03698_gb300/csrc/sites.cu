@@ -423,4 +423,38 @@ void site_validation(Ctx& c, cudaStream_t s) {
   }
 }
 
+// The reaction-field kernels with partial sums written to a caller-provided
+// scratch of `cap` doubles instead of the context's own buffer.  The number of
+// source splits is reduced until S * ns * 10 <= cap; every scratch entry the
+// reduction reads is written first by the partial kernel.  Returns false (and
+// launches nothing) when even one split does not fit.
+bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool hessian, double* scratch,
+                           size_t cap, cudaStream_t s) {
+  const int nsrc = c.n * c.K;
+  if ((size_t)c.ns * 10 > cap) return false;
+  int S = site_splits(c, c.ns, nsrc);
+  S = std::max(1, std::min<int>(S, (int)(cap / ((size_t)c.ns * 10))));
+  int per = cdiv(cdiv(nsrc, S), 256) * 256;
+  S = cdiv(nsrc, per);
+  strengths(c, x, fp32, s);
+  dim3 grid(cdiv(c.ns, 8), S);
+  if (fp32) {
+    if (hessian)
+      launch(site_reaction_kernel<float, float4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
+             nsrc, per, scratch);
+    else
+      launch(site_reaction_kernel<float, float4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
+             nsrc, per, scratch);
+  } else {
+    if (hessian)
+      launch(site_reaction_kernel<double, double4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
+             c.str64.p, nsrc, per, scratch);
+    else
+      launch(site_reaction_kernel<double, double4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
+             c.str64.p, nsrc, per, scratch);
+  }
+  launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, scratch, S, c.ns, out);
+  return true;
+}
+
 }  // namespace bp
