@@ -266,6 +266,20 @@ def main():
     value = total_ms / 1e3 / (args.steps * world)
     out = outs[-1]
 
+    # ---- one more step split into its phases (not part of the timed value)
+    def timed(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b)
+
+    phases = {"set_mesh_ms": timed(lambda: s.set_mesh(d_verts, d_tris)),
+              "set_sites_ms": timed(lambda: s.set_sites(*d_site, group=d_group)),
+              "solve_ms": timed(lambda: s.solve())}
+
     # ---- matvec alone: chosen operator and FP64 direct
     n = pr.n_panels
     K = pr.params.gauss_k
@@ -361,7 +375,7 @@ def main():
                   "scf_iters_vac": out["scf_iters_vac"], "gmres_iters": out["gmres_iters_total"],
                   "matvecs": out["matvecs_total"], "bem_solves": out["n_solves"],
                   "last_rel_residual": out["last_rel_residual"], "t_setup_ms": out["t_setup_ms"],
-                  "t_scf_ms": out["t_scf_ms"], "wall_s_timed_region": wall},
+                  "t_scf_ms": out["t_scf_ms"], "wall_s_timed_region": wall, "phases": phases},
         "matvec": {"op": args.op, "ms": mv_ms, "effective_ginter_s": inter / (mv_ms * 1e-3) / 1e9,
                    "performed_pairs": mv_stats["pair_interactions"] / max(1, args.matvec_reps),
                    "fp64_direct_ms": f64_ms,

@@ -261,6 +261,7 @@ bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, in
     DBuf<double> dv;
     to_device(dv, verts, 3 * (size_t)nv, where, s);
     build_geometry(*c, dv.p, ht.data(), s);
+    build_tree(*c, s);  // the octree also narrows the near-pair search
     build_near(*c, s);
     build_block_centers(*c, s);
     size_t len = 2 * (size_t)c->n;

@@ -184,8 +184,10 @@ void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, 
   BP_CUDA(cudaMemcpyAsync(h.data(), cen_c.p, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  c.max_area = 0.0;
   for (int t = 0; t < n; ++t) {
     if (!(h[t].w > 0.0)) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has zero or invalid area");
+    c.max_area = std::max(c.max_area, h[t].w);
     double v[3] = {h[t].x, h[t].y, h[t].z};
     for (int d = 0; d < 3; ++d) {
       lo[d] = std::min(lo[d], v[d]);

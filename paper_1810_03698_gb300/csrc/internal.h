@@ -92,9 +92,10 @@ struct Tree {
   DBuf<int> leaf_cell;                                   // leaf number -> cell
   // interaction lists per leaf (CSR): accepted far cells, near (direct) leaves
   DBuf<int> far_ptr, far_list, near_ptr, near_list;
-  // target blocks: (leaf number, first panel, count <= 128)
-  int nblk = 0;
-  DBuf<int4> blk;
+  // target blocks: (leaf number, first panel, count <= 128) for the far field and
+  // (leaf number, first panel, count <= 32) for the near field
+  int nblk = 0, nblk32 = 0, near_splits = 1;
+  DBuf<int4> blk, blk32;
   // multipole moments [ncell][2][NC]: single layer M_k, double layer D_k
   DBuf<float> mom32;
   DBuf<double> mom64;
@@ -129,6 +130,7 @@ struct Ctx {
   DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections
   int64_t nnz = 0;
   double bbox_lo[3], bbox_hi[3];
+  double max_area = 0.0;     // largest panel area (near-field search radius)
   std::vector<unsigned> h_morton;  // 30-bit Morton code of each internal panel (sorted)
   Tree tree;
   bool tree_ready = false;
@@ -189,6 +191,7 @@ void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s)
 // tree.cu
 void build_tree(Ctx& c, cudaStream_t s);
 void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
+void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells);
 // sites.cu
 void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s);
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s);

@@ -3,8 +3,8 @@
 // Near pairs: panel j is near collocation point i when |x_i - c_j|^2 < nf^2 * A_i
 // (nf = near_factor, A_i the area of the collocation point's own panel).  The
 // decision is taken in FP64 with explicitly rounded operations in the order
-// ((dx*dx + dy*dy) + dz*dz) < (nf*nf)*A_i; an FP32 pass with a safety margin only
-// skips pairs that are certainly far.
+// ((dx*dx + dy*dy) + dz*dz) < (nf*nf)*A_i; the octree only narrows the candidates
+// (leaves whose bounding spheres come within the largest threshold radius).
 //
 // For every near pair the FP64 correction (accurate integral - K-node sum) of the
 // four kernels V_L, K_L, V_Y, K_Y is stored, so that a matvec over all Gauss
@@ -71,41 +71,33 @@ __device__ __forceinline__ double dsq3(double dx, double dy, double dz) {
   return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
 }
 
-// pass 1/2: count, then fill, the near columns of every target (ascending j)
+// pass 1/2: count, then fill, the near columns of every target (ascending j).
+// One thread per target of a tree target block; it scans the panels of the
+// candidate leaves of its leaf (sorted by first panel, so j comes out ascending).
 template <bool FILL>
-__global__ void near_list_kernel(const double4* __restrict__ tgt64, const float4* __restrict__ tgt32, int n,
-                                 double nf2, float abs_margin, const int* __restrict__ ptr,
-                                 int* __restrict__ out) {
-  __shared__ float4 tile[256];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double4 xi = i < n ? tgt64[i] : make_double4(0, 0, 0, 0);
-  float4 xf = i < n ? tgt32[i] : make_float4(0, 0, 0, 0);
-  double thr = __dmul_rn(nf2, xi.w);
-  float rf = sqrtf((float)thr) + abs_margin;
-  float thrf = rf * rf;
+__global__ void near_list_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                 const int* __restrict__ cand_ptr, const int* __restrict__ cand,
+                                 const int* __restrict__ begin, const int* __restrict__ end, double nf2,
+                                 const int* __restrict__ ptr, int* __restrict__ out) {
+  const int4 B = blk[blockIdx.x];
+  if ((int)threadIdx.x >= B.z) return;
+  const int i = B.y + threadIdx.x;
+  const double4 xi = tgt64[i];
+  const double thr = __dmul_rn(nf2, xi.w);
   int cnt = 0;
-  int base = (FILL && i < n) ? ptr[i] : 0;
-  for (int t0 = 0; t0 < n; t0 += 256) {
-    int j = t0 + threadIdx.x;
-    tile[threadIdx.x] = j < n ? tgt32[j] : make_float4(3e30f, 3e30f, 3e30f, 0.f);
-    __syncthreads();
-    int lim = min(256, n - t0);
-    for (int k = 0; k < lim; ++k) {
-      float4 c = tile[k];
-      float dx = xf.x - c.x, dy = xf.y - c.y, dz = xf.z - c.z;
-      float d2 = dx * dx + dy * dy + dz * dz;
-      if (d2 <= thrf && i < n) {
-        double4 cj = tgt64[t0 + k];
-        double e2 = dsq3(__dsub_rn(xi.x, cj.x), __dsub_rn(xi.y, cj.y), __dsub_rn(xi.z, cj.z));
-        if (e2 < thr) {
-          if (FILL) out[base + cnt] = t0 + k;
-          ++cnt;
-        }
+  const int base = FILL ? ptr[i] : 0;
+  for (int e = cand_ptr[B.x]; e < cand_ptr[B.x + 1]; ++e) {
+    const int cl = cand[e];
+    for (int j = begin[cl]; j < end[cl]; ++j) {
+      const double4 cj = tgt64[j];
+      const double e2 = dsq3(__dsub_rn(xi.x, cj.x), __dsub_rn(xi.y, cj.y), __dsub_rn(xi.z, cj.z));
+      if (e2 < thr) {
+        if (FILL) out[base + cnt] = j;
+        ++cnt;
       }
     }
-    __syncthreads();
   }
-  if (!FILL && i < n) out[i] = cnt;
+  if (!FILL) out[i] = cnt;
 }
 
 __device__ void panel_exact(double xx, double xy, double xz, const double* __restrict__ v, bool self,
@@ -175,15 +167,24 @@ __device__ void panel_exact(double xx, double xy, double xz, const double* __res
   out[3] = acc3 * inv4pi;
 }
 
-__global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n,
+// one thread per near pair k (row found by binary search in the CSR pointers)
+__global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n, int nnz,
                                  const double4* __restrict__ tgt64, const double* __restrict__ vert9,
                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int K,
                                  double kappa, double4* __restrict__ corr) {
-  int i = blockIdx.x;  // one block per target row; threads over its near columns
-  if (i >= n) return;
-  int b = ptr[i], e = ptr[i + 1];
-  double4 x = tgt64[i];
-  for (int k = b + threadIdx.x; k < e; k += blockDim.x) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  int lo = 0, hi = n - 1;  // largest row i with ptr[i] <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (ptr[mid] <= k)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  const int i = lo;
+  const double4 x = tgt64[i];
+  {
     int j = col[k];
     double ex[4];
     panel_exact(x.x, x.y, x.z, vert9 + 9 * (size_t)j, i == j, kappa, ex);
@@ -220,17 +221,22 @@ void init_gauss_legendre() {
 
 void build_near(Ctx& c, cudaStream_t s) {
   const int n = c.n;
-  double nf2 = c.par.near_factor * c.par.near_factor;
-  // FP32 prefilter margin: coordinates are rounded to FP32 (relative 2^-24), so the
-  // FP32 distance is within a few ulps of max|coordinate| of the FP64 one.
-  double cmax = 0;
-  for (int d = 0; d < 3; ++d) cmax = std::max(cmax, std::max(std::fabs(c.bbox_lo[d]), std::fabs(c.bbox_hi[d])));
-  float margin = (float)(64.0 * cmax * 5.9604644775390625e-08 + 1e-30);
+  const double nf2 = c.par.near_factor * c.par.near_factor;
+  // candidate leaves from the tree: radius above every threshold near_factor*sqrt(A_i)
+  const double rmax = std::sqrt(nf2 * c.max_area) * (1.0 + 1e-9) + 1e-12;
+  std::vector<int> cptr, ccell;
+  tree_near_candidates(c, rmax, cptr, ccell);
+  DBuf<int> d_cptr, d_ccell;
+  d_cptr.alloc(cptr.size());
+  d_ccell.alloc(std::max<size_t>(1, ccell.size()));
+  BP_CUDA(cudaMemcpyAsync(d_cptr.p, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice, s));
+  if (!ccell.empty())
+    BP_CUDA(cudaMemcpyAsync(d_ccell.p, ccell.data(), sizeof(int) * ccell.size(), cudaMemcpyHostToDevice, s));
+  const Tree& T = c.tree;
   DBuf<int> cnt;
   cnt.alloc(n);
-  int tb = 256;
-  launch(near_list_kernel<false>, cdiv(n, tb), tb, 0, s, c.tgt64.p, c.tgt32.p, n, nf2, margin, nullptr, cnt.p);
-  BP_CHECK_LAUNCH();
+  launch(near_list_kernel<false>, T.nblk, 128, 0, s, T.blk.p, c.tgt64.p, d_cptr.p, d_ccell.p, T.begin.p, T.end.p,
+         nf2, nullptr, cnt.p);
   std::vector<int> h(n);
   BP_CUDA(cudaMemcpyAsync(h.data(), cnt.p, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
@@ -241,11 +247,10 @@ void build_near(Ctx& c, cudaStream_t s) {
   c.near_col.alloc(std::max<int64_t>(1, c.nnz));
   c.near_corr.alloc(std::max<int64_t>(1, c.nnz));
   BP_CUDA(cudaMemcpyAsync(c.near_ptr.p, ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
-  launch(near_list_kernel<true>, cdiv(n, tb), tb, 0, s, c.tgt64.p, c.tgt32.p, n, nf2, margin, c.near_ptr.p,
-                                                     c.near_col.p);
-  BP_CHECK_LAUNCH();
-  launch(near_corr_kernel, n, 32, 0, s, c.near_ptr.p, c.near_col.p, n, c.tgt64.p, c.vert9.p, c.src64.p, c.nrm64.p,
-                                    c.K, c.par.kappa, c.near_corr.p);
+  launch(near_list_kernel<true>, T.nblk, 128, 0, s, T.blk.p, c.tgt64.p, d_cptr.p, d_ccell.p, T.begin.p, T.end.p,
+         nf2, c.near_ptr.p, c.near_col.p);
+  launch(near_corr_kernel, cdiv(c.nnz, 128), 128, 0, s, c.near_ptr.p, c.near_col.p, n, (int)c.nnz, c.tgt64.p,
+         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.near_corr.p);
   BP_CHECK_LAUNCH();
   BP_CUDA(cudaStreamSynchronize(s));
 }

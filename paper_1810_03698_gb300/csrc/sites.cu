@@ -299,7 +299,7 @@ __global__ void sor_kernel(double* __restrict__ mu, const double4* __restrict__ 
 // ---------------------------------------------------------------- validation
 // flag[l] = 1 if site l is within the near radius of a panel centroid, 2 if outside the surface
 __global__ void site_check_kernel(const double4* __restrict__ spos, int ns, const double4* __restrict__ tgt64,
-                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int n,
+                                  const float4* __restrict__ src32, const double4* __restrict__ nrm64, int n,
                                   int K, double nf2, int* __restrict__ flag) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + warp;
@@ -311,14 +311,18 @@ __global__ void site_check_kernel(const double4* __restrict__ spos, int ns, cons
     double4 c = tgt64[j];
     double dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
     if (dx * dx + dy * dy + dz * dz < nf2 * c.w) near = 1;
+    // inside test in FP32: -K_L[1] is 1 inside and 0 outside, compared with 1/2
     double4 nj = nrm64[j];
+    const float nx = (float)nj.x, ny = (float)nj.y, nz = (float)nj.z;
+    float part = 0.f;
     for (int g = 0; g < K; ++g) {
-      double4 y = src64[(size_t)K * j + g];
-      double rx = p.x - y.x, ry = p.y - y.y, rz = p.z - y.z;
-      double r2 = rx * rx + ry * ry + rz * rz;
-      double ri = 1.0 / sqrt(r2);
-      dl += y.w * (nj.x * rx + nj.y * ry + nj.z * rz) * ri * ri * ri;
+      float4 y = src32[(size_t)K * j + g];
+      float rx = (float)p.x - y.x, ry = (float)p.y - y.y, rz = (float)p.z - y.z;
+      float r2 = rx * rx + ry * ry + rz * rz;
+      float ri = rsqrtf(r2);
+      part += y.w * (nx * rx + ny * ry + nz * rz) * ri * ri * ri;
     }
+    dl += (double)part;
   }
   for (int o = 16; o > 0; o >>= 1) {
     dl += __shfl_down_sync(0xffffffffu, dl, o);
@@ -410,7 +414,7 @@ void site_validation(Ctx& c, cudaStream_t s) {
   DBuf<int> flag;
   flag.alloc(c.ns);
   double nf2 = c.par.near_factor * c.par.near_factor;
-  launch(site_check_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.ns, c.tgt64.p, c.src64.p, c.nrm64.p, c.n, c.K,
+  launch(site_check_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.ns, c.tgt64.p, c.src32.p, c.nrm64.p, c.n, c.K,
                                                   nf2, flag.p);
   BP_CHECK_LAUNCH();
   std::vector<int> h(c.ns);

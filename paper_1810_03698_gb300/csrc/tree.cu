@@ -39,7 +39,10 @@ namespace bp {
 
 namespace {
 
-constexpr int TB = 128;      // targets per block (a leaf chunk)
+constexpr int TB = 128;      // threads per block of the moment kernels
+constexpr int TBT = 128;     // targets per block of the near/far kernels (up to four warps of one
+                             // leaf); warps with no target skip the arithmetic and only help
+                             // stage shared data, so only the last warp of a leaf has idle lanes
 constexpr int MAXP = 6;      // highest Taylor order compiled
 
 // ---------------------------------------------------------------- multi-index tables
@@ -284,17 +287,26 @@ __global__ void __launch_bounds__(TB) m2m_kernel(int first_cell, const int* __re
 }
 
 // ---------------------------------------------------------------- far field
-// One (target, cell) interaction: Laplace coefficients a_k, then Yukawa a_k, b_k,
-// each dotted with the cell's single-layer (M) and double-layer (Dm) moments.
-// Fully unrolled for a compile-time order, so every table index is a constant.
+// One (target, cell) interaction of one kernel: the Laplace coefficients a_k, or the
+// Yukawa a_k with their companions b_k, each dotted with the cell's single-layer (M)
+// and double-layer (Dm) moments.  Fully unrolled for a compile-time order, so every
+// table index is a constant; the per-order factors (2n-1)/(n|Delta|^2),
+// (n-1)/(n|Delta|^2), kappa/(n|Delta|^2) and kappa/n are formed once per order.
+// The two kernels run as separate launches so each body stays small.
 template <int P, typename Real>
-__device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict__ M, const Real* __restrict__ Dm,
-                                         Real kappa, Real& vl, Real& kl, Real& vy, Real& ky) {
+__device__ __forceinline__ void far_eval_laplace(const Real D[3], const Real* __restrict__ M,
+                                                 const Real* __restrict__ Dm, Real& v, Real& k) {
   constexpr MI<P> mi{};
   constexpr int NC = MI<P>::NC;
   const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
   const Real rinv = inv_sqrt(r2);
   const Real ir2 = rinv * rinv;
+  Real q1[P + 1], q2[P + 1];
+#pragma unroll
+  for (int n = 1; n <= P; ++n) {
+    q1[n] = ir2 * (Real)((2.0 * n - 1.0) / n);
+    q2[n] = ir2 * (Real)((n - 1.0) / n);
+  }
   Real a[NC];
   a[0] = rinv;
   Real sV = a[0] * M[0], sK = a[0] * Dm[0];
@@ -307,19 +319,35 @@ __device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict
       if (mi.m1[t][j] >= 0) s1 += D[j] * a[mi.m1[t][j]];
       if (mi.m2[t][j] >= 0) s2 += a[mi.m2[t][j]];
     }
-    a[t] = ((Real)(2 * n - 1) * s1 - (Real)(n - 1) * s2) * (ir2 * (Real)(1.0 / n));
+    a[t] = q1[n] * s1 - q2[n] * s2;
     sV += a[t] * M[t];
     sK += a[t] * Dm[t];
   }
-  vl += sV;
-  kl += sK;
-  const Real r = r2 * rinv;
-  const Real e = exp_neg(kappa * r);
+  v += sV;
+  k += sK;
+}
+
+template <int P, typename Real>
+__device__ __forceinline__ void far_eval_yukawa(const Real D[3], const Real* __restrict__ M,
+                                                const Real* __restrict__ Dm, Real kappa, Real& v, Real& k) {
+  constexpr MI<P> mi{};
+  constexpr int NC = MI<P>::NC;
+  const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
+  const Real rinv = inv_sqrt(r2);
+  const Real ir2 = rinv * rinv;
+  Real q1[P + 1], q2[P + 1], q3[P + 1], kn[P + 1];
+#pragma unroll
+  for (int n = 1; n <= P; ++n) {
+    q1[n] = ir2 * (Real)((2.0 * n - 1.0) / n);
+    q2[n] = ir2 * (Real)((n - 1.0) / n);
+    kn[n] = kappa * (Real)(1.0 / n);
+    q3[n] = kn[n] * ir2;
+  }
+  const Real e = exp_neg(kappa * (r2 * rinv));
   Real A[NC], Bc[NC];
   A[0] = e * rinv;
   Bc[0] = e;
-  sV = A[0] * M[0];
-  sK = A[0] * Dm[0];
+  Real sV = A[0] * M[0], sK = A[0] * Dm[0];
 #pragma unroll
   for (int t = 1; t < NC; ++t) {
     const int n = mi.ord[t];
@@ -335,20 +363,22 @@ __device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict
         s2b += Bc[mi.m2[t][j]];
       }
     }
-    Bc[t] = kappa * (Real)(1.0 / n) * (s1a - s2a);
-    A[t] = ((Real)(2 * n - 1) * s1a - (Real)(n - 1) * s2a + kappa * (s1b - s2b)) * (ir2 * (Real)(1.0 / n));
+    Bc[t] = kn[n] * (s1a - s2a);
+    A[t] = q1[n] * s1a - q2[n] * s2a + q3[n] * (s1b - s2b);
     sV += A[t] * M[t];
     sK += A[t] * Dm[t];
   }
-  vy += sV;
-  ky += sK;
+  v += sV;
+  k += sK;
 }
 
 constexpr int FCH = 8;  // far cells staged in shared memory per pass
 
-// One block per target block (<= 128 targets of one leaf); loops over the leaf's far cells.
-template <int P, typename Real>
-__global__ void __launch_bounds__(TB) far_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+// One block per target block (<= 128 targets of one leaf); loops over the leaf's far
+// cells.  YUK = 0 evaluates the Laplace kernel into rows (V_L, K_L), YUK = 1 the
+// Yukawa kernel into rows (V_Y, K_Y) of `out` ([4][n]).
+template <int P, typename Real, int YUK>
+__global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                  const int* __restrict__ leaf_cell, const double4* __restrict__ center,
                                                  const int* __restrict__ far_ptr, const int* __restrict__ far_list,
                                                  const Real* __restrict__ mom, Real kappa, int n,
@@ -368,11 +398,11 @@ __global__ void __launch_bounds__(TB) far_kernel(const int4* __restrict__ blk, c
     xr[1] = (Real)(x.y - ct.y);
     xr[2] = (Real)(x.z - ct.z);
   }
-  double aVL = 0, aKL = 0, aVY = 0, aKY = 0;
+  double aV = 0, aK = 0;
   const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
   for (int fb = f0; fb < f1; fb += FCH) {
     const int cnt = min(FCH, f1 - fb);
-    for (int q = threadIdx.x; q < cnt * 2 * NC; q += TB)
+    for (int q = threadIdx.x; q < cnt * 2 * NC; q += TBT)
       sm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
     if ((int)threadIdx.x < cnt) {
       double4 cc = center[far_list[fb + threadIdx.x]];
@@ -381,22 +411,23 @@ __global__ void __launch_bounds__(TB) far_kernel(const int4* __restrict__ blk, c
       so[threadIdx.x][2] = (Real)(ct.z - cc.z);
     }
     __syncthreads();
-    Real vl = 0, kl = 0, vy = 0, ky = 0;
-    for (int q = 0; q < cnt; ++q) {
-      const Real D[3] = {xr[0] + so[q][0], xr[1] + so[q][1], xr[2] + so[q][2]};
-      far_eval<P, Real>(D, sm[q], sm[q] + NC, kappa, vl, kl, vy, ky);
+    Real v = 0, k = 0;
+    if ((int)(threadIdx.x & ~31u) < B.z) {  // warp holds at least one target
+      for (int q = 0; q < cnt; ++q) {
+        const Real D[3] = {xr[0] + so[q][0], xr[1] + so[q][1], xr[2] + so[q][2]};
+        if (YUK)
+          far_eval_yukawa<P, Real>(D, sm[q], sm[q] + NC, kappa, v, k);
+        else
+          far_eval_laplace<P, Real>(D, sm[q], sm[q] + NC, v, k);
+      }
     }
-    aVL += (double)vl;
-    aKL += (double)kl;
-    aVY += (double)vy;
-    aKY += (double)ky;
+    aV += (double)v;
+    aK += (double)k;
     __syncthreads();
   }
   if (act) {
-    out[i] = aVL;
-    out[n + i] = aKL;
-    out[2 * n + i] = aVY;
-    out[3 * n + i] = aKY;
+    out[(2 * YUK) * (size_t)n + i] = aV;
+    out[(2 * YUK + 1) * (size_t)n + i] = aK;
   }
 }
 
@@ -433,9 +464,12 @@ __device__ __forceinline__ void pair_accum(const double x[3], double4 p, double4
   ky += t * (1.0 + kappa * R) * e;
 }
 
-// One block per target block; loops over the source leaves of the leaf's near list.
+// One warp per target block of <= 32 targets of one leaf.  The leaf's near list is
+// cut into gridDim.y consecutive pieces; piece s writes its partial sums to
+// out + s * 4n (no atomics: the combine kernel adds the pieces in order).
+constexpr int NTB = 32;
 template <typename Real>
-__global__ void __launch_bounds__(TB) near_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+__global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                   const int* __restrict__ leaf_cell,
                                                   const double4* __restrict__ center, const int* __restrict__ begin,
                                                   const int* __restrict__ end, const int* __restrict__ near_ptr,
@@ -444,8 +478,8 @@ __global__ void __launch_bounds__(TB) near_kernel(const int4* __restrict__ blk, 
                                                   const typename Vec4<Real>::T* __restrict__ str, Real kappa,
                                                   Real nk_log2e, int n, double* __restrict__ out) {
   typedef typename Vec4<Real>::T R4;
-  __shared__ R4 sp[TB];
-  __shared__ R4 ss[TB];
+  __shared__ R4 sp[NTB];
+  __shared__ R4 ss[NTB];
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
   const double4 ct = center[leaf_cell[leaf]];
@@ -458,28 +492,62 @@ __global__ void __launch_bounds__(TB) near_kernel(const int4* __restrict__ blk, 
     xr[1] = (Real)(x.y - ct.y);
     xr[2] = (Real)(x.z - ct.z);
   }
+  // The sources of up to NLC near leaves are streamed as one concatenated sequence,
+  // so every tile but the last of a pass is full and runs the unrolled loop.
+  constexpr int NLC = 64;
+  __shared__ int lb[NLC];       // first source index of each leaf of the pass
+  __shared__ int lc[NLC + 1];   // cumulative source counts
   double acc[4] = {0, 0, 0, 0};
-  for (int e = near_ptr[leaf]; e < near_ptr[leaf + 1]; ++e) {
-    const int cl = leaf_cell[near_list[e]];
-    const int s0 = begin[cl] * K, s1 = end[cl] * K;
-    for (int t0 = s0; t0 < s1; t0 += TB) {
+  const int nl = near_ptr[leaf + 1] - near_ptr[leaf];
+  const int e0 = near_ptr[leaf] + (int)(((long long)nl * blockIdx.y) / gridDim.y);
+  const int e1 = near_ptr[leaf] + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
+  for (int eb = e0; eb < e1; eb += NLC) {
+    const int cnt = min(NLC, e1 - eb);
+    __syncthreads();  // the previous pass is done with lb / lc
+    for (int q = threadIdx.x; q < cnt; q += NTB) {
+      const int cl = leaf_cell[near_list[eb + q]];
+      lb[q] = begin[cl] * K;
+      lc[q + 1] = (end[cl] - begin[cl]) * K;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      lc[0] = 0;
+      for (int q = 1; q <= cnt; ++q) lc[q] += lc[q - 1];
+    }
+    __syncthreads();
+    const int total = lc[cnt];
+    for (int t0 = 0; t0 < total; t0 += NTB) {
       const int j = t0 + threadIdx.x;
       R4 pz, sz;
       pz.x = pz.y = pz.z = pz.w = 0;
       sz = pz;
-      if (j < s1) {
-        double4 y = src64[j];
+      if (j < total) {
+        int lo = 0, hi = cnt - 1;  // largest q with lc[q] <= j
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (lc[mid] <= j)
+            lo = mid;
+          else
+            hi = mid - 1;
+        }
+        const int src = lb[lo] + (j - lc[lo]);
+        double4 y = src64[src];
         pz.x = (Real)(y.x - ct.x);
         pz.y = (Real)(y.y - ct.y);
         pz.z = (Real)(y.z - ct.z);
-        sz = str[j];
+        sz = str[src];
       }
       sp[threadIdx.x] = pz;
       ss[threadIdx.x] = sz;
       __syncthreads();
       Real vl = 0, kl = 0, vy = 0, ky = 0;
-      const int lim = min(TB, s1 - t0);
-      for (int k = 0; k < lim; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
+      if (t0 + NTB <= total) {
+#pragma unroll 8
+        for (int k = 0; k < NTB; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
+      } else {
+        const int lim = total - t0;
+        for (int k = 0; k < lim; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
+      }
       acc[0] += (double)vl;
       acc[1] += (double)kl;
       acc[2] += (double)vy;
@@ -488,10 +556,11 @@ __global__ void __launch_bounds__(TB) near_kernel(const int4* __restrict__ blk, 
     }
   }
   if (act) {
-    out[i] = acc[0];
-    out[n + i] = acc[1];
-    out[2 * n + i] = acc[2];
-    out[3 * n + i] = acc[3];
+    double* o = out + (size_t)blockIdx.y * 4 * n;
+    o[i] = acc[0];
+    o[n + i] = acc[1];
+    o[2 * n + i] = acc[2];
+    o[3 * n + i] = acc[3];
   }
 }
 
@@ -558,7 +627,7 @@ void build_lists(Ctx& c, cudaStream_t s) {
   std::vector<int> leaf_of(T.ncell, -1);
   for (int l = 0; l < T.nleaf; ++l) leaf_of[T.h_leaf_cell[l]] = l;
   std::vector<int> fptr(T.nleaf + 1, 0), nptr(T.nleaf + 1, 0), flist, nlist;
-  std::vector<int4> blk;
+  std::vector<int4> blk, blk32;
   std::vector<int> stack;
   long long pairs = 0, fars = 0;
   for (int l = 0; l < T.nleaf; ++l) {
@@ -584,9 +653,16 @@ void build_lists(Ctx& c, cudaStream_t s) {
     }
     fptr[l + 1] = (int)flist.size();
     nptr[l + 1] = (int)nlist.size();
-    for (int off = 0; off < ntgt; off += TB) blk.push_back(make_int4(l, T.h_begin[ct] + off, std::min(TB, ntgt - off), 0));
+    for (int off = 0; off < ntgt; off += TBT)
+      blk.push_back(make_int4(l, T.h_begin[ct] + off, std::min(TBT, ntgt - off), 0));
+    for (int off = 0; off < ntgt; off += 32)
+      blk32.push_back(make_int4(l, T.h_begin[ct] + off, std::min(32, ntgt - off), 0));
   }
   T.nblk = (int)blk.size();
+  T.nblk32 = (int)blk32.size();
+  // split each near-field block's source stream so the grid holds ~56 warps per SM
+  T.near_splits = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk32))));
+  upload(T.blk32, blk32, s);
   T.pairs_per_matvec = pairs;
   T.far_per_matvec = fars;
   upload(T.far_ptr, fptr, s);
@@ -617,23 +693,27 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
     launch(m2m_kernel<P, Real>, cnt, TB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
-  const size_t need = (size_t)8 * c.n;
+  const int S = T.near_splits;
+  const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
   const Real nk = (Real)(-c.par.kappa * 1.4426950408889634);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);
   c.stat_pairs += T.pairs_per_matvec;
-  launch(near_kernel<Real>, T.nblk, TB, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.begin.p, T.end.p,
-         T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, c.part.p);
+  launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+         T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, c.part.p);
   c.time_end(s, tm);
   Ctx::Timed tf;
   c.time_begin(1, s, tf);
   c.stat_far += T.far_per_matvec;
-  launch(far_kernel<P, Real>, T.nblk, TB, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
-         T.far_list.p, mom.p, kappa, c.n, c.part.p + 4 * (size_t)c.n);
+  double* far_out = c.part.p + (size_t)S * 4 * c.n;
+  launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
+         T.far_list.p, mom.p, kappa, c.n, far_out);
+  launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
+         T.far_list.p, mom.p, kappa, c.n, far_out);
   c.time_end(s, tf);
-  c.part_splits = 2;
+  c.part_splits = S + 1;
 }
 
 template <typename Real>
@@ -650,6 +730,37 @@ void dispatch(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Leaves that may hold a panel centroid within `rmax` of a centroid of leaf l: every
+// centroid lies inside its leaf's Gauss-node sphere, so a cell whose sphere is at
+// least rmax from the target leaf's sphere is pruned.  Candidates of each leaf are
+// sorted by their first panel, so scanning them in order visits panels in order.
+void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells) {
+  Tree& T = c.tree;
+  ptr.assign(T.nleaf + 1, 0);
+  cells.clear();
+  std::vector<int> stack, found;
+  for (int l = 0; l < T.nleaf; ++l) {
+    const int ct = T.h_leaf_cell[l];
+    const double4 a = T.h_center[ct];
+    found.clear();
+    stack.assign(1, 0);
+    while (!stack.empty()) {
+      const int q = stack.back();
+      stack.pop_back();
+      const double4 b = T.h_center[q];
+      const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+      if (std::sqrt(dx * dx + dy * dy + dz * dz) - a.w - b.w >= rmax) continue;
+      if (T.h_nchild[q] == 0)
+        found.push_back(q);
+      else
+        for (int k = 0; k < T.h_nchild[q]; ++k) stack.push_back(T.h_child0[q] + k);
+    }
+    std::sort(found.begin(), found.end(), [&](int u, int v) { return T.h_begin[u] < T.h_begin[v]; });
+    cells.insert(cells.end(), found.begin(), found.end());
+    ptr[l + 1] = (int)cells.size();
+  }
+}
 
 void build_tree(Ctx& c, cudaStream_t s) {
   Tree& T = c.tree;
