@@ -24,51 +24,53 @@ constexpr int DOT_BLOCKS = 256;
 constexpr int DOT_TPB = 256;
 constexpr int MAXV = 16;  // basis vectors handled per multi-dot pass
 
-// partial[b][k] = sum over this block's slice of V_k . w  (k < nv)
-__global__ void __launch_bounds__(DOT_TPB) multidot_partial(const double* __restrict__ V, size_t ld, int nv,
-                                                            const double* __restrict__ w, int len,
-                                                            double* __restrict__ partial) {
+// out[k] = V_k . w for k < nv, in one launch.  Each block writes its partial sums
+// partial[b][k] (chunks of MAXV vectors per pass over its slice); the last block to
+// finish (atomic ticket) adds the partials in block order, so the result does not
+// depend on scheduling, and resets the ticket for the next call.
+__global__ void __launch_bounds__(DOT_TPB) multidot_kernel(const double* __restrict__ V, size_t ld, int nv,
+                                                           const double* __restrict__ w, int len,
+                                                           double* __restrict__ partial, int ldp,
+                                                           unsigned* __restrict__ ticket, double* __restrict__ out,
+                                                           int accumulate) {
   __shared__ double sh[MAXV][DOT_TPB / 32];
-  double acc[MAXV];
-#pragma unroll
-  for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
-  for (int i = blockIdx.x * DOT_TPB + threadIdx.x; i < len; i += gridDim.x * DOT_TPB) {
-    double wi = w[i];
-#pragma unroll
-    for (int k = 0; k < MAXV; ++k)
-      if (k < nv) acc[k] += V[(size_t)k * ld + i] * wi;
-  }
+  __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nv; k0 += MAXV) {
+    const int cnt = min(MAXV, nv - k0);
+    double acc[MAXV];
 #pragma unroll
-  for (int k = 0; k < MAXV; ++k) {
-    double v = acc[k];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) sh[k][warp] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < nv) {
-    double v = 0.0;
-    for (int wv = 0; wv < DOT_TPB / 32; ++wv) v += sh[threadIdx.x][wv];
-    partial[(size_t)blockIdx.x * MAXV + threadIdx.x] = v;
-  }
-}
-
-// out[k] = sum_b partial[b][k] (fixed order), optionally accumulated (out[k] += ...)
-__global__ void multidot_reduce(const double* __restrict__ partial, int nb, int nv, double* __restrict__ out,
-                                int accumulate) {
-  __shared__ double sh[DOT_TPB];
-  for (int k = 0; k < nv; ++k) {
-    double v = 0.0;
-    for (int b = threadIdx.x; b < nb; b += DOT_TPB) v += partial[(size_t)b * MAXV + k];
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int s = DOT_TPB / 2; s > 0; s >>= 1) {
-      if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-      __syncthreads();
+    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
+    for (int i = blockIdx.x * DOT_TPB + threadIdx.x; i < len; i += gridDim.x * DOT_TPB) {
+      const double wi = w[i];
+#pragma unroll
+      for (int k = 0; k < MAXV; ++k)
+        if (k < cnt) acc[k] += V[(size_t)(k0 + k) * ld + i] * wi;
     }
-    if (threadIdx.x == 0) out[k] = accumulate ? out[k] + sh[0] : sh[0];
+#pragma unroll
+    for (int k = 0; k < MAXV; ++k) {
+      double v = acc[k];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < cnt) {
+      double v = 0.0;
+      for (int wv = 0; wv < DOT_TPB / 32; ++wv) v += sh[threadIdx.x][wv];
+      partial[(size_t)blockIdx.x * ldp + k0 + threadIdx.x] = v;
+    }
     __syncthreads();
   }
+  __threadfence();
+  if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!last) return;
+  for (int k = threadIdx.x; k < nv; k += DOT_TPB) {
+    double v = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(partial + (size_t)b * ldp + k);
+    out[k] = accumulate ? out[k] + v : v;
+  }
+  if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // w -= sum_k V_k h_k   (k < nv)
@@ -156,16 +158,14 @@ struct Work {
   double* H;
   int ldh;
   double *cs, *sn, *g, *y, *hcol, *nrm2, *res, *partial;
+  int ldp;
+  unsigned* ticket;
 };
 
 void multidot(Ctx& c, const Work& w, const double* V, int nv, const double* vec, int len, double* out,
               bool accumulate, cudaStream_t s) {
-  for (int k0 = 0; k0 < nv; k0 += MAXV) {
-    int cnt = std::min(MAXV, nv - k0);
-    launch(multidot_partial, DOT_BLOCKS, DOT_TPB, 0, s, V + (size_t)k0 * w.ld, w.ld, cnt, vec, len, w.partial);
-    launch(multidot_reduce, 1, DOT_TPB, 0, s, w.partial, DOT_BLOCKS, cnt, out + k0, accumulate ? 1 : 0);
-  }
-  BP_CHECK_LAUNCH();
+  launch(multidot_kernel, DOT_BLOCKS, DOT_TPB, 0, s, V, w.ld, nv, vec, len, w.partial, w.ldp, w.ticket, out,
+         accumulate ? 1 : 0);
   (void)c;
 }
 
@@ -184,7 +184,12 @@ Work workspace(Ctx& c) {
     c.gm_small.alloc(4 * (size_t)(m + 2) + 8);
     c.gm_m = m;
   }
-  if (c.gm_dots.n < (size_t)DOT_BLOCKS * MAXV + m + 2) c.gm_dots.alloc((size_t)DOT_BLOCKS * MAXV + m + 2);
+  const size_t ndots = (size_t)DOT_BLOCKS * (m + 2) + m + 2;
+  if (c.gm_dots.n < ndots) c.gm_dots.alloc(ndots);
+  if (!c.gm_ticket.p) {
+    c.gm_ticket.alloc(1);
+    BP_CUDA(cudaMemset(c.gm_ticket.p, 0, sizeof(unsigned)));
+  }
   Work w;
   w.V = c.gm_V.p;
   w.ld = len;
@@ -198,7 +203,9 @@ Work workspace(Ctx& c) {
   w.nrm2 = sm + 4 * (m + 2);
   w.res = w.nrm2 + 1;
   w.partial = c.gm_dots.p;
-  w.hcol = c.gm_dots.p + (size_t)DOT_BLOCKS * MAXV;
+  w.ldp = m + 2;
+  w.ticket = c.gm_ticket.p;
+  w.hcol = c.gm_dots.p + (size_t)DOT_BLOCKS * (m + 2);
   return w;
 }
 

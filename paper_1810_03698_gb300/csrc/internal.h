@@ -100,6 +100,9 @@ struct Tree {
   DBuf<float> mom32;
   DBuf<double> mom64;
   int mom_order = -1;
+  // FP32 Gauss-node positions relative to the centre of their own leaf (x, y, z, 0)
+  DBuf<float4> src_rel32;
+  int m2m_min_depth = 0;  // shallowest depth whose cells appear in a far list
   double theta_built = -1.0;
   long long pairs_per_matvec = 0, far_per_matvec = 0;
 };
@@ -149,6 +152,7 @@ struct Ctx {
   int part_splits = 0;
   DBuf<double> site_part;    // site partial sums
   DBuf<double> gm_V, gm_H, gm_small, gm_dots;
+  DBuf<unsigned> gm_ticket;  // last-block ticket of the multi-dot kernel (kept at 0 between calls)
   DBuf<double> vec_a, vec_b, vec_c, vec_d;   // [2n] scratch vectors
   DBuf<double> scal;         // device scalars
   double* h_pinned = nullptr;  // pinned host scalars

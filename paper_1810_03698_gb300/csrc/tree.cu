@@ -175,6 +175,20 @@ __global__ void cell_geometry_kernel(const int* __restrict__ begin, const int* _
   if (threadIdx.x == 0) center[cidx] = make_double4(cx, cy, cz, sqrt(sh[0][0]));
 }
 
+// FP32 position of every Gauss node relative to the centre of its leaf (FP64 subtraction)
+__global__ void src_rel_kernel(const int* __restrict__ leaf_cell, int nleaf, const int* __restrict__ begin,
+                               const int* __restrict__ end, const double4* __restrict__ center, int K,
+                               const double4* __restrict__ src64, float4* __restrict__ rel) {
+  const int l = blockIdx.x;
+  if (l >= nleaf) return;
+  const int cl = leaf_cell[l];
+  const double4 c = center[cl];
+  for (int j = begin[cl] * K + threadIdx.x; j < end[cl] * K; j += blockDim.x) {
+    const double4 y = src64[j];
+    rel[j] = make_float4((float)(y.x - c.x), (float)(y.y - c.y), (float)(y.z - c.z), 0.f);
+  }
+}
+
 // ---------------------------------------------------------------- moments
 // Leaf moments from the sources: one block per leaf, thread o owns moments o, o + TB, ...
 template <int P, typename Real>
@@ -476,7 +490,8 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
                                                   const int* __restrict__ near_list, int K,
                                                   const double4* __restrict__ src64,
                                                   const typename Vec4<Real>::T* __restrict__ str, Real kappa,
-                                                  Real nk_log2e, int n, double* __restrict__ out) {
+                                                  Real nk_log2e, int n, const float4* __restrict__ src_rel,
+                                                  double* __restrict__ out) {
   typedef typename Vec4<Real>::T R4;
   __shared__ R4 sp[NTB];
   __shared__ R4 ss[NTB];
@@ -497,6 +512,7 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
   constexpr int NLC = 64;
   __shared__ int lb[NLC];       // first source index of each leaf of the pass
   __shared__ int lc[NLC + 1];   // cumulative source counts
+  __shared__ float lo3[NLC][3]; // FP32 offset (source-leaf centre - target-leaf centre)
   double acc[4] = {0, 0, 0, 0};
   const int nl = near_ptr[leaf + 1] - near_ptr[leaf];
   const int e0 = near_ptr[leaf] + (int)(((long long)nl * blockIdx.y) / gridDim.y);
@@ -508,6 +524,10 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
       const int cl = leaf_cell[near_list[eb + q]];
       lb[q] = begin[cl] * K;
       lc[q + 1] = (end[cl] - begin[cl]) * K;
+      const double4 cs = center[cl];
+      lo3[q][0] = (float)(cs.x - ct.x);
+      lo3[q][1] = (float)(cs.y - ct.y);
+      lo3[q][2] = (float)(cs.z - ct.z);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -531,10 +551,18 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
             hi = mid - 1;
         }
         const int src = lb[lo] + (j - lc[lo]);
-        double4 y = src64[src];
-        pz.x = (Real)(y.x - ct.x);
-        pz.y = (Real)(y.y - ct.y);
-        pz.z = (Real)(y.z - ct.z);
+        if constexpr (sizeof(Real) == 4) {
+          // leaf-relative FP32 position plus the leaf-pair offset: no FP64 work per source
+          const float4 r = src_rel[src];
+          pz.x = r.x + lo3[lo][0];
+          pz.y = r.y + lo3[lo][1];
+          pz.z = r.z + lo3[lo][2];
+        } else {
+          const double4 y = src64[src];
+          pz.x = (Real)(y.x - ct.x);
+          pz.y = (Real)(y.y - ct.y);
+          pz.z = (Real)(y.z - ct.z);
+        }
         sz = str[src];
       }
       sp[threadIdx.x] = pz;
@@ -658,6 +686,29 @@ void build_lists(Ctx& c, cudaStream_t s) {
     for (int off = 0; off < ntgt; off += 32)
       blk32.push_back(make_int4(l, T.h_begin[ct] + off, std::min(32, ntgt - off), 0));
   }
+  // largest blocks first: the grids are only one or two waves deep, so launching the
+  // long blocks early shortens the tail (each block's result does not depend on order)
+  std::vector<long long> far_work(T.nleaf), near_work(T.nleaf, 0);
+  for (int l = 0; l < T.nleaf; ++l) {
+    far_work[l] = fptr[l + 1] - fptr[l];
+    for (int e = nptr[l]; e < nptr[l + 1]; ++e) {
+      const int q = T.h_leaf_cell[nlist[e]];
+      near_work[l] += T.h_end[q] - T.h_begin[q];
+    }
+  }
+  std::stable_sort(blk.begin(), blk.end(), [&](const int4& u, const int4& v) {
+    return far_work[u.x] * u.z > far_work[v.x] * v.z;
+  });
+  std::stable_sort(blk32.begin(), blk32.end(), [&](const int4& u, const int4& v) {
+    return near_work[u.x] * u.z > near_work[v.x] * v.z;
+  });
+  // shallowest tree depth that holds an accepted cell: moments above it are never read
+  T.m2m_min_depth = T.ndepth;
+  for (int q : flist) {
+    int d = 0;
+    while (d + 1 < T.ndepth && T.h_depth_begin[d + 1] <= q) ++d;
+    T.m2m_min_depth = std::min(T.m2m_min_depth, d);
+  }
   T.nblk = (int)blk.size();
   T.nblk32 = (int)blk32.size();
   // split each near-field block's source stream so the grid holds ~56 warps per SM
@@ -689,7 +740,7 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str64.p);
   launch(leaf_moments_kernel<P, Real>, T.nleaf, TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
          c.src64.p, str, mom.p);
-  for (int d = T.ndepth - 2; d >= 0; --d) {
+  for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
     launch(m2m_kernel<P, Real>, cnt, TB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
@@ -702,7 +753,8 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   c.time_begin(0, s, tm);
   c.stat_pairs += T.pairs_per_matvec;
   launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-         T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, c.part.p);
+         T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
+         c.part.p);
   c.time_end(s, tm);
   Ctx::Timed tf;
   c.time_begin(1, s, tf);
@@ -774,6 +826,9 @@ void build_tree(Ctx& c, cudaStream_t s) {
   launch(cell_geometry_kernel, T.ncell, 256, 0, s, T.begin.p, T.end.p, c.K, c.src64.p, T.center.p);
   T.h_center.resize(T.ncell);
   BP_CUDA(cudaMemcpyAsync(T.h_center.data(), T.center.p, sizeof(double4) * T.ncell, cudaMemcpyDeviceToHost, s));
+  T.src_rel32.alloc((size_t)c.K * c.n);
+  launch(src_rel_kernel, T.nleaf, 128, 0, s, T.leaf_cell.p, T.nleaf, T.begin.p, T.end.p, T.center.p, c.K, c.src64.p,
+         T.src_rel32.p);
   BP_CUDA(cudaStreamSynchronize(s));
   build_lists(c, s);
   BP_CUDA(cudaStreamSynchronize(s));
