@@ -6,6 +6,8 @@ workload number below, so the oracle and the CUDA path see identical inputs.
   1  sphere R=4 A, icosphere subdivision 3 (1,280 panels), two fixed sites
   2  sphere R=10 A, subdivision 5 (20,480 panels), 100 random sites in r <= 8 A
   3  bumpy star surface R=14 A, subdivision 6 (81,920 panels), 2,000 sites
+  4  16 triples (A, B, AB) of bumpy bodies, subdivisions 3-6, R 6-14 A; in AB the
+     two bodies are 3 A apart along x and share one solvent
   5  bumpy star surface R=24 A, subdivision 7 (327,680 panels), 10,000 sites
 
 The paper's own workloads are protein surfaces meshed with msms at 4 vertices
@@ -51,6 +53,7 @@ class Problem:
     sites: Sites
     params: Params
     meta: dict = field(default_factory=dict)
+    panel_body: np.ndarray = None   # [N] int32 body of each panel (None: one body)
 
     @property
     def n_panels(self) -> int:
@@ -133,6 +136,60 @@ def small_bumpy(subdiv: int = 3, n_sites: int = 40, radius: float = 8.0, seed_in
     """A small bumpy case for quick parity runs (several tiles, ragged tail)."""
     pr = bumpy_problem(radius, subdiv, n_sites, seed_index)
     return pr
+
+
+def two_body(a: Problem, b: Problem, gap: float = 3.0) -> Problem:
+    """The complex AB of two bodies in one solvent (Sec. "Calculation of the binding
+    energy"): B is moved along +x until the slab between A's largest x and B's smallest
+    x is ``gap`` wide, so no point of one surface is closer than ``gap`` to the other.
+    Panels and sites keep their order (A first); B's sites get body 1 and their own
+    polarisation groups."""
+    shift = float(a.verts[:, 0].max() - b.verts[:, 0].min() + gap)
+    off = np.array([shift, 0.0, 0.0])
+    verts = np.vstack([a.verts, b.verts + off])
+    tris = np.vstack([a.tris, b.tris + a.verts.shape[0]]).astype(a.tris.dtype)
+    sa, sb = a.sites, b.sites
+    sites = Sites(pos=np.vstack([sa.pos, sb.pos + off]), q=np.concatenate([sa.q, sb.q]),
+                  d=np.vstack([sa.d, sb.d]), Q=np.concatenate([sa.Q, sb.Q]),
+                  alpha=np.concatenate([sa.alpha, sb.alpha]),
+                  group=np.concatenate([sa.group, sb.group + int(sa.group.max()) + 1]).astype(np.int32),
+                  body=np.concatenate([np.zeros(sa.n, np.int32), np.ones(sb.n, np.int32)]))
+    body = np.concatenate([np.zeros(a.n_panels, np.int32), np.ones(b.n_panels, np.int32)])
+    return Problem(f"complex[{a.name}+{b.name}]", verts, tris, sites, a.params,
+                   meta={"kind": "complex", "shift": shift, "gap": gap}, panel_body=body)
+
+
+# Sites per body of the binding workload: 0.06 per A^3 of the ball of radius R,
+# clamped to [50, 2000].  Coarse meshes need a wider site-free shell (2 sqrt(A_max)),
+# which config 3's density of 0.17 per A^3 would not leave room for.
+TRIPLE_SITE_DENSITY = 0.06
+
+
+def config4(n_triples: int = 16, subdivs=(3, 4, 5, 6), radius=(6.0, 14.0)):
+    """Binding workload: ``n_triples`` triples (A, B, AB).  Per body: subdivision uniform
+    over ``subdivs``, R ~ U(radius), sites proportional to the volume; AB puts B 3 A
+    from A along x.  Returns a list of (A, B, AB)."""
+    rng = np.random.default_rng(SEED_BASE + 4)
+    out = []
+    for t in range(n_triples):
+        pair = []
+        for k in range(2):
+            sub = int(rng.choice(np.asarray(subdivs)))
+            R = float(rng.uniform(*radius))
+            ns = int(np.clip(round(TRIPLE_SITE_DENSITY * 4.0 / 3.0 * np.pi * R ** 3), 50, 2000))
+            pr = bumpy_problem(R, sub, ns, 4000 + 2 * t + k, alpha_range=DENSE_ALPHA)
+            pr.params = Params(gmres_tol=1e-6, scf_tol=1e-6, theta=0.5, order=5)
+            pair.append(pr)
+        out.append((pair[0], pair[1], two_body(pair[0], pair[1])))
+    return out
+
+
+def small_triple(seed_index: int = 401, subdiv: int = 2, radius: float = 6.0, n_sites: int = 12,
+                 gap: float = 3.0):
+    """A triple small enough for the dense oracle (two bodies of 20 * 4^subdiv panels)."""
+    a = bumpy_problem(radius, subdiv, n_sites, seed_index)
+    b = bumpy_problem(radius * 0.8, subdiv, max(2, n_sites // 2), seed_index + 1)
+    return a, b, two_body(a, b, gap)
 
 
 def with_params(pr: Problem, **kw) -> Problem:

@@ -34,17 +34,25 @@ class Mesh:
     wgauss: np.ndarray     # [N, K]
     near_ptr: np.ndarray
     near_cols: np.ndarray
+    body: np.ndarray       # [N] body of each panel (several closed surfaces in one solvent)
 
     @property
     def n(self):
         return int(self.tris.shape[0])
 
+    def same_body(self, rows, cols):
+        return self.body[rows] == self.body[cols]
 
-def build_mesh(verts, tris, gauss_k=4, near_factor=2.0) -> Mesh:
+
+def build_mesh(verts, tris, gauss_k=4, near_factor=2.0, body=None) -> Mesh:
+    """Panels, Gauss nodes and near pairs.  With several bodies (closed surfaces
+    enclosing separate solute cavities, Sec. "Calculation of the binding energy"),
+    ``body`` gives each panel's body."""
     cen, normal, area = geometry.panel_geometry(verts, tris)
     y, w = geometry.gauss_points(verts, tris, gauss_k)
     ptr, cols = geometry.near_pairs(cen, area, near_factor)
-    return Mesh(verts, tris, cen, normal, area, y, w, ptr, cols)
+    b = np.zeros(tris.shape[0], dtype=np.int32) if body is None else np.asarray(body, dtype=np.int32)
+    return Mesh(verts, tris, cen, normal, area, y, w, ptr, cols, b)
 
 
 def near_rows_cols(mesh: Mesh):
@@ -71,7 +79,10 @@ def near_correction(mesh: Mesh, kappa: float):
     """Accurate minus K-node value of each near pair (what a Gauss-node matvec must add)."""
     ex = near_exact(mesh, kappa)
     kp = near_kpoint(mesh, kappa)
-    return tuple(e - k for e, k in zip(ex, kp))
+    vl, kl, vy, ky = (e - k for e, k in zip(ex, kp))
+    rows, cols = near_rows_cols(mesh)
+    same = mesh.same_body(rows, cols)   # the Laplace layers do not couple bodies
+    return np.where(same, vl, 0.0), np.where(same, kl, 0.0), vy, ky
 
 
 def assemble_layers(mesh: Mesh, kappa: float, row_chunk: int = 256):
@@ -99,6 +110,11 @@ def assemble_layers(mesh: Mesh, kappa: float, row_chunk: int = 256):
     KL[rows, cols] = kl
     VY[rows, cols] = vy
     KY[rows, cols] = ky
+    # Several bodies: the interior (Laplace) representation of a body integrates over
+    # its own surface only; the solvent (Yukawa) one over every surface.
+    cross = mesh.body[:, None] != mesh.body[None, :]
+    VL[cross] = 0.0
+    KL[cross] = 0.0
     return VL, KL, VY, KY
 
 
@@ -149,6 +165,9 @@ def matvec_rows(mesh: Mesh, x: np.ndarray, rows: np.ndarray, eps_in, eps_out, ka
                                    mesh.verts[tv[:, 0]], mesh.verts[tv[:, 1]], mesh.verts[tv[:, 2]],
                                    kappa, self_panel=(cols == i))
         vl[cols], kl[cols], vy[cols], ky[cols] = ex
+        other = mesh.body != mesh.body[i]
+        vl[other] = 0.0
+        kl[other] = 0.0
         y1[t] = 0.5 * phi[i] + kl @ phi - vl @ psi
         y2[t] = 0.5 * phi[i] - ky @ phi + (eps_in / eps_out) * (vy @ psi)
     return y1, y2

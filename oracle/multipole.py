@@ -118,9 +118,11 @@ def damped_tensors(R: np.ndarray, l3, l5, l7):
 # right-hand side
 # ----------------------------------------------------------------------------
 
-def rhs(points: np.ndarray, pos, q, p, Q, eps_in: float, chunk: int = 2048):
+def rhs(points: np.ndarray, pos, q, p, Q, eps_in: float, chunk: int = 2048, point_body=None, site_body=None):
     """Eq. (rhs_multipole) at ``points`` [N, 3]:
-    1/(4 pi eps1) sum_k [ q_k/R + p_k . R / R^3 + Q_k : R R / (2 R^5) ], R = x - r_k."""
+    1/(4 pi eps1) sum_k [ q_k/R + p_k . R / R^3 + Q_k : R R / (2 R^5) ], R = x - r_k.
+    With bodies given, a point sees only the sites of its own body (each cavity's
+    interior representation holds its own charges)."""
     n = points.shape[0]
     out = np.zeros(n)
     for s in range(0, n, chunk):
@@ -132,6 +134,8 @@ def rhs(points: np.ndarray, pos, q, p, Q, eps_in: float, chunk: int = 2048):
         t = t + np.sum(p[None, :, :] * R, axis=2) / (r2 * r)
         t = t + np.einsum("mkij,mki,mkj->mk", np.broadcast_to(Q[None], (e - s,) + Q.shape), R, R) \
             / (2.0 * r2 * r2 * r)
+        if point_body is not None:
+            t = np.where(point_body[s:e, None] == site_body[None, :], t, 0.0)
         out[s:e] = np.sum(t, axis=1)
     return out / (FOUR_PI * eps_in)
 
@@ -140,18 +144,21 @@ def rhs(points: np.ndarray, pos, q, p, Q, eps_in: float, chunk: int = 2048):
 # reaction potential and its derivatives at the sites (Eqs. pot_solvent, Efield_solv, ddphi)
 # ----------------------------------------------------------------------------
 
-def reaction_at_sites(mesh, phi: np.ndarray, psi: np.ndarray, pos: np.ndarray, chunk: int = 64):
+def reaction_at_sites(mesh, phi: np.ndarray, psi: np.ndarray, pos: np.ndarray, chunk: int = 64,
+                      site_body=None):
     """phi_solv = -K_L(phi) + V_L(psi) at the sites, with gradient and Hessian.
 
     Sites are far from every panel, so the panel integrals use the K-node rule:
     node g of panel j carries a charge m = w_g A_j psi_j and a dipole
     d = w_g A_j phi_j n_j, and 4 pi phi_solv = sum_g [ m T0 + d . T1 ](r - y_g).
+    With several bodies a site sees only the surface of its own body.
     Returns (phi [Ns], grad [Ns, 3], hess [Ns, 3, 3]).
     """
     y = mesh.ygauss.reshape(-1, 3)
     k = mesh.ygauss.shape[1]
     m = (mesh.wgauss * psi[:, None]).reshape(-1)
     d = ((mesh.wgauss * phi[:, None])[:, :, None] * mesh.normal[:, None, :]).reshape(-1, 3)
+    node_body = np.repeat(mesh.body, k)
     ns = pos.shape[0]
     pot = np.zeros(ns)
     grad = np.zeros((ns, 3))
@@ -159,12 +166,13 @@ def reaction_at_sites(mesh, phi: np.ndarray, psi: np.ndarray, pos: np.ndarray, c
     for s in range(0, ns, chunk):
         e = min(ns, s + chunk)
         for l in range(s, e):
-            R = pos[l][None, :] - y
+            sel = slice(None) if site_body is None else (node_body == site_body[l])
+            R = pos[l][None, :] - y[sel]
             T0, T1, T2, T3 = t_tensors(R, 3)
-            pot[l] = np.sum(m * T0) + np.sum(d * T1)
-            grad[l] = m @ T1 + np.einsum("gi,gik->k", d, T2)
-            hess[l] = np.einsum("g,gkl->kl", m, T2) + np.einsum("gi,gikl->kl", d, T3)
-    del k
+            ml, dl = m[sel], d[sel]
+            pot[l] = np.sum(ml * T0) + np.sum(dl * T1)
+            grad[l] = ml @ T1 + np.einsum("gi,gik->k", dl, T2)
+            hess[l] = np.einsum("g,gkl->kl", ml, T2) + np.einsum("gi,gikl->kl", dl, T3)
     return pot / FOUR_PI, grad / FOUR_PI, hess / FOUR_PI
 
 
@@ -312,7 +320,8 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
     sites = problem.sites
     ns = sites.n
     if solver is None:
-        mesh = bem.build_mesh(problem.verts, problem.tris, par.gauss_k, par.near_factor)
+        mesh = bem.build_mesh(problem.verts, problem.tris, par.gauss_k, par.near_factor,
+                              body=getattr(problem, "panel_body", None))
         solver = bem.DenseSolver(mesh, par.eps_in, par.eps_out, par.kappa)
         solver.mesh = mesh
     mesh = solver.mesh
@@ -321,7 +330,8 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
 
     def bem_solve(p):
         b = np.zeros(2 * n)
-        b[:n] = rhs(mesh.cen, sites.pos, sites.q, p, sites.Q, par.eps_in)
+        b[:n] = rhs(mesh.cen, sites.pos, sites.q, p, sites.Q, par.eps_in, point_body=mesh.body,
+                    site_body=sites.body)
         return solver.solve(b), b
 
     _, gperm, _ = mult_potentials(sites.pos, sites.q, sites.d, sites.Q, np.zeros((ns, 3)), sites.alpha,
@@ -338,16 +348,17 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
     if direct_polarization:
         # E_solv is affine in p: E_solv(d + mu) = E_solv(d) + M mu
         x0, _ = bem_solve(sites.d)
-        _, g0, _ = reaction_at_sites(mesh, x0[:n], x0[n:], sites.pos)
+        _, g0, _ = reaction_at_sites(mesh, x0[:n], x0[n:], sites.pos, site_body=sites.body)
         M = np.zeros((3 * ns, 3 * ns))
         for m in range(ns):
             for c in range(3):
                 p = np.zeros((ns, 3))
                 p[m, c] = 1.0
                 b = np.zeros(2 * n)
-                b[:n] = rhs(mesh.cen, sites.pos, np.zeros(ns), p, np.zeros((ns, 3, 3)), par.eps_in)
+                b[:n] = rhs(mesh.cen, sites.pos, np.zeros(ns), p, np.zeros((ns, 3, 3)), par.eps_in,
+                            point_body=mesh.body, site_body=sites.body)
                 xx = solver.solve(b)
-                _, gg, _ = reaction_at_sites(mesh, xx[:n], xx[n:], sites.pos)
+                _, gg, _ = reaction_at_sites(mesh, xx[:n], xx[n:], sites.pos, site_body=sites.body)
                 M[:, 3 * m + c] = -gg.reshape(-1)
         T = thole_matrix(sites.pos, sites.alpha, sites.body, par.eps_in, par.thole_a, True)
         A = np.eye(3 * ns) - np.repeat(four_pi_alpha, 3)[:, None] * (M + T)
@@ -359,7 +370,7 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
         it = 0
         for it in range(1, par.scf_maxit + 1):
             x, _ = bem_solve(sites.d + mu)
-            _, g, _ = reaction_at_sites(mesh, x[:n], x[n:], sites.pos)
+            _, g, _ = reaction_at_sites(mesh, x[:n], x[n:], sites.pos, site_body=sites.body)
             E = -g + Eperm + E_induced(mu)
             new = (1.0 - par.sor_omega) * mu + par.sor_omega * four_pi_alpha[:, None] * E
             delta = _rms(new - mu)
@@ -368,7 +379,7 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
                 break
 
     x, b = bem_solve(sites.d + mu)
-    rp, rg, rh = reaction_at_sites(mesh, x[:n], x[n:], sites.pos)
+    rp, rg, rh = reaction_at_sites(mesh, x[:n], x[n:], sites.pos, site_body=sites.body)
     mp, mg, mh = mult_potentials(sites.pos, sites.q, sites.d, sites.Q, mu, sites.alpha, sites.group,
                                  sites.body, par.eps_in, par.thole_a, masked=False, same_body_only=True)
     G_diss = site_energy(sites.q, sites.d, sites.Q, rp + mp, rg + mg, rh + mh)
