@@ -17,6 +17,12 @@ bounded sample (the CPU baseline).
 Launch: python bench.py [--gpus N --steps K --warmup W] ; for N > 1 under
 torch.distributed.run each rank solves its own replica (independent problems, no
 collective in the data path: weak scaling).  --impl reference times the oracle.
+
+--workload binding times the binding workload instead: 16 triples (A, B, AB) of
+bumpy bodies (subdivisions 3-6, R 6-14 A) = 48 systems solved together in one
+context (one set of launches per matrix-vector product, per-system GMRES and SCF),
+reporting Delta Delta G_bind per triple, against the same 48 systems solved one
+after another in contexts of their own.
 """
 from __future__ import annotations
 
@@ -68,6 +74,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=384)
+    ap.add_argument("--workload", default="solvation", choices=["solvation", "binding"])
+    ap.add_argument("--triples", type=int, default=16)
     return ap.parse_args()
 
 
@@ -193,6 +201,72 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- binding workload
+def run_binding(args, local):
+    """48 systems (16 triples) in one context vs one context per system."""
+    import torch
+    import gen
+    build_library()
+    import paper_1810_03698_gb300 as bp
+
+    triples = gen.config4(n_triples=args.triples)
+    probs = [p for t in triples for p in t]
+    res_op = args.residual_op or args.op
+    kw = dict(op=args.op, residual_op=res_op)
+    stream = torch.cuda.current_stream()
+    s = bp.batch_solver(probs, device=local, **kw)
+
+    def ev_time(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), r
+
+    for _ in range(args.warmup):
+        s.solve(per_system=True)
+    s.stats(reset=True)
+    sampler = ClockSampler(local)
+    sampler.start()
+    times, outs = [], []
+    for _ in range(args.steps):
+        ms, r = ev_time(lambda: s.solve(per_system=True))
+        times.append(ms)
+        outs.append(r)
+    clocks = sampler.stop()
+    stats = s.stats(reset=True)
+    r = outs[-1]
+    sy = r["systems"]
+    ddg = [sy[3 * t + 2]["dG_solv_kcal"] - sy[3 * t]["dG_solv_kcal"] - sy[3 * t + 1]["dG_solv_kcal"]
+           for t in range(len(triples))]
+    # the same systems one at a time, each in a context of its own (set-up not timed)
+    seq_ms = 0.0
+    for pr in probs:
+        one = bp.problem_solver(pr, device=local, **kw)
+        one.solve()
+        ms, _ = ev_time(lambda: one.solve())
+        seq_ms += ms
+        one.close()
+    value = float(np.mean(times)) / 1e3
+    line = {
+        "metric": "time per batched solve of 16 binding triples (48 systems, 16 ΔΔG_bind)",
+        "value": value, "unit": "s/batch", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": float(np.mean(times)), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if "fp32" in args.op else "f64", "data": "synthetic",
+        "config": {"workload": f"binding_{len(triples)}_triples", "systems": len(probs),
+                   "panels": int(sum(p.n_panels for p in probs)), "sites": int(sum(p.sites.n for p in probs)),
+                   "op": args.op, "residual_op": res_op, "gmres_tol": probs[0].params.gmres_tol,
+                   "scf_tol": probs[0].params.scf_tol},
+        "sequential_s": seq_ms / 1e3, "batch_speedup": seq_ms / 1e3 / value,
+        "ddG_bind_kcal": ddg, "lockstep_gmres_iters": r["gmres_iters_total"], "matvecs": r["matvecs_total"],
+        "converged": all(x["converged"] for x in sy), "gpu_launches": int(stats["kernel_launches"]),
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- native arm
 def main():
     args = parse()
@@ -204,6 +278,10 @@ def main():
         return
     import torch
     torch.cuda.set_device(local)
+    if args.workload == "binding":
+        if rank == 0:
+            run_binding(args, local)
+        return
     dist = None
     if world > 1:
         import torch.distributed as dist

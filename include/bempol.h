@@ -39,6 +39,14 @@
  *  - Panel-indexed arrays at the ABI are in the caller's triangle order
  *    (the library reorders internally and maps back).
  *  - Double-precision is used at the ABI throughout.
+ *
+ * Several bodies and several systems (Sec. "Calculation of the binding energy":
+ * a complex AB is two solute cavities in one solvent).  A context may hold
+ * several independent systems, each with one or more bodies (closed surfaces).
+ * Within a system the Laplace layers, the right-hand side and the reaction field
+ * at a site involve only the site's or panel's own body; the Yukawa layers couple
+ * every panel of the system; different systems never interact.  The entry points
+ * without "_systems" in their name treat everything as one body of one system.
  */
 #ifndef BEMPOL_H
 #define BEMPOL_H
@@ -114,6 +122,18 @@ typedef struct {
   int where;                   /* BEMPOL_HOST or BEMPOL_DEVICE for the optional outputs */
 } bempol_result;
 
+/* Per-system result of bempol_solve_systems (host memory). */
+typedef struct {
+  double dG_solv_kcal;         /* this system's G_diss - G_vac in kcal/mol */
+  double G_diss, G_vac;        /* paper units as in bempol_result */
+  int scf_iters_diss, scf_iters_vac;
+  int gmres_iters;             /* GMRES iterations this system took, summed over its solves */
+  int n_solves;                /* BEM solves that included this system */
+  double last_rel_residual;    /* relative residual of its final solve */
+  int converged;               /* 1 if its SCFs and every solve converged */
+  int64_t n_panels, n_sites;
+} bempol_system_result;
+
 /* Fill `p` with the defaults: eps 1/80, kappa 0.125, K=4, near 2.0, theta 0.5,
  * P=5, leaf 256, GMRES 1e-8/100/500, SCF 1e-8/omega 0.7/200, op FP64 direct,
  * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39. */
@@ -157,10 +177,40 @@ bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, in
  *   group [ns] int32 polarisation group (NULL = every site its own group).
  * All host or device per `where`.  Validation: every site strictly inside the
  * surface and farther than near_factor*sqrt(A_j) from every panel centroid j
- * (BEMPOL_ERR_SITES).  Requires bempol_set_mesh first (BEMPOL_ERR_STATE). */
+ * (BEMPOL_ERR_SITES).  Requires bempol_set_mesh first, and a single-body mesh
+ * (BEMPOL_ERR_STATE; see bempol_set_sites_systems). */
 bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, const double* q,
                                const double* d, const double* Q, const double* alpha,
                                const int32_t* group, int where, void* stream);
+
+/* Set several bodies and systems at once.  As bempol_set_mesh, plus
+ *   panel_system [nt] int32 system of each triangle: ids 0..S-1, each present
+ *                (NULL = all 0);
+ *   panel_body   [nt] int32 body of each triangle within its system, any ids >= 0
+ *                (NULL = all 0);
+ * host or device per `where`.  Every (system, body) must be a closed surface of
+ * its own (no edge shared between bodies: BEMPOL_ERR_MESH).  Limits: at most
+ * 1,023 (system, body) pairs and 16,777,215 triangles (BEMPOL_ERR_ARG).  Panels
+ * are reordered by system, body and Morton code; the octree is a forest with one
+ * root per body, and near-field pairs and treecode interaction lists never cross
+ * systems. */
+bempol_status bempol_set_mesh_systems(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt,
+                                      const int32_t* tris, const int32_t* panel_system,
+                                      const int32_t* panel_body, int where, void* stream);
+
+/* Sites of a context set with bempol_set_mesh_systems.  As bempol_set_sites, plus
+ *   site_system, site_body [ns] int32 (NULL = all 0), host or device per `where`.
+ * Sites must be ordered by system, then by body (in the order the bodies' ids
+ * sort), and each site's (system, body) must have a surface (BEMPOL_ERR_SITES
+ * otherwise).  Validation also rejects a site inside another body of its system.
+ * Polarisation groups are global ids (a group should not span bodies). */
+bempol_status bempol_set_sites_systems(bempol_ctx* c, int64_t ns, const double* pos, const double* q,
+                                       const double* d, const double* Q, const double* alpha,
+                                       const int32_t* group, const int32_t* site_system,
+                                       const int32_t* site_body, int where, void* stream);
+
+/* Number of systems and of bodies ((system, body) pairs) of the current mesh. */
+bempol_status bempol_systems(const bempol_ctx* c, int64_t* n_systems, int64_t* n_bodies);
 
 /* Solvation free energy Delta G_solv = G_diss - G_vac (Sec. "Calculation of the
  * solvation energy") with the self-consistent induced dipoles of Sec.
@@ -174,10 +224,69 @@ bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, con
  * their limits.  Synchronises `stream`. */
 bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out);
 
+/* bempol_solve for every system of the context at once (Sec. "Calculation of the
+ * binding energy": Delta G_solv of A, B and AB gives Delta Delta G_bind =
+ * Delta G_solv,AB - Delta G_solv,A - Delta G_solv,B).  The systems share every
+ * kernel launch: one matrix-vector product serves all of them, while each system
+ * runs its own GMRES (own Krylov basis, Hessenberg matrix and stopping test) and
+ * its own vacuum and dissolved SCF (own RMS test); a converged system stops
+ * updating while the others continue.  In the dissolved state a site feels the
+ * reaction field of its own body's surface and the multipoles of its own body; in
+ * vacuum it feels every site of its system.
+ *   per [n_per] host array (NULL to skip), n_per >= number of systems.
+ * `out` receives the sums over systems (dG_solv_kcal, G_diss, G_vac), the largest
+ * SCF iteration counts and residual, the totals of GMRES iterations (lockstep
+ * iterations, each counted once), operator applications and solves, and the
+ * optional arrays for every panel and site.  BEMPOL_ERR_NOT_CONVERGED if any
+ * system did not converge (results filled). */
+bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* out, bempol_system_result* per,
+                                   int64_t n_per);
+
+/* Adjoint gradient (not part of the paper's method: its derivatives with respect
+ * to the site parameters, for force fields and fitting).  Uses the state of the
+ * last bempol_solve / bempol_solve_systems on this context (mesh, sites and
+ * parameters unchanged since; BEMPOL_ERR_STATE otherwise).  The energy of Eq.
+ * energy_multipole_polarizable is not stationary in the induced dipoles, so the
+ * gradient is the full discrete adjoint: one transposed BEM system A^T lambda = c
+ * per step of a transposed induced-dipole relaxation (same omega, scf_tol and
+ * scf_maxit; GMRES with params.op / residual_op applied as transposed products),
+ * the same without BEM for the vacuum state, then per-site fields and,
+ * for positions, their derivatives (dual numbers, no differencing).
+ * Outputs (device float64, caller's site order, NULL to skip):
+ *   grad_q [ns]   dDelta G_solv/dq_l,   grad_d [ns*3] dDelta G_solv/dd_l,
+ *   grad_Q [ns*9] dDelta G_solv/dQ_l as the symmetric traceless 3x3 matrix G with
+ *                 dDelta G = sum_l G_l : dQ_l for symmetric traceless dQ_l,
+ *   grad_pos [ns*3] dDelta G_solv/dr_l with the mesh held fixed (the surface does
+ *                 not follow the sites).
+ * Units: paper units (e^2/A per e, per e*A, per e*A^2, per A); multiply by
+ * 4 pi 332.0637 for kcal/mol.  With several systems each site's gradient is that
+ * of its own system's Delta G_solv.  info (host, may be NULL) receives iteration
+ * counts and the event time.  BEMPOL_ERR_NOT_CONVERGED if a limit was hit (outputs
+ * written).  Synchronises `stream`. */
+typedef struct {
+  int scf_iters_diss, scf_iters_vac;  /* transposed relaxation steps */
+  int gmres_iters_total;              /* GMRES iterations of the transposed solves */
+  int n_solves;                       /* transposed BEM solves */
+  int converged;
+  double t_ms;
+} bempol_gradient_info;
+
+bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, double* grad_d, double* grad_Q,
+                              double* grad_pos, bempol_gradient_info* info);
+
 /* y = A x for the operator form `op` (BEMPOL_OP_*), one matrix-vector product of
  * Eq. integral_eq.  x, y: device float64 [2N] = [phi; psi] in the caller's panel
  * order (y may not alias x).  Enqueued on `stream`, no synchronisation. */
 bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, void* stream);
+
+/* y = A^T x, the transpose of the operator of bempol_matvec (used by the adjoint;
+ * the paper has no counterpart): charges x_phi (Laplace) and x_psi (Yukawa) at the
+ * collocation points evaluated at every panel's Gauss nodes, plus the near
+ * corrections by columns.  The tree forms use the same octree and lists, with
+ * charge moments and coefficients to order P + 1 for the nodes' potential gradient.
+ * x, y: device float64 [2N] in the caller's order (y may not alias x).  Enqueued
+ * on `stream`, no synchronisation. */
+bempol_status bempol_matvec_transposed(bempol_ctx* c, const double* x, double* y, int op, void* stream);
 
 /* Right-hand side of Eq. rhs_multipole at every collocation point, with the
  * sites' q and Q and the total dipoles p (device float64 [ns*3]; NULL = the
@@ -189,7 +298,8 @@ bempol_status bempol_rhs(bempol_ctx* c, const double* p, double* b, int op, void
  * solution x = [phi; psi] (device float64 [2N], caller order) (Eqs. pot_solvent,
  * Efield_solv, ddphi): out [ns*10] device float64, per site phi_solv,
  * dphi/dx,dy,dz, then d2phi xx,xy,xz,yy,yz,zz.  K-node quadrature over every
- * panel (sites are validated to be far from the surface).  Enqueued on `stream`. */
+ * panel of the site's own body (sites are validated to be far from the surface).
+ * Enqueued on `stream`. */
 bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, int op, void* stream);
 
 /* Same result as bempol_site_reaction, for callers that cannot allow a device
@@ -215,6 +325,8 @@ bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const double* x, doubl
  *          are masked, induced dipoles Thole-damped; out [ns*3] = E (field).
  *   mode 1 (energy): permanent moments unmasked, induced dipoles damped;
  *          out [ns*10] = phi, grad phi (3), Hessian (6) as in bempol_site_reaction.
+ *   Modes 0 and 1 sum over the sites of each site's own body (dissolved state);
+ *   modes 2 and 3 are modes 0 and 1 summed over every site of its system (vacuum).
  * FP64.  Enqueued on `stream`. */
 bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, double* out, void* stream);
 

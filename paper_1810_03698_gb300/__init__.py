@@ -48,6 +48,22 @@ class Result(C.Structure):
     ]
 
 
+class SystemResult(C.Structure):
+    _fields_ = [
+        ("dG_solv_kcal", C.c_double), ("G_diss", C.c_double), ("G_vac", C.c_double),
+        ("scf_iters_diss", C.c_int), ("scf_iters_vac", C.c_int), ("gmres_iters", C.c_int),
+        ("n_solves", C.c_int), ("last_rel_residual", C.c_double), ("converged", C.c_int),
+        ("n_panels", C.c_int64), ("n_sites", C.c_int64),
+    ]
+
+
+class GradientInfo(C.Structure):
+    _fields_ = [
+        ("scf_iters_diss", C.c_int), ("scf_iters_vac", C.c_int), ("gmres_iters_total", C.c_int),
+        ("n_solves", C.c_int), ("converged", C.c_int), ("t_ms", C.c_double),
+    ]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("kernel_launches", C.c_int64), ("pair_launches", C.c_int64), ("pair_ms", C.c_double),
@@ -69,8 +85,14 @@ def _load():
         "bempol_last_error": (C.c_char_p, [vp]),
         "bempol_set_mesh": (i32, [vp, i64, vp, i64, vp, i32, vp]),
         "bempol_set_sites": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
+        "bempol_set_mesh_systems": (i32, [vp, i64, vp, i64, vp, vp, vp, i32, vp]),
+        "bempol_set_sites_systems": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]),
+        "bempol_systems": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
         "bempol_solve": (i32, [vp, vp, C.POINTER(Result)]),
+        "bempol_solve_systems": (i32, [vp, vp, C.POINTER(Result), C.POINTER(SystemResult), i64]),
         "bempol_matvec": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_matvec_transposed": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_gradient": (i32, [vp, vp, vp, vp, vp, vp, C.POINTER(GradientInfo)]),
         "bempol_rhs": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction_noalloc": (i32, [vp, vp, vp, i32, vp]),
@@ -167,30 +189,55 @@ class Solver:
             setattr(self.params, k, v)
         self._chk(_lib.bempol_set_params(self._h, C.byref(self.params)))
 
-    def set_mesh(self, verts, tris, stream=None):
+    def set_mesh(self, verts, tris, system=None, body=None, stream=None):
+        """Surface(s).  ``system`` / ``body`` (int32 per triangle) give several bodies
+        and independent systems (bempol_set_mesh_systems); None = one body."""
         pv, wv = _ptr(verts)
         pt, wt = _ptr(tris)
         if wv != wt:
             raise ValueError("verts and tris must both be host or both be device arrays")
-        self._chk(_lib.bempol_set_mesh(self._h, verts.shape[0], pv, tris.shape[0], pt, wv, _stream(stream)))
+        if system is None and body is None:
+            self._chk(_lib.bempol_set_mesh(self._h, verts.shape[0], pv, tris.shape[0], pt, wv, _stream(stream)))
+            return
+        ps, ws = _ptr(system)
+        pb, wb = _ptr(body)
+        for w, a in ((ws, system), (wb, body)):
+            if a is not None and w != wv:
+                raise ValueError("system/body arrays must live where the mesh arrays live")
+        self._chk(_lib.bempol_set_mesh_systems(self._h, verts.shape[0], pv, tris.shape[0], pt, ps, pb, wv,
+                                               _stream(stream)))
 
-    def set_sites(self, pos, q, d, Q, alpha, group=None, stream=None):
-        arrs = [pos, q, d, Q, alpha] + ([group] if group is not None else [])
+    def set_sites(self, pos, q, d, Q, alpha, group=None, system=None, body=None, stream=None):
+        """Point multipoles; with several bodies/systems pass ``system`` / ``body`` per
+        site (sites ordered by system, then body)."""
+        arrs = [pos, q, d, Q, alpha] + [a for a in (group, system, body) if a is not None]
         ptrs = [_ptr(a) for a in arrs]
         where = {w for _, w in ptrs}
         if len(where) != 1:
             raise ValueError("site arrays must all be host or all be device")
-        pg = ptrs[5][0] if group is not None else None
-        self._chk(_lib.bempol_set_sites(self._h, pos.shape[0], ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0],
-                                        ptrs[4][0], pg, where.pop(), _stream(stream)))
+        w = where.pop()
+        pg, ps, pb = _ptr(group)[0], _ptr(system)[0], _ptr(body)[0]
+        if system is None and body is None:
+            self._chk(_lib.bempol_set_sites(self._h, pos.shape[0], ptrs[0][0], ptrs[1][0], ptrs[2][0], ptrs[3][0],
+                                            ptrs[4][0], pg, w, _stream(stream)))
+        else:
+            self._chk(_lib.bempol_set_sites_systems(self._h, pos.shape[0], ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                                                    ptrs[3][0], ptrs[4][0], pg, ps, pb, w, _stream(stream)))
+
+    def systems(self):
+        ns, nb = C.c_int64(), C.c_int64()
+        self._chk(_lib.bempol_systems(self._h, C.byref(ns), C.byref(nb)))
+        return ns.value, nb.value
 
     def sizes(self):
         v = [C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()]
         self._chk(_lib.bempol_sizes(self._h, *[C.byref(x) for x in v]))
         return dict(zip(["n_panels", "gauss_k", "n_sites", "n_near", "n_cells", "n_leaves"], [x.value for x in v]))
 
-    def solve(self, stream=None, outputs=False, where="host", allow_unconverged=False):
-        """Run the SCF + BEM solve; returns a dict of scalars (and arrays if ``outputs``)."""
+    def solve(self, stream=None, outputs=False, where="host", allow_unconverged=False, per_system=False):
+        """Run the SCF + BEM solve; returns a dict of scalars (and arrays if ``outputs``).
+        With ``per_system`` every system of the context is solved together
+        (bempol_solve_systems) and ``out["systems"]`` lists each one's results."""
         r = Result()
         arrays = {}
         if outputs:
@@ -207,17 +254,49 @@ class Solver:
                       "mu_vac": mk(ns * 3)}
             for k, a in arrays.items():
                 setattr(r, k, _ptr(a)[0])
-        st = _lib.bempol_solve(self._h, _stream(stream), C.byref(r))
+        per = None
+        if per_system:
+            nsys = self.systems()[0]
+            per = (SystemResult * nsys)()
+            st = _lib.bempol_solve_systems(self._h, _stream(stream), C.byref(r), per, nsys)
+        else:
+            st = _lib.bempol_solve(self._h, _stream(stream), C.byref(r))
         if st != 0 and not (allow_unconverged and st == 4):
             self._chk(st)
         out = {k: getattr(r, k) for k, _ in Result._fields_ if k not in arrays and k != "where"}
         out["status"] = st
+        if per is not None:
+            out["systems"] = [{k: getattr(x, k) for k, _ in SystemResult._fields_} for x in per]
         for k, a in arrays.items():
             out[k] = a
         return out
 
     def matvec(self, x, y, op=OP_FP64_DIRECT, stream=None):
         self._chk(_lib.bempol_matvec(self._h, _ptr(x)[0], _ptr(y)[0], OP_NAMES.get(op, op), _stream(stream)))
+
+    def matvec_transposed(self, x, y, op=OP_FP64_DIRECT, stream=None):
+        self._chk(_lib.bempol_matvec_transposed(self._h, _ptr(x)[0], _ptr(y)[0], OP_NAMES.get(op, op),
+                                                _stream(stream)))
+
+    def gradient(self, stream=None, allow_unconverged=False):
+        """Adjoint gradient of the last solve's Delta G_solv (paper units) with respect to
+        every site's q, d, Q and position: dict of numpy arrays ``q`` [ns], ``d`` [ns, 3],
+        ``Q`` [ns, 3, 3], ``pos`` [ns, 3] and ``info``."""
+        import torch
+        ns = self.sizes()["n_sites"]
+        dev = f"cuda:{self.device}"
+        gq = torch.zeros(ns, dtype=torch.float64, device=dev)
+        gd = torch.zeros(ns * 3, dtype=torch.float64, device=dev)
+        gQ = torch.zeros(ns * 9, dtype=torch.float64, device=dev)
+        gp = torch.zeros(ns * 3, dtype=torch.float64, device=dev)
+        info = GradientInfo()
+        st = _lib.bempol_gradient(self._h, _stream(stream), _ptr(gq)[0], _ptr(gd)[0], _ptr(gQ)[0], _ptr(gp)[0],
+                                  C.byref(info))
+        if st != 0 and not (allow_unconverged and st == 4):
+            self._chk(st)
+        return {"q": gq.cpu().numpy(), "d": gd.cpu().numpy().reshape(-1, 3), "Q": gQ.cpu().numpy().reshape(-1, 3, 3),
+                "pos": gp.cpu().numpy().reshape(-1, 3),
+                "info": {k: getattr(info, k) for k, _ in GradientInfo._fields_}, "status": st}
 
     def rhs(self, b, p=None, op=OP_FP64_DIRECT, stream=None):
         self._chk(_lib.bempol_rhs(self._h, _ptr(p)[0], _ptr(b)[0], OP_NAMES.get(op, op), _stream(stream)))
@@ -256,8 +335,56 @@ class Solver:
         return out
 
 
+def _param_kw(par, overrides):
+    kw = dict(eps_in=par.eps_in, eps_out=par.eps_out, kappa=par.kappa, gauss_k=par.gauss_k,
+              near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,
+              gmres_tol=par.gmres_tol, gmres_restart=par.gmres_restart, gmres_maxit=par.gmres_maxit,
+              scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a)
+    kw.update(overrides)
+    return kw
+
+
+def batch_solver(problems, device: int = 0, stream=None, **overrides) -> Solver:
+    """One Solver holding several ``gen.Problem`` s as independent systems (system k =
+    problems[k]; each problem's ``panel_body`` and ``sites.body`` give its bodies).
+    Parameters come from the first problem."""
+    verts, tris, psys, pbody = [], [], [], []
+    cols = {k: [] for k in ("pos", "q", "d", "Q", "alpha", "group", "system", "body")}
+    voff = goff = 0
+    for k, pr in enumerate(problems):
+        verts.append(np.asarray(pr.verts, dtype=np.float64))
+        tris.append(np.asarray(pr.tris, dtype=np.int64) + voff)
+        voff += pr.verts.shape[0]
+        psys.append(np.full(pr.tris.shape[0], k, dtype=np.int32))
+        pb = getattr(pr, "panel_body", None)
+        pbody.append(np.zeros(pr.tris.shape[0], np.int32) if pb is None else np.asarray(pb, np.int32))
+        st = pr.sites
+        order = np.argsort(st.body, kind="stable")
+        cols["pos"].append(st.pos[order])
+        cols["q"].append(st.q[order])
+        cols["d"].append(st.d[order])
+        cols["Q"].append(st.Q[order].reshape(-1, 9))
+        cols["alpha"].append(st.alpha[order])
+        cols["group"].append(np.asarray(st.group, np.int64)[order] + goff)
+        goff += int(np.max(st.group)) + 1 if st.n else 0
+        cols["system"].append(np.full(st.n, k, np.int32))
+        cols["body"].append(np.asarray(st.body, np.int32)[order])
+    s = Solver(device=device, **_param_kw(problems[0].params, overrides))
+    s.set_mesh(np.ascontiguousarray(np.vstack(verts)), np.ascontiguousarray(np.vstack(tris), dtype=np.int32),
+               system=np.concatenate(psys), body=np.ascontiguousarray(np.concatenate(pbody)), stream=stream)
+    cat = {k: np.concatenate(v) for k, v in cols.items()}
+    s.set_sites(np.ascontiguousarray(cat["pos"]), np.ascontiguousarray(cat["q"]), np.ascontiguousarray(cat["d"]),
+                np.ascontiguousarray(cat["Q"]), np.ascontiguousarray(cat["alpha"]),
+                np.ascontiguousarray(cat["group"], dtype=np.int32), system=np.ascontiguousarray(cat["system"]),
+                body=np.ascontiguousarray(cat["body"]), stream=stream)
+    return s
+
+
 def problem_solver(problem, device: int = 0, stream=None, **overrides) -> Solver:
-    """A Solver loaded with a ``gen.Problem`` (mesh and sites from host arrays)."""
+    """A Solver loaded with a ``gen.Problem`` (mesh and sites from host arrays); a
+    problem with several bodies (``panel_body``) is loaded as one system of bodies."""
+    if getattr(problem, "panel_body", None) is not None:
+        return batch_solver([problem], device=device, stream=stream, **overrides)
     par = problem.params
     kw = dict(eps_in=par.eps_in, eps_out=par.eps_out, kappa=par.kappa, gauss_k=par.gauss_k,
               near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,

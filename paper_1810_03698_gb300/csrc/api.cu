@@ -100,6 +100,7 @@ bempol_status guard(bempol_ctx* c, F&& f) {
   if (!c) return BEMPOL_ERR_ARG;
   try {
     if (cudaSetDevice(c->device) != cudaSuccess) fail(BEMPOL_ERR_CUDA, "cudaSetDevice failed");
+    c->mv_active = nullptr;  // products outside a solve compute every system
     f();
     c->err.clear();
     return BEMPOL_OK;
@@ -131,6 +132,54 @@ std::vector<T> to_host(const T* src, size_t count, int where, cudaStream_t s) {
     std::memcpy(h.data(), src, count * sizeof(T));
   }
   return h;
+}
+
+// Pinned host and device scalar areas sized for per-system values.
+void size_scalars(Ctx& c) {
+  const size_t want = 4 * (size_t)c.nsys + 16;
+  if (c.scal.n < want) {
+    c.scal.alloc(want);
+    if (c.h_pinned) cudaFreeHost(c.h_pinned);
+    c.h_pinned = nullptr;
+    BP_CUDA(cudaMallocHost(&c.h_pinned, want * sizeof(double)));
+  }
+}
+
+// Groups (bodies of systems) from per-panel system and body ids (NULL = all 0):
+// sorted (system, body) pairs; returns the group of every panel (caller order).
+std::vector<int> make_groups(Ctx& c, int64_t nt, const std::vector<int32_t>& sy, const std::vector<int32_t>& bo) {
+  std::vector<std::pair<int, int>> key(nt);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int a = sy.empty() ? 0 : sy[t], b = bo.empty() ? 0 : bo[t];
+    if (a < 0 || b < 0) fail(BEMPOL_ERR_ARG, "system and body ids must be >= 0");
+    key[t] = {a, b};
+  }
+  std::vector<std::pair<int, int>> u(key);
+  std::sort(u.begin(), u.end());
+  u.erase(std::unique(u.begin(), u.end()), u.end());
+  if (u.size() > 1023) fail(BEMPOL_ERR_ARG, "at most 1023 (system, body) groups");
+  const int S = u.back().first + 1;
+  c.ngroup = (int)u.size();
+  c.nsys = S;
+  c.h_grp_sys.resize(c.ngroup);
+  c.h_grp_body.resize(c.ngroup);
+  c.h_sys_grp.assign(S + 1, 0);
+  for (int g = 0; g < c.ngroup; ++g) {
+    c.h_grp_sys[g] = u[g].first;
+    c.h_grp_body[g] = u[g].second;
+    ++c.h_sys_grp[u[g].first + 1];
+  }
+  for (int q = 0; q < S; ++q) {
+    if (c.h_sys_grp[q + 1] == 0)
+      fail(BEMPOL_ERR_ARG, "system ids must be 0..S-1 with every system present (missing " + std::to_string(q) + ")");
+    c.h_sys_grp[q + 1] += c.h_sys_grp[q];
+  }
+  std::vector<int> grp;
+  if (c.ngroup > 1) {
+    grp.resize(nt);
+    for (int64_t t = 0; t < nt; ++t) grp[t] = (int)(std::lower_bound(u.begin(), u.end(), key[t]) - u.begin());
+  }
+  return grp;
 }
 
 void ensure_tree(Ctx& c, int op, cudaStream_t s) {
@@ -168,6 +217,124 @@ struct EventTimer {
     cudaEventDestroy(b);
   }
 };
+
+void set_mesh_impl(Ctx* c, int64_t nv, const double* verts, int64_t nt, const int32_t* tris,
+                   const int32_t* panel_system, const int32_t* panel_body, int where, cudaStream_t s) {
+  if (nv < 4 || nt < 4 || !verts || !tris) fail(BEMPOL_ERR_ARG, "need nv >= 4, nt >= 4 and non-NULL arrays");
+  if (nt >= (int64_t)1 << 24) fail(BEMPOL_ERR_ARG, "at most 16,777,215 triangles");
+  if (nv >= (int64_t)1 << 31) fail(BEMPOL_ERR_ARG, "too many vertices");
+  if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
+  c->have_mesh = false;
+  c->have_sites = false;
+  c->have_solution = false;
+  c->tree_ready = false;
+  c->n = (int)nt;
+  c->nv = (int)nv;
+  c->K = c->par.gauss_k;
+  std::vector<int32_t> ht = to_host(tris, 3 * (size_t)nt, where, s);
+  std::vector<int32_t> hs, hb;
+  if (panel_system) hs = to_host(panel_system, (size_t)nt, where, s);
+  if (panel_body) hb = to_host(panel_body, (size_t)nt, where, s);
+  std::vector<int> grp = make_groups(*c, nt, hs, hb);
+  size_scalars(*c);
+  DBuf<double> dv;
+  to_device(dv, verts, 3 * (size_t)nv, where, s);
+  build_geometry(*c, dv.p, ht.data(), grp, s);
+  build_blocks(*c, s);
+  build_tree(*c, s);  // the octree also narrows the near-pair search
+  build_near(*c, s);
+  size_t len = 2 * (size_t)c->n;
+  c->vec_a.alloc(len);
+  c->vec_b.alloc(len);
+  c->vec_c.alloc(len);
+  c->vec_d.alloc(len);
+  c->gm_m = 0;  // GMRES workspace is sized per mesh
+  c->have_mesh = true;
+}
+
+void set_sites_impl(Ctx* c, int64_t ns, const double* pos, const double* q, const double* d, const double* Q,
+                    const double* alpha, const int32_t* group, const int32_t* site_system, const int32_t* site_body,
+                    int where, cudaStream_t s) {
+  if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "set_mesh must come before set_sites");
+  if (ns < 1 || ns > (1 << 24) || !pos || !q || !d || !Q || !alpha) fail(BEMPOL_ERR_ARG, "bad site arrays");
+  if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
+  c->have_sites = false;
+  c->have_solution = false;
+  // group of every site; sites must come sorted by (system, body)
+  std::vector<int32_t> hs, hb;
+  if (site_system) hs = to_host(site_system, (size_t)ns, where, s);
+  if (site_body) hb = to_host(site_body, (size_t)ns, where, s);
+  std::vector<int> tag(ns);
+  c->h_gsite.assign(c->ngroup + 1, 0);
+  for (int64_t l = 0; l < ns; ++l) {
+    const int a = hs.empty() ? 0 : hs[l], b = hb.empty() ? 0 : hb[l];
+    int g = -1;
+    for (int k = (a >= 0 && a < c->nsys) ? c->h_sys_grp[a] : 0; a >= 0 && a < c->nsys && k < c->h_sys_grp[a + 1]; ++k)
+      if (c->h_grp_body[k] == b) g = k;
+    if (g < 0)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": its (system, body) has no surface");
+    if (l > 0 && g < tag[l - 1])
+      fail(BEMPOL_ERR_SITES, "sites must be ordered by system, then body (site " + std::to_string(l) + ")");
+    tag[l] = g;
+    ++c->h_gsite[g + 1];
+  }
+  for (int g = 0; g < c->ngroup; ++g) c->h_gsite[g + 1] += c->h_gsite[g];
+  c->h_sys_site.assign(c->nsys + 1, 0);
+  for (int k = 0; k <= c->nsys; ++k) c->h_sys_site[k] = c->h_gsite[c->h_sys_grp[k]];
+  std::vector<int4> sblk;
+  for (int g = 0; g < c->ngroup; ++g)
+    for (int l = c->h_gsite[g]; l < c->h_gsite[g + 1]; l += 8)
+      sblk.push_back(make_int4(l, std::min(8, c->h_gsite[g + 1] - l), g, 0));
+  // host-side checks of the moments (small arrays)
+  std::vector<double> hQ = to_host(Q, 9 * (size_t)ns, where, s);
+  std::vector<double> ha = to_host(alpha, (size_t)ns, where, s);
+  std::vector<double> Q6(6 * (size_t)ns);
+  for (int64_t l = 0; l < ns; ++l) {
+    const double* m = hQ.data() + 9 * l;
+    double mx = 0;
+    for (int k = 0; k < 9; ++k) mx = std::max(mx, std::fabs(m[k]));
+    if (!std::isfinite(mx)) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " has a non-finite quadrupole");
+    double asym = std::max(std::fabs(m[1] - m[3]), std::max(std::fabs(m[2] - m[6]), std::fabs(m[5] - m[7])));
+    double tr = m[0] + m[4] + m[8];
+    if (asym > 1e-9 * mx || std::fabs(tr) > 1e-9 * mx)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": Q must be symmetric and traceless");
+    double t3 = tr / 3.0;
+    double* o = Q6.data() + 6 * l;
+    o[0] = m[0] - t3;
+    o[1] = m[1];
+    o[2] = m[2];
+    o[3] = m[4] - t3;
+    o[4] = m[5];
+    o[5] = m[8] - t3;
+    if (!(ha[l] >= 0.0) || !std::isfinite(ha[l]))
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": alpha must be finite and >= 0");
+  }
+  c->ns = (int)ns;
+  DBuf<double> dpos, dal;
+  to_device(dpos, pos, 3 * (size_t)ns, where, s);
+  to_device(dal, alpha, (size_t)ns, where, s);
+  c->site_pos.alloc(ns);
+  launch(pack_sites, cdiv(ns, 256), 256, 0, s, dpos.p, dal.p, (int)ns, c->site_pos.p);
+  BP_CHECK_LAUNCH();
+  to_device(c->site_q, q, (size_t)ns, where, s);
+  to_device(c->site_d, d, 3 * (size_t)ns, where, s);
+  to_device(c->site_Q, Q6.data(), 6 * (size_t)ns, BEMPOL_HOST, s);
+  std::vector<int32_t> g(ns);
+  if (group) {
+    g = to_host(group, (size_t)ns, where, s);
+  } else {
+    for (int64_t l = 0; l < ns; ++l) g[l] = (int32_t)l;
+  }
+  to_device(c->site_group, g.data(), (size_t)ns, BEMPOL_HOST, s);
+  to_device(c->stag, tag.data(), (size_t)ns, BEMPOL_HOST, s);
+  to_device(c->gsite, c->h_gsite.data(), c->h_gsite.size(), BEMPOL_HOST, s);
+  to_device(c->sys_site, c->h_sys_site.data(), c->h_sys_site.size(), BEMPOL_HOST, s);
+  c->nsblk = (int)sblk.size();
+  to_device(c->sblk, sblk.data(), sblk.size(), BEMPOL_HOST, s);
+  site_validation(*c, s);
+  BP_CUDA(cudaStreamSynchronize(s));
+  c->have_sites = true;
+}
 
 }  // namespace
 }  // namespace bp
@@ -232,6 +399,7 @@ bempol_status bempol_set_params(bempol_ctx* c, const bempol_params* p) {
     bool tree = p->leaf != c->par.leaf || p->theta != c->par.theta || geo;
     if (geo && c->have_mesh) fail(BEMPOL_ERR_STATE, "gauss_k, near_factor and kappa are fixed once a mesh is set");
     c->par = *p;
+    c->have_solution = false;
     if (tree) c->tree_ready = false;
   });
 }
@@ -246,30 +414,14 @@ const char* bempol_last_error(const bempol_ctx* c) { return c ? c->err.c_str() :
 
 bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt, const int32_t* tris,
                               int where, void* stream) {
+  return guard(c, [&] { set_mesh_impl(c, nv, verts, nt, tris, nullptr, nullptr, where, (cudaStream_t)stream); });
+}
+
+bempol_status bempol_set_mesh_systems(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt,
+                                      const int32_t* tris, const int32_t* panel_system, const int32_t* panel_body,
+                                      int where, void* stream) {
   return guard(c, [&] {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (nv < 4 || nt < 4 || !verts || !tris) fail(BEMPOL_ERR_ARG, "need nv >= 4, nt >= 4 and non-NULL arrays");
-    if (nt > (int64_t)1 << 28) fail(BEMPOL_ERR_ARG, "too many triangles");
-    if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
-    c->have_mesh = false;
-    c->have_sites = false;
-    c->tree_ready = false;
-    c->n = (int)nt;
-    c->nv = (int)nv;
-    c->K = c->par.gauss_k;
-    std::vector<int32_t> ht = to_host(tris, 3 * (size_t)nt, where, s);
-    DBuf<double> dv;
-    to_device(dv, verts, 3 * (size_t)nv, where, s);
-    build_geometry(*c, dv.p, ht.data(), s);
-    build_tree(*c, s);  // the octree also narrows the near-pair search
-    build_near(*c, s);
-    build_block_centers(*c, s);
-    size_t len = 2 * (size_t)c->n;
-    c->vec_a.alloc(len);
-    c->vec_b.alloc(len);
-    c->vec_c.alloc(len);
-    c->vec_d.alloc(len);
-    c->have_mesh = true;
+    set_mesh_impl(c, nv, verts, nt, tris, panel_system, panel_body, where, (cudaStream_t)stream);
   });
 }
 
@@ -277,56 +429,25 @@ bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, con
                                const double* Q, const double* alpha, const int32_t* group, int where,
                                void* stream) {
   return guard(c, [&] {
-    cudaStream_t s = (cudaStream_t)stream;
-    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "set_mesh must come before set_sites");
-    if (ns < 1 || ns > (1 << 24) || !pos || !q || !d || !Q || !alpha) fail(BEMPOL_ERR_ARG, "bad site arrays");
-    if (where != BEMPOL_HOST && where != BEMPOL_DEVICE) fail(BEMPOL_ERR_ARG, "bad `where`");
-    c->have_sites = false;
-    // host-side checks of the moments (small arrays)
-    std::vector<double> hQ = to_host(Q, 9 * (size_t)ns, where, s);
-    std::vector<double> ha = to_host(alpha, (size_t)ns, where, s);
-    std::vector<double> Q6(6 * (size_t)ns);
-    for (int64_t l = 0; l < ns; ++l) {
-      const double* m = hQ.data() + 9 * l;
-      double mx = 0;
-      for (int k = 0; k < 9; ++k) mx = std::max(mx, std::fabs(m[k]));
-      if (!std::isfinite(mx)) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " has a non-finite quadrupole");
-      double asym = std::max(std::fabs(m[1] - m[3]), std::max(std::fabs(m[2] - m[6]), std::fabs(m[5] - m[7])));
-      double tr = m[0] + m[4] + m[8];
-      if (asym > 1e-9 * mx || std::fabs(tr) > 1e-9 * mx)
-        fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": Q must be symmetric and traceless");
-      double t3 = tr / 3.0;
-      double* o = Q6.data() + 6 * l;
-      o[0] = m[0] - t3;
-      o[1] = m[1];
-      o[2] = m[2];
-      o[3] = m[4] - t3;
-      o[4] = m[5];
-      o[5] = m[8] - t3;
-      if (!(ha[l] >= 0.0) || !std::isfinite(ha[l]))
-        fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": alpha must be finite and >= 0");
-    }
-    c->ns = (int)ns;
-    DBuf<double> dpos, dal;
-    to_device(dpos, pos, 3 * (size_t)ns, where, s);
-    to_device(dal, alpha, (size_t)ns, where, s);
-    c->site_pos.alloc(ns);
-    launch(pack_sites, cdiv(ns, 256), 256, 0, s, dpos.p, dal.p, (int)ns, c->site_pos.p);
-    BP_CHECK_LAUNCH();
-    to_device(c->site_q, q, (size_t)ns, where, s);
-    to_device(c->site_d, d, 3 * (size_t)ns, where, s);
-    to_device(c->site_Q, Q6.data(), 6 * (size_t)ns, BEMPOL_HOST, s);
-    std::vector<int32_t> g(ns);
-    if (group) {
-      g = to_host(group, (size_t)ns, where, s);
-    } else {
-      for (int64_t l = 0; l < ns; ++l) g[l] = (int32_t)l;
-    }
-    to_device(c->site_group, g.data(), (size_t)ns, BEMPOL_HOST, s);
-    site_validation(*c, s);
-    BP_CUDA(cudaStreamSynchronize(s));
-    c->have_sites = true;
+    if (c->ngroup != 1) fail(BEMPOL_ERR_STATE, "the mesh has several bodies: use bempol_set_sites_systems");
+    set_sites_impl(c, ns, pos, q, d, Q, alpha, group, nullptr, nullptr, where, (cudaStream_t)stream);
   });
+}
+
+bempol_status bempol_set_sites_systems(bempol_ctx* c, int64_t ns, const double* pos, const double* q,
+                                       const double* d, const double* Q, const double* alpha, const int32_t* group,
+                                       const int32_t* site_system, const int32_t* site_body, int where,
+                                       void* stream) {
+  return guard(c, [&] {
+    set_sites_impl(c, ns, pos, q, d, Q, alpha, group, site_system, site_body, where, (cudaStream_t)stream);
+  });
+}
+
+bempol_status bempol_systems(const bempol_ctx* cc, int64_t* n_systems, int64_t* n_bodies) {
+  if (!cc) return BEMPOL_ERR_ARG;
+  if (n_systems) *n_systems = cc->have_mesh ? cc->nsys : 0;
+  if (n_bodies) *n_bodies = cc->have_mesh ? cc->ngroup : 0;
+  return BEMPOL_OK;
 }
 
 bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, void* stream) {
@@ -338,6 +459,19 @@ bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, v
     ensure_tree(*c, op, s);
     permute_to_internal(*c, x, c->vec_a.p, 2, s);
     matvec_internal(*c, c->vec_a.p, c->vec_b.p, op, s);
+    permute_to_caller(*c, c->vec_b.p, y, 2, s);
+  });
+}
+
+bempol_status bempol_matvec_transposed(bempol_ctx* c, const double* x, double* y, int op, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "no mesh");
+    if (!x || !y || x == y) fail(BEMPOL_ERR_ARG, "x and y must be distinct device arrays");
+    if (op < 0 || op > 3) fail(BEMPOL_ERR_ARG, "bad op");
+    ensure_tree(*c, op, s);
+    permute_to_internal(*c, x, c->vec_a.p, 2, s);
+    matvec_T_internal(*c, c->vec_a.p, c->vec_b.p, op, s);
     permute_to_caller(*c, c->vec_b.p, y, 2, s);
   });
 }
@@ -366,7 +500,7 @@ bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, 
   return guard(c, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
-    if (!out || (mode != 0 && mode != 1)) fail(BEMPOL_ERR_ARG, "bad arguments");
+    if (!out || mode < 0 || mode > 3) fail(BEMPOL_ERR_ARG, "bad arguments");
     DBuf<double> zero;
     const double* m = mu;
     if (!m) {
@@ -478,19 +612,26 @@ bempol_status bempol_get_geometry(bempol_ctx* c, double* centroid, double* norma
   });
 }
 
-bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
+bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* out, bempol_system_result* per,
+                                   int64_t n_per) {
   return guard(c, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->have_sites) fail(BEMPOL_ERR_STATE, "set_mesh and set_sites must come first");
     if (!out) fail(BEMPOL_ERR_ARG, "out is NULL");
+    if (per && n_per < c->nsys) fail(BEMPOL_ERR_ARG, "per-system result array is shorter than the number of systems");
     auto wall0 = std::chrono::steady_clock::now();
     EventTimer tt(s);
     const bempol_params& P = c->par;
-    const int n = c->n, ns = c->ns, len = 2 * n;
+    const int n = c->n, ns = c->ns, len = 2 * n, S = c->nsys;
     ensure_tree(*c, P.op, s);
     ensure_tree(*c, P.residual_op, s);
     const bool f32 = op_fp32(P.residual_op);
-    DBuf<double> mu, mu_v, emult, react, mult10, p, b, x;
+    DBuf<double>& mu = c->sol_mu;
+    DBuf<double>& mu_v = c->sol_mu_v;
+    DBuf<double>& x = c->sol_x;
+    DBuf<double> emult, react, mult10, p, b;
+    DBuf<int> d_act;
+    c->have_solution = false;
     mu.alloc(3 * ns);
     mu_v.alloc(3 * ns);
     emult.alloc(3 * ns);
@@ -499,6 +640,7 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
     p.alloc(3 * ns);
     b.alloc(len);
     x.alloc(len);
+    d_act.alloc(S);
     mu.zero(s);
     mu_v.zero(s);
     x.zero(s);
@@ -506,80 +648,144 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
     double t_setup = tt.ms();
     EventTimer ts(s);
     int gm_iters = 0, matvecs = 0, solves = 0;
-    double last_res = 0;
-    bool ok = true;
-    // Divergence guard: the relaxed update converges only when every eigenvalue of
-    // 4 pi alpha T (plus the reaction coupling) exceeds 1 - 2/omega.  A change that is
-    // not finite, or that has grown 8 times in a row to more than 10x its smallest
-    // value, ends the solve with an error (stagnation at the operator's noise level
-    // instead runs to scf_maxit).
+    std::vector<int> it_d(S, 0), it_v(S, 0), sys_gm(S, 0), sys_solves(S, 0);
+    std::vector<double> sys_res(S, 0.0);
+    std::vector<char> conv_v(S, 0), conv_d(S, 0), gm_ok(S, 1), diverged(S, 0);
+    // Divergence guard (per system): the relaxed update converges only when every
+    // eigenvalue of 4 pi alpha T (plus the reaction coupling) exceeds 1 - 2/omega.
+    // A change that is not finite, or that has grown 8 times in a row to more than
+    // 10x its smallest value, stops that system with an error (stagnation at the
+    // operator's noise level instead runs to scf_maxit).
     struct Guard {
       double best = 1e300, prev = 1e300;
       int grow = 0;
-      void check(double rms, const char* state) {
-        if (!std::isfinite(rms)) grow = 1000;
+      bool diverges(double rms) {
+        if (!std::isfinite(rms)) return true;
         grow = (rms > prev) ? grow + 1 : 0;
         prev = rms;
         best = std::min(best, rms);
-        if (grow >= 1000 || (grow >= 8 && rms > 10.0 * best))
-          fail(BEMPOL_ERR_NOT_CONVERGED, std::string("induced-dipole iteration diverges in the ") + state +
-                                             " state (RMS change grows); sor_omega is outside the convergence range "
-                                             "of this polarizability coupling");
+        return grow >= 8 && rms > 10.0 * best;
       }
     };
-    // vacuum state: multipoles only
-    int it_v = 0;
-    Guard gv;
-    for (it_v = 1; it_v <= P.scf_maxit; ++it_v) {
-      multipole_internal(*c, mu_v.p, 0, emult.p, s);
-      double rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, s);
-      if (rms < P.scf_tol) break;
-      gv.check(rms, "vacuum");
+    auto upload_act = [&](const std::vector<int>& act) {
+      int* hp = reinterpret_cast<int*>(c->h_pinned + 2 * S);
+      std::copy(act.begin(), act.end(), hp);
+      BP_CUDA(cudaMemcpyAsync(d_act.p, hp, sizeof(int) * S, cudaMemcpyHostToDevice, s));
+      BP_CUDA(cudaStreamSynchronize(s));
+    };
+    // vacuum state: multipoles only, every site of a system interacting
+    {
+      std::vector<int> act(S, 1);
+      std::vector<Guard> gv(S);
+      for (int it = 1; it <= P.scf_maxit; ++it) {
+        upload_act(act);
+        multipole_internal(*c, mu_v.p, 2, emult.p, s);
+        std::vector<double> rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, d_act.p, s);
+        int left = 0;
+        for (int q = 0; q < S; ++q) {
+          if (!act[q]) continue;
+          it_v[q] = it;
+          if (rms[q] < P.scf_tol) {
+            conv_v[q] = 1;
+            act[q] = 0;
+          } else if (gv[q].diverges(rms[q])) {
+            diverged[q] = 1;
+            act[q] = 0;
+          } else {
+            ++left;
+          }
+        }
+        if (!left) break;
+      }
     }
-    if (it_v > P.scf_maxit) {
-      ok = false;
-      it_v = P.scf_maxit;
-    }
-    auto bem = [&]() {
+    std::vector<char> want(S, 1);
+    auto bem = [&](const std::vector<char>& which) {
       launch(add_vec, cdiv(3 * ns, 256), 256, 0, s, c->site_d.p, mu.p, p.p, 3 * ns);
       rhs_internal(*c, p.p, b.p, f32, s);
-      GmresOut g = solve_bem(*c, b.p, x.p, s);
+      GmresOut g = solve_bem(*c, b.p, x.p, which, s);
       gm_iters += g.iters;
       matvecs += g.matvecs;
       ++solves;
-      last_res = g.rel_res;
-      if (!g.converged) ok = false;
+      for (int q = 0; q < S; ++q) {
+        if (!which[q]) continue;
+        sys_gm[q] += g.sys_iters[q];
+        ++sys_solves[q];
+        sys_res[q] = g.sys_res[q];
+        if (!g.sys_conv[q]) gm_ok[q] = 0;
+      }
     };
-    int it = 0;
-    Guard gd;
-    for (it = 1; it <= P.scf_maxit; ++it) {
-      bem();
-      site_reaction_internal(*c, x.p, react.p, f32, false, s);
-      multipole_internal(*c, mu.p, 0, emult.p, s);
-      double rms = sor_update(*c, mu.p, react.p, emult.p, false, s);
-      if (rms < P.scf_tol) break;
-      gd.check(rms, "dissolved");
+    {
+      std::vector<int> act(S, 1);
+      std::vector<Guard> gd(S);
+      for (int q = 0; q < S; ++q)
+        if (diverged[q]) act[q] = 0;
+      for (int it = 1; it <= P.scf_maxit; ++it) {
+        for (int q = 0; q < S; ++q) want[q] = (char)act[q];
+        bem(want);
+        site_reaction_internal(*c, x.p, react.p, f32, false, s);
+        multipole_internal(*c, mu.p, 0, emult.p, s);
+        upload_act(act);
+        std::vector<double> rms = sor_update(*c, mu.p, react.p, emult.p, false, d_act.p, s);
+        int left = 0;
+        for (int q = 0; q < S; ++q) {
+          if (!act[q]) continue;
+          it_d[q] = it;
+          if (rms[q] < P.scf_tol) {
+            conv_d[q] = 1;
+            act[q] = 0;
+          } else if (gd[q].diverges(rms[q])) {
+            diverged[q] = 1;
+            act[q] = 0;
+          } else {
+            ++left;
+          }
+        }
+        if (!left) break;
+      }
     }
-    if (it > P.scf_maxit) {
-      ok = false;
-      it = P.scf_maxit;
-    }
-    bem();
+    std::fill(want.begin(), want.end(), 1);
+    bem(want);
     site_reaction_internal(*c, x.p, react.p, f32, true, s);
     multipole_internal(*c, mu.p, 1, mult10.p, s);
-    double G_diss = energy_internal(*c, react.p, mult10.p, s);
-    multipole_internal(*c, mu_v.p, 1, mult10.p, s);
-    double G_vac = energy_internal(*c, nullptr, mult10.p, s);
+    std::vector<double> Gd = energy_internal(*c, react.p, mult10.p, s);
+    multipole_internal(*c, mu_v.p, 3, mult10.p, s);
+    std::vector<double> Gv = energy_internal(*c, nullptr, mult10.p, s);
     double t_scf = ts.ms();
-    out->G_diss = G_diss;
-    out->G_vac = G_vac;
-    out->dG_solv_kcal = (G_diss - G_vac) * KCAL_PER_UNIT;
-    out->scf_iters_diss = it;
-    out->scf_iters_vac = it_v;
+    bool ok = true;
+    double Gd_sum = 0.0, Gv_sum = 0.0, res_max = 0.0;
+    int itd_max = 0, itv_max = 0;
+    for (int q = 0; q < S; ++q) {
+      const bool sys_ok = conv_v[q] && conv_d[q] && gm_ok[q] && !diverged[q];
+      ok = ok && sys_ok;
+      Gd_sum += Gd[q];
+      Gv_sum += Gv[q];
+      res_max = std::max(res_max, sys_res[q]);
+      itd_max = std::max(itd_max, it_d[q]);
+      itv_max = std::max(itv_max, it_v[q]);
+      if (per) {
+        bempol_system_result& r = per[q];
+        r.dG_solv_kcal = (Gd[q] - Gv[q]) * KCAL_PER_UNIT;
+        r.G_diss = Gd[q];
+        r.G_vac = Gv[q];
+        r.scf_iters_diss = it_d[q];
+        r.scf_iters_vac = it_v[q];
+        r.gmres_iters = sys_gm[q];
+        r.n_solves = sys_solves[q];
+        r.last_rel_residual = sys_res[q];
+        r.converged = sys_ok ? 1 : 0;
+        r.n_panels = c->h_sys_pan[q + 1] - c->h_sys_pan[q];
+        r.n_sites = c->h_sys_site[q + 1] - c->h_sys_site[q];
+      }
+    }
+    out->G_diss = Gd_sum;
+    out->G_vac = Gv_sum;
+    out->dG_solv_kcal = (Gd_sum - Gv_sum) * KCAL_PER_UNIT;
+    out->scf_iters_diss = itd_max;
+    out->scf_iters_vac = itv_max;
     out->gmres_iters_total = gm_iters;
     out->matvecs_total = matvecs;
     out->n_solves = solves;
-    out->last_rel_residual = last_res;
+    out->last_rel_residual = res_max;
     out->t_setup_ms = t_setup;
     out->t_scf_ms = t_scf;
     // optional arrays
@@ -597,8 +803,38 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
     put(out->mu_diss, mu.p, 3 * (size_t)ns);
     put(out->mu_vac, mu_v.p, 3 * (size_t)ns);
     BP_CUDA(cudaStreamSynchronize(s));
+    c->have_solution = true;
     out->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
+    for (int q = 0; q < S; ++q)
+      if (diverged[q])
+        fail(BEMPOL_ERR_NOT_CONVERGED,
+             "induced-dipole iteration diverges in system " + std::to_string(q) +
+                 " (RMS change grows); sor_omega is outside the convergence range of this polarizability coupling");
     if (!ok) fail(BEMPOL_ERR_NOT_CONVERGED, "GMRES or SCF reached its iteration limit");
+  });
+}
+
+bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
+  return bempol_solve_systems(c, stream, out, nullptr, 0);
+}
+
+bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, double* grad_d, double* grad_Q,
+                              double* grad_pos, bempol_gradient_info* info) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_sites || !c->have_solution) fail(BEMPOL_ERR_STATE, "bempol_gradient needs a completed solve");
+    EventTimer t(s);
+    AdjointOut ao = gradient_internal(*c, grad_q, grad_d, grad_Q, grad_pos, s);
+    const double ms = t.ms();
+    if (info) {
+      info->scf_iters_diss = ao.iters_diss;
+      info->scf_iters_vac = ao.iters_vac;
+      info->gmres_iters_total = ao.gmres_iters;
+      info->n_solves = ao.solves;
+      info->converged = ao.converged ? 1 : 0;
+      info->t_ms = ms;
+    }
+    if (!ao.converged) fail(BEMPOL_ERR_NOT_CONVERGED, "the adjoint GMRES or SCF reached its iteration limit");
   });
 }
 

@@ -40,8 +40,10 @@ __global__ void panel_geom_kernel(const double* __restrict__ verts, const int* _
   v[6] = cx; v[7] = cy; v[8] = cz;
 }
 
-__global__ void morton_kernel(const double4* __restrict__ cen, int n, int npad, double lox, double loy,
-                              double loz, double inv, unsigned long long* __restrict__ keys) {
+// Sort key of panel t: group (10 bits) | Morton code of the centroid in the group's
+// bounding box (30 bits) | caller index (24 bits).
+__global__ void morton_kernel(const double4* __restrict__ cen, int n, int npad, const int* __restrict__ grp,
+                              const double4* __restrict__ gbox, unsigned long long* __restrict__ keys) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= npad) return;
   if (t >= n) {
@@ -49,8 +51,10 @@ __global__ void morton_kernel(const double4* __restrict__ cen, int n, int npad, 
     return;
   }
   double4 c = cen[t];
+  const int g = grp ? grp[t] : 0;
+  const double4 b = gbox[g];  // lo x, y, z and 1 / extent
   auto q = [&](double v, double lo) {
-    double s = (v - lo) * inv;
+    double s = (v - lo) * b.w;
     int iv = (int)(s * 1024.0);
     return (unsigned)min(1023, max(0, iv));
   };
@@ -62,8 +66,8 @@ __global__ void morton_kernel(const double4* __restrict__ cen, int n, int npad, 
     x = (x | (x << 2)) & 0x09249249u;
     return x;
   };
-  unsigned m = (spread(q(c.x, lox)) << 2) | (spread(q(c.y, loy)) << 1) | spread(q(c.z, loz));
-  keys[t] = ((unsigned long long)m << 32) | (unsigned)t;
+  unsigned m = (spread(q(c.x, b.x)) << 2) | (spread(q(c.y, b.y)) << 1) | spread(q(c.z, b.z));
+  keys[t] = ((unsigned long long)g << 54) | ((unsigned long long)m << 24) | (unsigned)t;
 }
 
 // one compare-exchange stage of a bitonic sort (ascending)
@@ -85,7 +89,7 @@ __global__ void perm_from_keys(const unsigned long long* __restrict__ keys, int 
                                int* __restrict__ iperm) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int p = (int)(keys[i] & 0xffffffffu);
+  int p = (int)(keys[i] & 0xffffffu);
   perm[i] = p;
   iperm[p] = i;
 }
@@ -141,9 +145,10 @@ __global__ void gather_geometry(const int* __restrict__ perm, int n, int K, cons
   }
 }
 
-void validate_closed(const int* tris, int n, int nv) {
-  // every directed edge must appear once and its reverse once (closed, consistently oriented)
-  std::vector<unsigned long long> e;
+// Every directed edge must appear once and its reverse once, in a triangle of the
+// same group: each body is a closed, consistently oriented surface of its own.
+void validate_closed(const int* tris, int n, int nv, const std::vector<int>& grp) {
+  std::vector<std::pair<unsigned long long, int>> e;
   e.reserve(3 * (size_t)n);
   for (int t = 0; t < n; ++t) {
     for (int k = 0; k < 3; ++k) {
@@ -151,24 +156,29 @@ void validate_closed(const int* tris, int n, int nv) {
       if (a < 0 || a >= nv || b < 0 || b >= nv)
         fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has a vertex index out of range");
       if (a == b) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " repeats a vertex");
-      e.push_back(((unsigned long long)(unsigned)a << 32) | (unsigned)b);
+      e.push_back({((unsigned long long)(unsigned)a << 32) | (unsigned)b, grp.empty() ? 0 : grp[t]});
     }
   }
   std::sort(e.begin(), e.end());
   for (size_t i = 1; i < e.size(); ++i)
-    if (e[i] == e[i - 1]) fail(BEMPOL_ERR_MESH, "a directed edge is used twice (inconsistent orientation or non-manifold mesh)");
-  for (auto k : e) {
-    unsigned long long r = ((k & 0xffffffffull) << 32) | (k >> 32);
-    if (!std::binary_search(e.begin(), e.end(), r))
+    if (e[i].first == e[i - 1].first)
+      fail(BEMPOL_ERR_MESH, "a directed edge is used twice (inconsistent orientation or non-manifold mesh)");
+  for (auto& k : e) {
+    unsigned long long r = ((k.first & 0xffffffffull) << 32) | (k.first >> 32);
+    auto it = std::lower_bound(e.begin(), e.end(), std::make_pair(r, -1));
+    if (it == e.end() || it->first != r)
       fail(BEMPOL_ERR_MESH, "the mesh is not closed: an edge has no opposite neighbour");
+    if (it->second != k.second) fail(BEMPOL_ERR_MESH, "two bodies share an edge: each body must be closed");
   }
 }
 
 }  // namespace
 
-void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, cudaStream_t s) {
+void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, const std::vector<int>& h_group,
+                    cudaStream_t s) {
   const int n = c.n;
-  validate_closed(h_tris_for_check, n, c.nv);
+  const int G = c.ngroup;
+  validate_closed(h_tris_for_check, n, c.nv, h_group);
   DBuf<int> d_tris;
   d_tris.alloc(3 * (size_t)n);
   BP_CUDA(cudaMemcpyAsync(d_tris.p, h_tris_for_check, 3 * sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s));
@@ -179,32 +189,49 @@ void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, 
   v9_c.alloc(9 * (size_t)n);
   launch(panel_geom_kernel, cdiv(n, 256), 256, 0, s, d_verts, d_tris.p, n, cen_c.p, nrm_c.p, v9_c.p);
   BP_CHECK_LAUNCH();
-  // areas and the centroid bounding box on the host (validation, Morton normalisation)
+  // areas and the centroid bounding box of each group on the host (validation, Morton normalisation)
   std::vector<double4> h(n);
   BP_CUDA(cudaMemcpyAsync(h.data(), cen_c.p, sizeof(double4) * (size_t)n, cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
-  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  std::vector<double> lo(3 * (size_t)G, 1e300), hi(3 * (size_t)G, -1e300);
   c.max_area = 0.0;
   for (int t = 0; t < n; ++t) {
     if (!(h[t].w > 0.0)) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has zero or invalid area");
     c.max_area = std::max(c.max_area, h[t].w);
+    const int g = h_group.empty() ? 0 : h_group[t];
     double v[3] = {h[t].x, h[t].y, h[t].z};
     for (int d = 0; d < 3; ++d) {
-      lo[d] = std::min(lo[d], v[d]);
-      hi[d] = std::max(hi[d], v[d]);
+      lo[3 * g + d] = std::min(lo[3 * g + d], v[d]);
+      hi[3 * g + d] = std::max(hi[3 * g + d], v[d]);
     }
   }
-  double ext = std::max(hi[0] - lo[0], std::max(hi[1] - lo[1], hi[2] - lo[2]));
-  if (!(ext > 0.0)) ext = 1.0;
+  std::vector<double4> gbox(G);
+  for (int g = 0; g < G; ++g) {
+    double ext = std::max(hi[3 * g] - lo[3 * g], std::max(hi[3 * g + 1] - lo[3 * g + 1], hi[3 * g + 2] - lo[3 * g + 2]));
+    if (!(ext > 0.0)) ext = 1.0;
+    gbox[g] = make_double4(lo[3 * g], lo[3 * g + 1], lo[3 * g + 2], 1.0 / ext);
+  }
   for (int d = 0; d < 3; ++d) {
-    c.bbox_lo[d] = lo[d];
-    c.bbox_hi[d] = hi[d];
+    c.bbox_lo[d] = 1e300;
+    c.bbox_hi[d] = -1e300;
+    for (int g = 0; g < G; ++g) {
+      c.bbox_lo[d] = std::min(c.bbox_lo[d], lo[3 * g + d]);
+      c.bbox_hi[d] = std::max(c.bbox_hi[d], hi[3 * g + d]);
+    }
+  }
+  DBuf<double4> d_gbox;
+  d_gbox.alloc(G);
+  BP_CUDA(cudaMemcpyAsync(d_gbox.p, gbox.data(), sizeof(double4) * G, cudaMemcpyHostToDevice, s));
+  DBuf<int> d_grp;
+  if (!h_group.empty()) {
+    d_grp.alloc(n);
+    BP_CUDA(cudaMemcpyAsync(d_grp.p, h_group.data(), sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s));
   }
   int npad = 1;
   while (npad < n) npad <<= 1;
   DBuf<unsigned long long> keys;
   keys.alloc(npad);
-  launch(morton_kernel, cdiv(npad, 256), 256, 0, s, cen_c.p, n, npad, lo[0], lo[1], lo[2], 1.0 / ext, keys.p);
+  launch(morton_kernel, cdiv(npad, 256), 256, 0, s, cen_c.p, n, npad, d_grp.p, d_gbox.p, keys.p);
   BP_CHECK_LAUNCH();
   for (int k = 2; k <= npad; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) launch(bitonic_step, cdiv(npad, 256), 256, 0, s, keys.p, npad, j, k);
@@ -214,12 +241,32 @@ void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, 
   launch(perm_from_keys, cdiv(n, 256), 256, 0, s, keys.p, n, c.perm.p, c.iperm.p);
   BP_CHECK_LAUNCH();
   {
-    // sorted Morton codes (high 32 bits of the keys) for the host-side tree topology
+    // sorted Morton codes for the host-side tree topology; group ranges and tags
     std::vector<unsigned long long> hk(n);
     BP_CUDA(cudaMemcpyAsync(hk.data(), keys.p, sizeof(unsigned long long) * (size_t)n, cudaMemcpyDeviceToHost, s));
     BP_CUDA(cudaStreamSynchronize(s));
     c.h_morton.resize(n);
-    for (int i = 0; i < n; ++i) c.h_morton[i] = (unsigned)(hk[i] >> 32);
+    std::vector<int> tag(n), sys(n);
+    c.h_gpan.assign(G + 1, 0);
+    for (int i = 0; i < n; ++i) {
+      c.h_morton[i] = (unsigned)((hk[i] >> 24) & 0x3fffffffu);
+      tag[i] = (int)(hk[i] >> 54);
+      sys[i] = c.h_grp_sys[tag[i]];
+      ++c.h_gpan[tag[i] + 1];
+    }
+    for (int g = 0; g < G; ++g) c.h_gpan[g + 1] += c.h_gpan[g];
+    c.h_sys_pan.assign(c.nsys + 1, 0);
+    for (int q = 0; q <= c.nsys; ++q) c.h_sys_pan[q] = c.h_gpan[c.h_sys_grp[q]];
+    auto up = [&](DBuf<int>& d, const std::vector<int>& v) {
+      d.alloc(v.size());
+      BP_CUDA(cudaMemcpyAsync(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice, s));
+    };
+    up(c.ptag, tag);
+    up(c.psys, sys);
+    up(c.gpan, c.h_gpan);
+    up(c.sys_pan, c.h_sys_pan);
+    up(c.grp_sys, c.h_grp_sys);
+    BP_CUDA(cudaStreamSynchronize(s));
   }
   c.tgt64.alloc(n);
   c.tgt32.alloc(n);

@@ -1,15 +1,21 @@
 // FP64 restarted GMRES (Saad and Schultz; Sec. "The boundary element method")
 // with optional FP64 iterative refinement around a lower-precision operator.
 //
+// Every system of the context (independent surfaces sharing one set of launches)
+// runs its own Arnoldi process in lockstep: one matrix-vector product serves all
+// systems, inner products are segmented by system, and each system has its own
+// Hessenberg matrix, Givens rotations, residual estimate and stopping test.  A
+// system that has converged stops updating while the others go on.
+//
 // Arnoldi: classical Gram-Schmidt applied twice (CGS2) with every inner product
-// formed by a deterministic two-stage reduction (per-block partials, then a
-// fixed-order sum), so reruns are bit-identical.  Givens rotations, the residual
-// estimate and the triangular solve run in single-thread device kernels; the
-// host reads one scalar per iteration to decide convergence.
+// formed by a deterministic two-stage reduction (per-chunk partials, then a
+// fixed-order sum per system), so reruns are bit-identical.  Givens rotations,
+// the residual estimates and the triangular solves run in one device thread per
+// system; the host reads one scalar per system and iteration.
 //
 // Refinement (when params.residual_op != params.op): x <- x + A_op^{-1} (b - A_res x),
 // the residual formed in FP64 with the more accurate operator, each inner solve
-// run to params.inner_tol, until ||b - A_res x|| / ||b|| < params.gmres_tol.
+// run to params.inner_tol, until ||b - A_res x|| / ||b|| < params.gmres_tol (per system).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -20,67 +26,100 @@ namespace bp {
 
 namespace {
 
-constexpr int DOT_BLOCKS = 256;
 constexpr int DOT_TPB = 256;
 constexpr int MAXV = 16;  // basis vectors handled per multi-dot pass
 
-// out[k] = V_k . w for k < nv, in one launch.  Each block writes its partial sums
-// partial[b][k] (chunks of MAXV vectors per pass over its slice); the last block to
-// finish (atomic ticket) adds the partials in block order, so the result does not
-// depend on scheduling, and resets the ticket for the next call.
+// out[s * ldo + k] = sum over the elements of system s of V_k . w, for k < nv, in one
+// launch.  Block b handles chunks b, b + gridDim.x, ... and writes the partial sums
+// partial[chunk][k]; the last block to finish (atomic ticket) adds, for every
+// system, its chunks' partials in chunk order -- so the result does not depend on
+// scheduling -- and resets the ticket for the next call.  Systems with
+// active[s] == 0 are skipped (NULL = all active).
 __global__ void __launch_bounds__(DOT_TPB) multidot_kernel(const double* __restrict__ V, size_t ld, int nv,
-                                                           const double* __restrict__ w, int len,
+                                                           const double* __restrict__ w,
+                                                           const int4* __restrict__ chunks, int nchunk,
+                                                           const int* __restrict__ chunk_ptr, int nsys,
+                                                           const int* __restrict__ active,
                                                            double* __restrict__ partial, int ldp,
                                                            unsigned* __restrict__ ticket, double* __restrict__ out,
-                                                           int accumulate) {
+                                                           int ldo, int accumulate) {
   __shared__ double sh[MAXV][DOT_TPB / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < nv; k0 += MAXV) {
-    const int cnt = min(MAXV, nv - k0);
-    double acc[MAXV];
+  for (int ci = blockIdx.x; ci < nchunk; ci += gridDim.x) {
+    const int4 C = chunks[ci];
+    if (active && !active[C.x]) continue;  // uniform across the block
+    for (int k0 = 0; k0 < nv; k0 += MAXV) {
+      const int cnt = min(MAXV, nv - k0);
+      double acc[MAXV];
 #pragma unroll
-    for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
-    for (int i = blockIdx.x * DOT_TPB + threadIdx.x; i < len; i += gridDim.x * DOT_TPB) {
-      const double wi = w[i];
+      for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
+      for (int i = C.y + threadIdx.x; i < C.z; i += DOT_TPB) {
+        const double wi = w[i];
 #pragma unroll
-      for (int k = 0; k < MAXV; ++k)
-        if (k < cnt) acc[k] += V[(size_t)(k0 + k) * ld + i] * wi;
-    }
+        for (int k = 0; k < MAXV; ++k)
+          if (k < cnt) acc[k] += V[(size_t)(k0 + k) * ld + i] * wi;
+      }
 #pragma unroll
-    for (int k = 0; k < MAXV; ++k) {
-      double v = acc[k];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if (lane == 0) sh[k][warp] = v;
+      for (int k = 0; k < MAXV; ++k) {
+        double v = acc[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[k][warp] = v;
+      }
+      __syncthreads();
+      if ((int)threadIdx.x < cnt) {
+        double v = 0.0;
+        for (int wv = 0; wv < DOT_TPB / 32; ++wv) v += sh[threadIdx.x][wv];
+        partial[(size_t)ci * ldp + k0 + threadIdx.x] = v;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    if ((int)threadIdx.x < cnt) {
-      double v = 0.0;
-      for (int wv = 0; wv < DOT_TPB / 32; ++wv) v += sh[threadIdx.x][wv];
-      partial[(size_t)blockIdx.x * ldp + k0 + threadIdx.x] = v;
-    }
-    __syncthreads();
   }
   __threadfence();
   if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  for (int k = threadIdx.x; k < nv; k += DOT_TPB) {
+  for (int t = threadIdx.x; t < nsys * nv; t += DOT_TPB) {
+    const int sy = t / nv, k = t - sy * nv;
+    if (active && !active[sy]) continue;
     double v = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) v += __ldcg(partial + (size_t)b * ldp + k);
-    out[k] = accumulate ? out[k] + v : v;
+    for (int ci = chunk_ptr[sy]; ci < chunk_ptr[sy + 1]; ++ci) v += __ldcg(partial + (size_t)ci * ldp + k);
+    double* o = out + (size_t)sy * ldo + k;
+    *o = accumulate ? *o + v : v;
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
 
-// w -= sum_k V_k h_k   (k < nv)
-__global__ void subtract_proj(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h,
-                              double* __restrict__ w, int len) {
+__device__ __forceinline__ int sys_of(const int* __restrict__ psys, int i, int n) {
+  return psys[i < n ? i : i - n];
+}
+
+// w -= sum_k V_k h[s][k]   (k < nv, s the system of the element; active systems only)
+__global__ void subtract_proj(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h, int ldh,
+                              const int* __restrict__ psys, const int* __restrict__ active, double* __restrict__ w,
+                              int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= len) return;
+  if (i >= 2 * n) return;
+  const int sy = sys_of(psys, i, n);
+  if (active && !active[sy]) return;
+  const double* hs = h + (size_t)sy * ldh;
   double v = w[i];
-  for (int k = 0; k < nv; ++k) v -= V[(size_t)k * ld + i] * h[k];
+  for (int k = 0; k < nv; ++k) v -= V[(size_t)k * ld + i] * hs[k];
   w[i] = v;
+}
+
+// x += sum_{k < kk[s]} V_k y[s][k]
+__global__ void add_basis(const double* __restrict__ V, size_t ld, const double* __restrict__ y, int ldy,
+                          const int* __restrict__ kk, const int* __restrict__ psys, double* __restrict__ x, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  const int sy = sys_of(psys, i, n);
+  const int k = kk[sy];
+  if (k == 0) return;
+  const double* ys = y + (size_t)sy * ldy;
+  double v = x[i];
+  for (int q = 0; q < k; ++q) v += V[(size_t)q * ld + i] * ys[q];
+  x[i] = v;
 }
 
 __global__ void axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
@@ -89,55 +128,73 @@ __global__ void axpby(double a, const double* __restrict__ x, double b, const do
   if (i < len) out[i] = a * x[i] + b * y[i];
 }
 
-// v_out = w / sqrt(*nrm2)  (the norm read on the device)
-__global__ void normalize_kernel(const double* __restrict__ w, const double* __restrict__ nrm2,
-                                 double* __restrict__ out, int len) {
+// v_out = w / sqrt(nrm2[s * ldn]) for the active systems (the norm read on the device)
+__global__ void normalize_kernel(const double* __restrict__ w, const double* __restrict__ nrm2, int ldn,
+                                 const int* __restrict__ psys, const int* __restrict__ active,
+                                 double* __restrict__ out, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < len) out[i] = w[i] / sqrt(*nrm2);
+  if (i >= 2 * n) return;
+  const int sy = sys_of(psys, i, n);
+  if (active && !active[sy]) return;
+  out[i] = w[i] / sqrt(nrm2[(size_t)sy * ldn]);
 }
 
-// Givens step for column j of the Hessenberg matrix.  hcol[0..j] = projections,
-// *nrm2 = |w|^2 gives h_{j+1,j}.  State: cs, sn [m], g [m+1].  Writes |g_{j+1}| to *res.
-__global__ void givens_kernel(double* __restrict__ H, int ldh, int j, const double* __restrict__ hcol,
-                              const double* __restrict__ nrm2, double* __restrict__ cs, double* __restrict__ sn,
-                              double* __restrict__ g, double* __restrict__ res) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double* col = H + (size_t)j * ldh;
-  for (int k = 0; k <= j; ++k) col[k] = hcol[k];
-  col[j + 1] = sqrt(*nrm2);
+// Givens step for column j of system s's Hessenberg matrix (one thread per active
+// system).  hcol[s][0..j] = projections, nrm2[s] = |w|^2 gives h_{j+1,j}.  State
+// cs, sn [m], g [m+1] per system.  Writes |g_{j+1}| to res[s].
+__global__ void givens_kernel(double* __restrict__ H, int ldh, size_t sH, int j, const double* __restrict__ hcol,
+                              int ldc, const double* __restrict__ nrm2, double* __restrict__ cs,
+                              double* __restrict__ sn, double* __restrict__ g, int ldg, double* __restrict__ res,
+                              const int* __restrict__ active, int nsys) {
+  const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sy >= nsys || (active && !active[sy])) return;
+  double* col = H + sy * sH + (size_t)j * ldh;
+  const double* hc = hcol + (size_t)sy * ldc;
+  double* c_ = cs + (size_t)sy * ldg;
+  double* s_ = sn + (size_t)sy * ldg;
+  double* g_ = g + (size_t)sy * ldg;
+  for (int k = 0; k <= j; ++k) col[k] = hc[k];
+  col[j + 1] = sqrt(nrm2[(size_t)sy * ldc]);
   for (int k = 0; k < j; ++k) {
-    double t = cs[k] * col[k] + sn[k] * col[k + 1];
-    col[k + 1] = -sn[k] * col[k] + cs[k] * col[k + 1];
+    double t = c_[k] * col[k] + s_[k] * col[k + 1];
+    col[k + 1] = -s_[k] * col[k] + c_[k] * col[k + 1];
     col[k] = t;
   }
   double a = col[j], b = col[j + 1];
   double r = hypot(a, b);
   double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
-  cs[j] = c;
-  sn[j] = s;
+  c_[j] = c;
+  s_[j] = s;
   col[j] = r;
   col[j + 1] = 0.0;
-  g[j + 1] = -s * g[j];
-  g[j] = c * g[j];
-  *res = fabs(g[j + 1]);
+  g_[j + 1] = -s * g_[j];
+  g_[j] = c * g_[j];
+  res[sy] = fabs(g_[j + 1]);
 }
 
-// solve the k x k upper-triangular system R y = g
-__global__ void backsolve_kernel(const double* __restrict__ H, int ldh, int k, const double* __restrict__ g,
-                                 double* __restrict__ y) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// solve the k[s] x k[s] upper-triangular system R y = g of every system
+__global__ void backsolve_kernel(const double* __restrict__ H, int ldh, size_t sH, const int* __restrict__ kk,
+                                 const double* __restrict__ g, int ldg, double* __restrict__ y, int nsys) {
+  const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sy >= nsys) return;
+  const int k = kk[sy];
+  const double* Hs = H + sy * sH;
+  const double* gs = g + (size_t)sy * ldg;
+  double* ys = y + (size_t)sy * ldg;
   for (int i = k - 1; i >= 0; --i) {
-    double v = g[i];
-    for (int c = i + 1; c < k; ++c) v -= H[(size_t)c * ldh + i] * y[c];
-    y[i] = v / H[(size_t)i * ldh + i];
+    double v = gs[i];
+    for (int c = i + 1; c < k; ++c) v -= Hs[(size_t)c * ldh + i] * ys[c];
+    ys[i] = v / Hs[(size_t)i * ldh + i];
   }
 }
 
-__global__ void set_g0(double* __restrict__ g, const double* __restrict__ nrm2, int m) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    g[0] = sqrt(*nrm2);
-    for (int i = 1; i <= m; ++i) g[i] = 0.0;
-  }
+__global__ void set_g0(double* __restrict__ g, int ldg, const double* __restrict__ nrm2, int ldn, int m,
+                       const int* __restrict__ active, int nsys) {
+  const int sy = blockIdx.x * blockDim.x + threadIdx.x;
+  if (sy >= nsys || (active && !active[sy])) return;
+  double* gs = g + (size_t)sy * ldg;
+  gs[0] = sqrt(nrm2[(size_t)sy * ldn]);
+  for (int i = 1; i <= m; ++i) gs[i] = 0.0;
 }
 
 __global__ void permute_kernel(const int* __restrict__ perm, int n, int nb, const double* __restrict__ src,
@@ -157,122 +214,187 @@ struct Work {
   size_t ld;
   double* H;
   int ldh;
-  double *cs, *sn, *g, *y, *hcol, *nrm2, *res, *partial;
+  size_t sH;               // stride between systems' Hessenberg matrices
+  int lds;                 // stride between systems' small vectors (m + 2)
+  double *cs, *sn, *g, *y, *hcol, *h2, *nrm2, *res, *partial;
   int ldp;
   unsigned* ticket;
+  int *active, *kk;        // device [S] flags and Krylov sizes
 };
 
-void multidot(Ctx& c, const Work& w, const double* V, int nv, const double* vec, int len, double* out,
-              bool accumulate, cudaStream_t s) {
-  launch(multidot_kernel, DOT_BLOCKS, DOT_TPB, 0, s, V, w.ld, nv, vec, len, w.partial, w.ldp, w.ticket, out,
-         accumulate ? 1 : 0);
-  (void)c;
-}
-
-double read_scalar(Ctx& c, const double* d, cudaStream_t s) {
-  BP_CUDA(cudaMemcpyAsync(c.h_pinned + 2, d, sizeof(double), cudaMemcpyDeviceToHost, s));
-  BP_CUDA(cudaStreamSynchronize(s));
-  return c.h_pinned[2];
+void multidot(Ctx& c, const Work& w, const double* V, int nv, const double* vec, double* out, const int* active,
+              cudaStream_t s) {
+  launch(multidot_kernel, std::min(c.nchunk, 1024), DOT_TPB, 0, s, V, w.ld, nv, vec, c.chunks.p, c.nchunk,
+         c.chunk_ptr.p, c.nsys, active, w.partial, w.ldp, w.ticket, out, w.lds, 0);
 }
 
 Work workspace(Ctx& c) {
   const int len = 2 * c.n;
+  const int S = c.nsys;
   int m = std::max(1, c.par.gmres_restart);
-  if (c.gm_m != m || c.gm_V.n < (size_t)(m + 1) * len) {
+  const int lds = m + 2;
+  if (c.gm_m != m || c.gm_V.n < (size_t)(m + 1) * len || c.gm_H.n < (size_t)S * (m + 1) * m) {
     c.gm_V.alloc((size_t)(m + 1) * len);
-    c.gm_H.alloc((size_t)(m + 1) * m);
-    c.gm_small.alloc(4 * (size_t)(m + 2) + 8);
+    BP_CUDA(cudaMemset(c.gm_V.p, 0, sizeof(double) * c.gm_V.n));  // finite values in every slot
+    c.gm_H.alloc((size_t)S * (m + 1) * m);
+    c.gm_small.alloc((size_t)S * 8 * lds);
     c.gm_m = m;
   }
-  const size_t ndots = (size_t)DOT_BLOCKS * (m + 2) + m + 2;
+  const size_t ndots = (size_t)c.nchunk * lds;
   if (c.gm_dots.n < ndots) c.gm_dots.alloc(ndots);
   if (!c.gm_ticket.p) {
     c.gm_ticket.alloc(1);
     BP_CUDA(cudaMemset(c.gm_ticket.p, 0, sizeof(unsigned)));
   }
+  if (c.gm_flags.n < 2 * (size_t)S) c.gm_flags.alloc(2 * (size_t)S);
   Work w;
   w.V = c.gm_V.p;
   w.ld = len;
   w.H = c.gm_H.p;
   w.ldh = m + 1;
+  w.sH = (size_t)(m + 1) * m;
+  w.lds = lds;
   double* sm = c.gm_small.p;
+  const size_t blk = (size_t)S * lds;
   w.cs = sm;
-  w.sn = sm + (m + 2);
-  w.g = sm + 2 * (m + 2);
-  w.y = sm + 3 * (m + 2);
-  w.nrm2 = sm + 4 * (m + 2);
-  w.res = w.nrm2 + 1;
+  w.sn = sm + blk;
+  w.g = sm + 2 * blk;
+  w.y = sm + 3 * blk;
+  w.hcol = sm + 4 * blk;
+  w.h2 = sm + 5 * blk;
+  w.nrm2 = sm + 6 * blk;   // nrm2[s * lds]
+  w.res = sm + 7 * blk;    // res[s]
   w.partial = c.gm_dots.p;
-  w.ldp = m + 2;
+  w.ldp = lds;
   w.ticket = c.gm_ticket.p;
-  w.hcol = c.gm_dots.p + (size_t)DOT_BLOCKS * (m + 2);
+  w.active = c.gm_flags.p;
+  w.kk = c.gm_flags.p + S;
   return w;
 }
 
-// GMRES on A_op x = b from the initial x; stops when ||b - A x|| <= tol_abs (true
+// per-system squared norms of v (device; host copy returned)
+std::vector<double> sys_norm2(Ctx& c, const Work& w, const double* v, const int* active, cudaStream_t s) {
+  multidot(c, w, v, 1, v, w.nrm2, active, s);
+  BP_CUDA(cudaMemcpy2DAsync(c.h_pinned, sizeof(double), w.nrm2, sizeof(double) * w.lds, sizeof(double), c.nsys,
+                            cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  return std::vector<double>(c.h_pinned, c.h_pinned + c.nsys);
+}
+
+void put_flags(Ctx& c, int* d, const std::vector<int>& h, cudaStream_t s) {
+  int* hp = reinterpret_cast<int*>(c.h_pinned + 2 * c.nsys);
+  std::copy(h.begin(), h.end(), hp);
+  BP_CUDA(cudaMemcpyAsync(d, hp, sizeof(int) * h.size(), cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaStreamSynchronize(s));  // the pinned staging area is reused right away
+}
+
+// GMRES on A_op x = b from the initial x for the systems with tol_abs[s] >= 0 (the
+// others are left alone); system s stops when ||b - A x||_s <= tol_abs[s] (true
 // residual at restarts and on exit, the Givens estimate inside a cycle).
-GmresOut gmres(Ctx& c, int op, const double* b, double* x, double tol_abs, int maxit, cudaStream_t s) {
-  const int len = 2 * c.n;
+// rres[s] receives the final true residual norm of each solved system.
+GmresOut gmres(Ctx& c, int op, const double* b, double* x, const std::vector<double>& tol_abs, int maxit,
+               std::vector<double>& rres, cudaStream_t s) {
+  const int n = c.n, len = 2 * n, S = c.nsys;
   Work w = workspace(c);
   const int m = c.gm_m;
   const int tb = 256, nb = cdiv(len, tb);
   double* r = c.vec_a.p;
   GmresOut out;
+  out.sys_iters.assign(S, 0);
+  out.sys_conv.assign(S, 0);
+  std::vector<int> todo(S, 0), act(S, 0), kk(S, 0);
+  for (int q = 0; q < S; ++q) todo[q] = tol_abs[q] >= 0.0;
+  rres.assign(S, 0.0);
   int total = 0;
   while (true) {
-    // r = b - A x
+    // r = b - A x, per-system norms
+    put_flags(c, w.active, todo, s);
+    c.mv_active = w.active;
     matvec_internal(c, x, r, op, s);
+    c.mv_active = nullptr;
     ++out.matvecs;
     launch(axpby, nb, tb, 0, s, 1.0, b, -1.0, r, r, len);
-    multidot(c, w, r, 1, r, len, w.nrm2, false, s);
-    double beta = std::sqrt(read_scalar(c, w.nrm2, s));
-    out.rel_res = beta;
-    if (beta <= tol_abs) {
-      out.converged = true;
-      break;
+    std::vector<double> nr = sys_norm2(c, w, r, w.active, s);
+    int nact = 0;
+    for (int q = 0; q < S; ++q) {
+      if (!todo[q]) continue;
+      rres[q] = std::sqrt(nr[q]);
+      if (rres[q] <= tol_abs[q]) {
+        out.sys_conv[q] = 1;
+        todo[q] = 0;
+      } else {
+        ++nact;
+      }
     }
-    if (total >= maxit) break;
-    launch(normalize_kernel, nb, tb, 0, s, r, w.nrm2, w.V, len);
-    launch(set_g0, 1, 1, 0, s, w.g, w.nrm2, m);
+    if (nact == 0 || total >= maxit) break;
+    act = todo;
+    put_flags(c, w.active, act, s);
+    launch(normalize_kernel, nb, tb, 0, s, r, w.nrm2, w.lds, c.psys.p, w.active, w.V, n);
+    launch(set_g0, cdiv(S, 64), 64, 0, s, w.g, w.lds, w.nrm2, w.lds, m, w.active, S);
     BP_CHECK_LAUNCH();
-    int k = 0;
+    std::fill(kk.begin(), kk.end(), 0);
     for (int j = 0; j < m && total < maxit; ++j) {
       double* vj = w.V + (size_t)j * w.ld;
       double* wv = w.V + (size_t)(j + 1) * w.ld;
+      c.mv_active = w.active;
       matvec_internal(c, vj, wv, op, s);
+      c.mv_active = nullptr;
       ++out.matvecs;
-      // CGS2
-      multidot(c, w, w.V, j + 1, wv, len, w.hcol, false, s);
-      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.hcol, wv, len);
-      double* h2 = w.y;  // scratch for the second pass
-      multidot(c, w, w.V, j + 1, wv, len, h2, false, s);
-      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, h2, wv, len);
-      launch(axpby, cdiv(j + 1, 64), 64, 0, s, 1.0, w.hcol, 1.0, h2, w.hcol, j + 1);
-      multidot(c, w, wv, 1, wv, len, w.nrm2, false, s);
-      launch(givens_kernel, 1, 1, 0, s, w.H, w.ldh, j, w.hcol, w.nrm2, w.cs, w.sn, w.g, w.res);
-      launch(normalize_kernel, nb, tb, 0, s, wv, w.nrm2, wv, len);
+      // CGS2, per system
+      multidot(c, w, w.V, j + 1, wv, w.hcol, w.active, s);
+      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.hcol, w.lds, c.psys.p, w.active, wv, n);
+      multidot(c, w, w.V, j + 1, wv, w.h2, w.active, s);
+      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.h2, w.lds, c.psys.p, w.active, wv, n);
+      launch(axpby, cdiv(S * w.lds, 256), 256, 0, s, 1.0, w.hcol, 1.0, w.h2, w.hcol, S * w.lds);
+      multidot(c, w, wv, 1, wv, w.nrm2, w.active, s);
+      launch(givens_kernel, cdiv(S, 64), 64, 0, s, w.H, w.ldh, w.sH, j, w.hcol, w.lds, w.nrm2, w.cs, w.sn, w.g,
+             w.lds, w.res, w.active, S);
+      launch(normalize_kernel, nb, tb, 0, s, wv, w.nrm2, w.lds, c.psys.p, w.active, wv, n);
       BP_CHECK_LAUNCH();
       ++total;
       ++out.iters;
-      k = j + 1;
-      double est = read_scalar(c, w.res, s);
-      if (!(est > tol_abs)) break;
+      BP_CUDA(cudaMemcpyAsync(c.h_pinned, w.res, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
+      BP_CUDA(cudaStreamSynchronize(s));
+      bool any = false, changed = false;
+      for (int q = 0; q < S; ++q) {
+        if (!act[q]) continue;
+        kk[q] = j + 1;
+        ++out.sys_iters[q];
+        if (!(c.h_pinned[q] > tol_abs[q])) {
+          act[q] = 0;
+          changed = true;
+        } else {
+          any = true;
+        }
+      }
+      if (!any) break;
+      if (changed) put_flags(c, w.active, act, s);
     }
-    launch(backsolve_kernel, 1, 1, 0, s, w.H, w.ldh, k, w.g, w.y);
-    // x += V y   (subtract_proj with -y)
-    launch(axpby, cdiv(k, 64), 64, 0, s, -1.0, w.y, 0.0, w.y, w.y, k);
-    launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, k, w.y, x, len);
+    // x += V y per system
+    put_flags(c, w.kk, kk, s);
+    launch(backsolve_kernel, cdiv(S, 64), 64, 0, s, w.H, w.ldh, w.sH, w.kk, w.g, w.lds, w.y, S);
+    launch(add_basis, nb, tb, 0, s, w.V, w.ld, w.y, w.lds, w.kk, c.psys.p, x, n);
     BP_CHECK_LAUNCH();
   }
+  out.converged = true;
+  for (int q = 0; q < S; ++q)
+    if (tol_abs[q] >= 0.0 && !out.sys_conv[q]) out.converged = false;
   return out;
 }
 
 }  // namespace
 
 double dot_dev(Ctx& c, const double* a, const double* b, int len, cudaStream_t s) {
+  // plain FP64 dot over the whole vector (a single-system segmentation is not needed)
+  (void)len;
   Work w = workspace(c);
-  multidot(c, w, a, 1, b, len, w.nrm2, false, s);
-  return read_scalar(c, w.nrm2, s);
+  multidot(c, w, a, 1, b, w.nrm2, nullptr, s);
+  BP_CUDA(cudaMemcpy2DAsync(c.h_pinned, sizeof(double), w.nrm2, sizeof(double) * w.lds, sizeof(double), c.nsys,
+                            cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  double v = 0.0;
+  for (int q = 0; q < c.nsys; ++q) v += c.h_pinned[q];
+  return v;
 }
 
 void permute_to_internal(const Ctx& c, const double* src, double* dst, int nb, cudaStream_t s) {
@@ -285,46 +407,101 @@ void permute_to_caller(const Ctx& c, const double* src, double* dst, int nb, cud
   BP_CHECK_LAUNCH();
 }
 
-GmresOut solve_bem(Ctx& c, const double* b, double* x, cudaStream_t s) {
-  const int len = 2 * c.n;
-  double bn = std::sqrt(dot_dev(c, b, b, len, s));
-  if (bn == 0.0) {
-    BP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * len, s));
-    GmresOut o;
-    o.converged = true;
-    return o;
-  }
-  const double tol = c.par.gmres_tol * bn;
-  if (c.par.residual_op == c.par.op) {
-    GmresOut o = gmres(c, c.par.op, b, x, tol, c.par.gmres_maxit, s);
-    o.rel_res /= bn;
-    return o;
-  }
-  // iterative refinement
+GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s) {
+  const int n = c.n, len = 2 * n, S = c.nsys;
+  Work w = workspace(c);
+  std::vector<int> all(S, 1);
+  for (int q = 0; q < S; ++q) all[q] = want.empty() ? 1 : (want[q] ? 1 : 0);
+  put_flags(c, w.active, all, s);
+  std::vector<double> bn2 = sys_norm2(c, w, b, w.active, s);
+  std::vector<double> bn(S, 0.0), tol(S, -1.0);
   GmresOut tot;
+  tot.sys_iters.assign(S, 0);
+  tot.sys_res.assign(S, 0.0);
+  tot.sys_conv.assign(S, 1);
+  std::vector<int> zero_sys(S, 0);
+  bool any_zero = false;
+  for (int q = 0; q < S; ++q) {
+    if (!all[q]) continue;
+    bn[q] = std::sqrt(bn2[q]);
+    if (bn[q] == 0.0) {
+      zero_sys[q] = 1;  // b = 0: x = 0 exactly
+      any_zero = true;
+    } else {
+      tol[q] = c.par.gmres_tol * bn[q];
+      tot.sys_conv[q] = 0;
+    }
+  }
+  if (any_zero) {
+    for (int q = 0; q < S; ++q)
+      if (zero_sys[q]) {
+        BP_CUDA(cudaMemsetAsync(x + c.h_sys_pan[q], 0, sizeof(double) * (c.h_sys_pan[q + 1] - c.h_sys_pan[q]), s));
+        BP_CUDA(cudaMemsetAsync(x + n + c.h_sys_pan[q], 0,
+                                sizeof(double) * (c.h_sys_pan[q + 1] - c.h_sys_pan[q]), s));
+      }
+  }
+  auto finish = [&](const std::vector<double>& rn) {
+    tot.converged = true;
+    tot.rel_res = 0.0;
+    for (int q = 0; q < S; ++q) {
+      if (tol[q] < 0.0) continue;
+      tot.sys_res[q] = rn[q] / bn[q];
+      tot.rel_res = std::max(tot.rel_res, tot.sys_res[q]);
+      if (!tot.sys_conv[q]) tot.converged = false;
+    }
+  };
+  if (c.par.residual_op == c.par.op) {
+    std::vector<double> rn;
+    GmresOut o = gmres(c, c.par.op, b, x, tol, c.par.gmres_maxit, rn, s);
+    tot.iters = o.iters;
+    tot.matvecs = o.matvecs;
+    for (int q = 0; q < S; ++q) {
+      tot.sys_iters[q] = o.sys_iters[q];
+      if (tol[q] >= 0.0) tot.sys_conv[q] = o.sys_conv[q];
+    }
+    finish(rn);
+    return tot;
+  }
+  // iterative refinement, per system
   double* r = c.vec_b.p;
   double* e = c.vec_c.p;
   const int tb = 256, nb = cdiv(len, tb);
+  std::vector<double> rn(S, 0.0), itol(S, -1.0);
+  std::vector<int> todo(S, 0);
+  for (int q = 0; q < S; ++q) todo[q] = tol[q] >= 0.0;
   for (int it = 0; it <= c.par.refine_maxit; ++it) {
+    put_flags(c, w.active, todo, s);
+    c.mv_active = w.active;
     matvec_internal(c, x, r, c.par.residual_op, s);
+    c.mv_active = nullptr;
     ++tot.matvecs;
     launch(axpby, nb, tb, 0, s, 1.0, b, -1.0, r, r, len);
     BP_CHECK_LAUNCH();
-    double rn = std::sqrt(dot_dev(c, r, r, len, s));
-    tot.rel_res = rn / bn;
-    if (rn <= tol) {
-      tot.converged = true;
-      break;
+    std::vector<double> r2 = sys_norm2(c, w, r, w.active, s);
+    int nact = 0;
+    for (int q = 0; q < S; ++q) {
+      itol[q] = -1.0;
+      if (!todo[q]) continue;
+      rn[q] = std::sqrt(r2[q]);
+      if (rn[q] <= tol[q]) {
+        tot.sys_conv[q] = 1;
+        todo[q] = 0;
+        continue;
+      }
+      itol[q] = std::max(c.par.inner_tol * rn[q], 0.5 * tol[q]);
+      ++nact;
     }
-    if (it == c.par.refine_maxit) break;
+    if (nact == 0 || it == c.par.refine_maxit) break;
     BP_CUDA(cudaMemsetAsync(e, 0, sizeof(double) * len, s));
-    double itol = std::max(c.par.inner_tol * rn, 0.5 * tol);
-    GmresOut o = gmres(c, c.par.op, r, e, itol, c.par.gmres_maxit, s);
+    std::vector<double> ir;
+    GmresOut o = gmres(c, c.par.op, r, e, itol, c.par.gmres_maxit, ir, s);
     tot.iters += o.iters;
     tot.matvecs += o.matvecs;
-    launch(axpby, nb, tb, 0, s, 1.0, x, 1.0, e, x, len);
+    for (int q = 0; q < S; ++q) tot.sys_iters[q] += o.sys_iters[q];
+    launch(axpby, nb, tb, 0, s, 1.0, x, 1.0, e, x, len);  // e = 0 outside the refined systems
     BP_CHECK_LAUNCH();
   }
+  finish(rn);
   return tot;
 }
 

@@ -1,8 +1,16 @@
 // Internal declarations of the bempol library (not part of the ABI).
 //
-// Internal order: panels are stored in Morton order of their centroids
-// (perm[i] = caller index of internal panel i).  Gauss node g of internal
-// panel j is source K*j + g.  Every device array below is in internal order.
+// Internal order: panels are sorted by group (a group is one body of one system,
+// groups numbered in (system, body) order), then by the Morton code of their
+// centroid within the group's bounding box (perm[i] = caller index of internal
+// panel i).  So every group, and every system, owns a contiguous range of
+// internal panels.  Gauss node g of internal panel j is source K*j + g.  Every
+// device array below is in internal order.
+//
+// Coupling rules (Sec. "Calculation of the binding energy"): the Laplace layers
+// and the multipole right-hand side of a body involve only that body's panels
+// and sites; the Yukawa layers couple every panel of a system; different systems
+// never interact.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -90,8 +98,15 @@ struct Tree {
   DBuf<int> begin, end, child0, nchild;
   DBuf<double4> center;                                  // x, y, z of the node bounding-box centre; w = radius
   DBuf<int> leaf_cell;                                   // leaf number -> cell
-  // interaction lists per leaf (CSR): accepted far cells, near (direct) leaves
-  DBuf<int> far_ptr, far_list, near_ptr, near_list;
+  DBuf<int> leaf_sys;                                    // leaf number -> system
+  // group of each cell (-1 for the root when it holds several groups)
+  std::vector<int> h_cell_grp;
+  // interaction lists per leaf (CSR): accepted far cells of the Yukawa kernel (every
+  // body of the leaf's system) and of the Laplace kernel (the leaf's own body), and
+  // near (direct) leaves; a near entry with bit 30 set is a leaf of another body
+  // (Yukawa terms only)
+  DBuf<int> far_ptr, far_list, farL_ptr, farL_list, near_ptr, near_list;
+  bool farL_same = true;  // one group: the Laplace lists are the Yukawa lists
   // target blocks: (leaf number, first panel, count <= 128) for the far field and
   // (leaf number, first panel, count <= 32) for the near field
   int nblk = 0, nblk32 = 0, near_splits = 1;
@@ -100,12 +115,18 @@ struct Tree {
   DBuf<float> mom32;
   DBuf<double> mom64;
   int mom_order = -1;
-  // FP32 Gauss-node positions relative to the centre of their own leaf (x, y, z, 0)
-  DBuf<float4> src_rel32;
+  // FP32 Gauss-node positions relative to the centre of their own leaf (x, y, z, 0),
+  // and the same for the collocation points
+  DBuf<float4> src_rel32, cen_rel32;
+  // charge moments of the transposed product (Laplace, Yukawa)
+  DBuf<float> momT32[2];
+  DBuf<double> momT64[2];
   int m2m_min_depth = 0;  // shallowest depth whose cells appear in a far list
   double theta_built = -1.0;
-  long long pairs_per_matvec = 0, far_per_matvec = 0;
+  long long pairs_per_matvec = 0, far_per_matvec = 0, farL_per_matvec = 0;
 };
+
+constexpr int NEAR_CROSS = 1 << 30;  // near-list flag: source leaf of another body
 
 // ---------------------------------------------------------------- context
 struct Ctx {
@@ -123,7 +144,11 @@ struct Ctx {
   DBuf<double4> tgt64;       // centroid x,y,z, area
   DBuf<float4> tgt32;        // centroid x,y,z, 0
   DBuf<double4> nrm64;       // unit normal, 0
-  DBuf<double4> blk_center;  // FP64 centre of each block of 128 consecutive targets
+  // target blocks of the direct kernels: (first target, count <= 128, group, 0), and
+  // each block's source ranges (Yukawa begin, end, Laplace begin, end) in Gauss nodes
+  int ndblk = 0;
+  DBuf<int4> dblk, dblk_rng;
+  DBuf<double4> blk_center;  // FP64 centre of each direct block's targets
   DBuf<double4> src64;       // Gauss node x,y,z, weight w_g*A_j   [n*K]
   DBuf<float4> src32;
   DBuf<double4> str64;       // per-matvec strengths m, d (x,y,z)  [n*K]
@@ -132,11 +157,32 @@ struct Ctx {
   DBuf<int> near_col;        // [nnz]
   DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections
   int64_t nnz = 0;
+  // the near table by columns: for panel j, entries [near_ptrT[j], near_ptrT[j+1])
+  // hold (row i, index into near_corr) of every near pair (i, j)
+  DBuf<int> near_ptrT, near_rowT, near_eT;
   double bbox_lo[3], bbox_hi[3];
   double max_area = 0.0;     // largest panel area (near-field search radius)
   std::vector<unsigned> h_morton;  // 30-bit Morton code of each internal panel (sorted)
   Tree tree;
   bool tree_ready = false;
+
+  // groups (bodies) and systems
+  int ngroup = 1, nsys = 1;
+  std::vector<int> h_grp_sys, h_grp_body;  // [G] system and caller body id of each group
+  std::vector<int> h_gpan, h_sys_pan;      // [G+1], [S+1] internal panel ranges
+  std::vector<int> h_sys_grp;              // [S+1] group ranges of the systems
+  DBuf<int> ptag;                          // [n] group of each internal panel
+  DBuf<int> psys;                          // [n] system of each internal panel
+  DBuf<int> gpan, sys_pan, grp_sys;        // device copies
+  std::vector<int> h_gsite, h_sys_site;    // [G+1], [S+1] site ranges (sites are sorted by group)
+  DBuf<int> gsite, sys_site, stag;         // device copies; stag [ns] group of each site
+  int nsblk = 0;
+  DBuf<int4> sblk;                         // site blocks (first site, count <= 8, group, 0)
+  // GMRES segmentation: chunks (system, begin, end, 0) of the [2n] vectors, each
+  // inside one system and one half; chunks of system s are [chunk_ptr[s], chunk_ptr[s+1])
+  int nchunk = 0;
+  DBuf<int4> chunks;
+  DBuf<int> chunk_ptr;
 
   // sites
   int ns = 0;
@@ -152,6 +198,18 @@ struct Ctx {
   int part_splits = 0;
   DBuf<double> site_part;    // site partial sums
   DBuf<double> gm_V, gm_H, gm_small, gm_dots;
+  DBuf<int> gm_flags;        // [S] active flags and [S] Krylov sizes
+  // Device flags [S] of the systems a matrix-vector product must compute (set by the
+  // GMRES driver around its products; NULL = every system).  Rows of the other
+  // systems are left unspecified.
+  const int* mv_active = nullptr;
+  // matrix-vector products apply A^T instead of A (set by the adjoint driver around
+  // its solves)
+  bool transposed = false;
+  // state of the last solve, kept for the adjoint: surface solution (internal
+  // order) and the dissolved and vacuum induced dipoles
+  bool have_solution = false;
+  DBuf<double> sol_x, sol_mu, sol_mu_v;
   DBuf<unsigned> gm_ticket;  // last-block ticket of the multi-dot kernel (kept at 0 between calls)
   DBuf<double> vec_a, vec_b, vec_c, vec_d;   // [2n] scratch vectors
   DBuf<double> scal;         // device scalars
@@ -182,12 +240,13 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 int num_sms(int device);
 
 // geometry.cu
-void build_geometry(Ctx& c, const double* h_verts, const int* h_tris, cudaStream_t s);
+void build_geometry(Ctx& c, const double* d_verts, const int* h_tris, const std::vector<int>& h_group,
+                    cudaStream_t s);
+void build_blocks(Ctx& c, cudaStream_t s);
 // near.cu
 void build_near(Ctx& c, cudaStream_t s);
 void init_gauss_legendre();
 // p2p.cu
-void build_block_centers(Ctx& c, cudaStream_t s);
 void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s);
 void p2p_direct(Ctx& c, bool fp32, cudaStream_t s);
 void combine(Ctx& c, const double* x, double* y, cudaStream_t s);
@@ -195,14 +254,27 @@ void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s)
 // tree.cu
 void build_tree(Ctx& c, cudaStream_t s);
 void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
+void tree_matvec_T_sums(Ctx& c, const double* u, bool fp32, cudaStream_t s);
 void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells);
+// adjoint.cu
+void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s);
+void matvec_T_internal(Ctx& c, const double* u, double* y, int op, cudaStream_t s);
+struct AdjointOut {
+  int iters_diss = 0, iters_vac = 0, solves = 0, gmres_iters = 0;
+  bool converged = true;
+};
+AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, double* g_pos, cudaStream_t s);
 // sites.cu
+void site_field_of_charges(Ctx& c, const double4* src, const double4* str, int K, double* out10, cudaStream_t s);
 void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s);
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s);
 void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s);
-double energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s);
-double sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
-                  cudaStream_t s);
+// per-system energies (host vector of nsys)
+std::vector<double> energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s);
+// SOR step for the systems with active[s] != 0 (device flags, NULL = all); returns
+// the per-system RMS change
+std::vector<double> sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
+                               const int* d_active, cudaStream_t s);
 void site_validation(Ctx& c, cudaStream_t s);
 bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool hessian, double* scratch,
                            size_t cap, cudaStream_t s);
@@ -210,10 +282,15 @@ bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool
 struct GmresOut {
   int iters = 0;
   int matvecs = 0;
-  double rel_res = 0;
-  bool converged = false;
+  double rel_res = 0;          // largest relative residual over the solved systems
+  bool converged = false;      // every solved system converged
+  std::vector<int> sys_iters;  // per system
+  std::vector<double> sys_res; // per system relative residual
+  std::vector<char> sys_conv;
 };
-GmresOut solve_bem(Ctx& c, const double* b, double* x, cudaStream_t s);
+// Solve A x = b for every system with want[s] != 0 (empty = all); x holds the
+// initial guess and is left unchanged for the other systems.
+GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s);
 // vector helpers (gmres.cu)
 double dot_dev(Ctx& c, const double* a, const double* b, int len, cudaStream_t s);
 void permute_to_internal(const Ctx& c, const double* src, double* dst, int blocks_of_n, cudaStream_t s);

@@ -171,7 +171,7 @@ __device__ void panel_exact(double xx, double xy, double xz, const double* __res
 __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n, int nnz,
                                  const double4* __restrict__ tgt64, const double* __restrict__ vert9,
                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int K,
-                                 double kappa, double4* __restrict__ corr) {
+                                 double kappa, const int* __restrict__ ptag, double4* __restrict__ corr) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnz) return;
   int lo = 0, hi = n - 1;  // largest row i with ptr[i] <= k
@@ -206,7 +206,10 @@ __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restr
       ky += y.w * nr * (1.0 + kappa * R) * ek * inv3;
     }
     const double inv4pi = 0.25 / M_PI;
-    corr[k] = make_double4(ex[0] - vl * inv4pi, ex[1] - kl * inv4pi, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
+    if (ptag[i] == ptag[j])
+      corr[k] = make_double4(ex[0] - vl * inv4pi, ex[1] - kl * inv4pi, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
+    else  // another body: its Laplace layers do not reach this target
+      corr[k] = make_double4(0.0, 0.0, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
   }
 }
 
@@ -250,8 +253,9 @@ void build_near(Ctx& c, cudaStream_t s) {
   launch(near_list_kernel<true>, T.nblk, 128, 0, s, T.blk.p, c.tgt64.p, d_cptr.p, d_ccell.p, T.begin.p, T.end.p,
          nf2, c.near_ptr.p, c.near_col.p);
   launch(near_corr_kernel, cdiv(c.nnz, 128), 128, 0, s, c.near_ptr.p, c.near_col.p, n, (int)c.nnz, c.tgt64.p,
-         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.near_corr.p);
+         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.ptag.p, c.near_corr.p);
   BP_CHECK_LAUNCH();
+  build_near_transpose(c, ptr, s);
   BP_CUDA(cudaStreamSynchronize(s));
 }
 

@@ -53,23 +53,34 @@ __global__ void strength_kernel(const double* __restrict__ x, int n, int K, cons
     str64[t] = make_double4(m, dd * nj.x, dd * nj.y, dd * nj.z);
 }
 
+// Target blocks come from the block table (first target, count, group); every
+// target of a block belongs to one body, so its sources are one range of Gauss
+// nodes: the block's system (Yukawa terms), of which the block's own body
+// (Laplace terms) is a sub-range.  The staged source carries that Laplace weight
+// (1 or 0) in its fourth component.  blockIdx.y takes an equal share of the range.
 __global__ void __launch_bounds__(P2P_TPB) p2p_f32_kernel(const double4* __restrict__ tgt, int n,
+                                                          const int4* __restrict__ blk, const int4* __restrict__ rng,
                                                           const double4* __restrict__ blk_center,
                                                           const double4* __restrict__ spos,
-                                                          const float4* __restrict__ sstr, int nsrc, int per_split,
-                                                          float kappa, float nk_log2e, double* __restrict__ part) {
+                                                          const float4* __restrict__ sstr, float kappa,
+                                                          float nk_log2e, const int* __restrict__ active,
+                                                          const int* __restrict__ grp_sys, double* __restrict__ part) {
   // Coordinates enter the FP32 arithmetic relative to this block's centre c (the
   // subtraction done in FP64), so the rounding of a position is that of a number
   // of the block's size instead of the molecule's: pair distances keep ~1e-7
   // relative accuracy down to the closest (same-panel) pairs.
   __shared__ float4 sp[P2P_TPB];
   __shared__ float4 ss[P2P_TPB];
-  const int i = blockIdx.x * P2P_TPB + threadIdx.x;
-  const int s0 = blockIdx.y * per_split;
-  const int s1 = min(nsrc, s0 + per_split);
+  const int4 B = blk[blockIdx.x], Rg = rng[blockIdx.x];
+  if (active && !active[grp_sys[B.z]]) return;  // system not being solved
+  const int i = B.x + threadIdx.x;
+  const bool act = (int)threadIdx.x < B.y;
+  const int per = ((Rg.y - Rg.x + (int)gridDim.y - 1) / (int)gridDim.y + P2P_TPB - 1) / P2P_TPB * P2P_TPB;
+  const int s0 = Rg.x + blockIdx.y * per;
+  const int s1 = min(Rg.y, s0 + per);
   const double4 c = blk_center[blockIdx.x];
   float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (i < n) {
+  if (act) {
     double4 xd = tgt[i];
     x = make_float4((float)(xd.x - c.x), (float)(xd.y - c.y), (float)(xd.z - c.z), 0.f);
   }
@@ -78,7 +89,8 @@ __global__ void __launch_bounds__(P2P_TPB) p2p_f32_kernel(const double4* __restr
     int j = t0 + threadIdx.x;
     if (j < s1) {
       double4 yd = spos[j];
-      sp[threadIdx.x] = make_float4((float)(yd.x - c.x), (float)(yd.y - c.y), (float)(yd.z - c.z), 0.f);
+      const float wl = (j >= Rg.z && j < Rg.w) ? 1.f : 0.f;
+      sp[threadIdx.x] = make_float4((float)(yd.x - c.x), (float)(yd.y - c.y), (float)(yd.z - c.z), wl);
       ss[threadIdx.x] = sstr[j];
     } else {
       sp[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -96,11 +108,11 @@ __global__ void __launch_bounds__(P2P_TPB) p2p_f32_kernel(const double4* __restr
       float r = r2 * rinv;
       float e = exp2_approx(r * nk_log2e);
       float mr = s.x * rinv;
-      vl += mr;
+      vl = fmaf(mr, p.w, vl);
       vy = fmaf(mr, e, vy);
       float dR = fmaf(s.y, dx, fmaf(s.z, dy, s.w * dz));
       float t = dR * (rinv * rinv) * rinv;
-      kl += t;
+      kl = fmaf(t, p.w, kl);
       ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
     }
     aVL += vl;
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(P2P_TPB) p2p_f32_kernel(const double4* __restr
     aKY += ky;
     __syncthreads();
   }
-  if (i < n) {
+  if (act) {
     double* o = part + (size_t)blockIdx.y * 4 * n;
     o[i] = aVL;
     o[n + i] = aKL;
@@ -119,20 +131,32 @@ __global__ void __launch_bounds__(P2P_TPB) p2p_f32_kernel(const double4* __restr
 }
 
 __global__ void __launch_bounds__(P2P_TPB) p2p_f64_kernel(const double4* __restrict__ tgt, int n,
+                                                          const int4* __restrict__ blk, const int4* __restrict__ rng,
                                                           const double4* __restrict__ spos,
-                                                          const double4* __restrict__ sstr, int nsrc,
-                                                          int per_split, double kappa, double* __restrict__ part) {
+                                                          const double4* __restrict__ sstr, double kappa,
+                                                          const int* __restrict__ active,
+                                                          const int* __restrict__ grp_sys, double* __restrict__ part) {
   __shared__ double4 sp[P2P_TPB];
   __shared__ double4 ss[P2P_TPB];
-  const int i = blockIdx.x * P2P_TPB + threadIdx.x;
-  const int s0 = blockIdx.y * per_split;
-  const int s1 = min(nsrc, s0 + per_split);
-  double4 x = i < n ? tgt[i] : make_double4(0, 0, 0, 0);
+  const int4 B = blk[blockIdx.x], Rg = rng[blockIdx.x];
+  if (active && !active[grp_sys[B.z]]) return;  // system not being solved
+  const int i = B.x + threadIdx.x;
+  const bool act = (int)threadIdx.x < B.y;
+  const int per = ((Rg.y - Rg.x + (int)gridDim.y - 1) / (int)gridDim.y + P2P_TPB - 1) / P2P_TPB * P2P_TPB;
+  const int s0 = Rg.x + blockIdx.y * per;
+  const int s1 = min(Rg.y, s0 + per);
+  double4 x = act ? tgt[i] : make_double4(0, 0, 0, 0);
   double aVL = 0, aKL = 0, aVY = 0, aKY = 0;
   for (int t0 = s0; t0 < s1; t0 += P2P_TPB) {
     int j = t0 + threadIdx.x;
-    sp[threadIdx.x] = j < s1 ? spos[j] : make_double4(0, 0, 0, 0);
-    ss[threadIdx.x] = j < s1 ? sstr[j] : make_double4(0, 0, 0, 0);
+    if (j < s1) {
+      const double4 y = spos[j];
+      sp[threadIdx.x] = make_double4(y.x, y.y, y.z, (j >= Rg.z && j < Rg.w) ? 1.0 : 0.0);
+      ss[threadIdx.x] = sstr[j];
+    } else {
+      sp[threadIdx.x] = make_double4(0, 0, 0, 0);
+      ss[threadIdx.x] = make_double4(0, 0, 0, 0);
+    }
     __syncthreads();
     int lim = min(P2P_TPB, s1 - t0);
     for (int k = 0; k < lim; ++k) {
@@ -145,15 +169,15 @@ __global__ void __launch_bounds__(P2P_TPB) p2p_f64_kernel(const double4* __restr
       double rinv = 1.0 / R;
       double e = exp(-kappa * R);
       double mr = s.x * rinv;
-      aVL += mr;
+      aVL = fma(mr, p.w, aVL);
       aVY += mr * e;
       double t = (s.y * dx + s.z * dy + s.w * dz) * rinv * rinv * rinv;
-      aKL += t;
+      aKL = fma(t, p.w, aKL);
       aKY += t * (1.0 + kappa * R) * e;
     }
     __syncthreads();
   }
-  if (i < n) {
+  if (act) {
     double* o = part + (size_t)blockIdx.y * 4 * n;
     o[i] = aVL;
     o[n + i] = aKL;
@@ -195,14 +219,14 @@ __global__ void combine_kernel(const double* __restrict__ part, int S, int n, co
   y[n + i] = 0.5 * ph - ky + eps_ratio * vy;
 }
 
-// centre of each block of `bs` consecutive targets: midpoint of their bounding box (FP64)
-__global__ void block_center_kernel(const double4* __restrict__ tgt, int n, int bs, double4* __restrict__ out) {
+// centre of each target block: midpoint of its targets' bounding box (FP64)
+__global__ void block_center_kernel(const double4* __restrict__ tgt, const int4* __restrict__ blk, int nb,
+                                    double4* __restrict__ out) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
-  int i0 = b * bs;
-  if (i0 >= n) return;
-  int i1 = min(n, i0 + bs);
+  if (b >= nb) return;
+  const int4 B = blk[b];
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-  for (int i = i0; i < i1; ++i) {
+  for (int i = B.x; i < B.x + B.y; ++i) {
     double4 t = tgt[i];
     lo[0] = fmin(lo[0], t.x); hi[0] = fmax(hi[0], t.x);
     lo[1] = fmin(lo[1], t.y); hi[1] = fmax(hi[1], t.y);
@@ -211,20 +235,56 @@ __global__ void block_center_kernel(const double4* __restrict__ tgt, int n, int 
   out[b] = make_double4(0.5 * (lo[0] + hi[0]), 0.5 * (lo[1] + hi[1]), 0.5 * (lo[2] + hi[2]), 0.0);
 }
 
-int choose_splits(int n, int nsrc, int device) {
-  int bx = cdiv(n, P2P_TPB);
-  int want = num_sms(device) * 8;  // resident blocks to aim for
-  int S = std::max(1, cdiv(want, bx));
-  S = std::min(S, std::max(1, nsrc / (4 * P2P_TPB)));
-  return std::min(S, 64);
+// splits of the source range so the grid holds about eight resident blocks per SM
+int choose_splits(int nblk, int max_range, int device) {
+  int want = num_sms(device) * 8;
+  int S = std::max(1, cdiv(want, std::max(1, nblk)));
+  S = std::min(S, std::max(1, max_range / (4 * P2P_TPB)));
+  S = std::min(S, 64);
+  // no split may be empty for the longest range (equal shares rounded up to tiles)
+  int per = cdiv(cdiv(max_range, S), P2P_TPB) * P2P_TPB;
+  return std::max(1, cdiv(max_range, per));
 }
 
 }  // namespace
 
-void build_block_centers(Ctx& c, cudaStream_t s) {
-  int nb = cdiv(c.n, P2P_TPB);
-  c.blk_center.alloc(nb);
-  launch(block_center_kernel, cdiv(nb, 128), 128, 0, s, c.tgt64.p, c.n, P2P_TPB, c.blk_center.p);
+// Direct-kernel target blocks (<= 128 consecutive targets of one group) with their
+// source ranges, and the chunks of the GMRES vectors (per system and half).
+void build_blocks(Ctx& c, cudaStream_t s) {
+  const int K = c.K;
+  std::vector<int4> blk, rng;
+  for (int g = 0; g < c.ngroup; ++g) {
+    const int sy = c.h_grp_sys[g];
+    for (int off = c.h_gpan[g]; off < c.h_gpan[g + 1]; off += P2P_TPB) {
+      blk.push_back(make_int4(off, std::min(P2P_TPB, c.h_gpan[g + 1] - off), g, 0));
+      rng.push_back(make_int4(K * c.h_sys_pan[sy], K * c.h_sys_pan[sy + 1], K * c.h_gpan[g], K * c.h_gpan[g + 1]));
+    }
+  }
+  c.ndblk = (int)blk.size();
+  c.dblk.alloc(blk.size());
+  c.dblk_rng.alloc(rng.size());
+  BP_CUDA(cudaMemcpyAsync(c.dblk.p, blk.data(), sizeof(int4) * blk.size(), cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaMemcpyAsync(c.dblk_rng.p, rng.data(), sizeof(int4) * rng.size(), cudaMemcpyHostToDevice, s));
+  c.blk_center.alloc(c.ndblk);
+  launch(block_center_kernel, cdiv(c.ndblk, 128), 128, 0, s, c.tgt64.p, c.dblk.p, c.ndblk, c.blk_center.p);
+  BP_CHECK_LAUNCH();
+  // GMRES chunks: about 512 in all, each within one system and one half of [phi; psi]
+  const int n = c.n;
+  const int ch = std::max(512, cdiv(cdiv(2 * (long long)n, 512), 256) * 256);
+  std::vector<int4> chunks;
+  std::vector<int> cptr(c.nsys + 1, 0);
+  for (int sy = 0; sy < c.nsys; ++sy) {
+    for (int half = 0; half < 2; ++half)
+      for (int b = c.h_sys_pan[sy]; b < c.h_sys_pan[sy + 1]; b += ch)
+        chunks.push_back(make_int4(sy, half * n + b, half * n + std::min(b + ch, c.h_sys_pan[sy + 1]), 0));
+    cptr[sy + 1] = (int)chunks.size();
+  }
+  c.nchunk = (int)chunks.size();
+  c.chunks.alloc(chunks.size());
+  c.chunk_ptr.alloc(cptr.size());
+  BP_CUDA(cudaMemcpyAsync(c.chunks.p, chunks.data(), sizeof(int4) * chunks.size(), cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaMemcpyAsync(c.chunk_ptr.p, cptr.data(), sizeof(int) * cptr.size(), cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaStreamSynchronize(s));
 }
 
 void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s) {
@@ -234,22 +294,29 @@ void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s) {
 }
 
 void p2p_direct(Ctx& c, bool fp32, cudaStream_t s) {
-  const int n = c.n, nsrc = c.n * c.K;
-  int S = choose_splits(n, nsrc, c.device);
-  int per = cdiv(cdiv(nsrc, S), P2P_TPB) * P2P_TPB;
-  S = cdiv(nsrc, per);
+  const int n = c.n;
+  int maxr = 0;
+  long long pairs = 0;
+  for (int g = 0; g < c.ngroup; ++g) {
+    const int sy = c.h_grp_sys[g];
+    const int r = c.K * (c.h_sys_pan[sy + 1] - c.h_sys_pan[sy]);
+    maxr = std::max(maxr, r);
+    pairs += (long long)(c.h_gpan[g + 1] - c.h_gpan[g]) * r;
+  }
+  const int S = choose_splits(c.ndblk, maxr, c.device);
   if (c.part.n < (size_t)S * 4 * n) c.part.alloc((size_t)S * 4 * n);
   c.part_splits = S;
-  dim3 grid(cdiv(n, P2P_TPB), S);
+  dim3 grid(c.ndblk, S);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);
-  c.stat_pairs += (long long)n * nsrc;
+  c.stat_pairs += pairs;
   if (fp32) {
     const float k = (float)c.par.kappa;
-    launch(p2p_f32_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.blk_center.p, c.src64.p, c.str32.p, nsrc, per, k,
-                                            (float)(-c.par.kappa * 1.4426950408889634), c.part.p);
+    launch(p2p_f32_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.dblk.p, c.dblk_rng.p, c.blk_center.p, c.src64.p,
+           c.str32.p, k, (float)(-c.par.kappa * 1.4426950408889634), c.mv_active, c.grp_sys.p, c.part.p);
   } else {
-    launch(p2p_f64_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.src64.p, c.str64.p, nsrc, per, c.par.kappa, c.part.p);
+    launch(p2p_f64_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.dblk.p, c.dblk_rng.p, c.src64.p, c.str64.p,
+           c.par.kappa, c.mv_active, c.grp_sys.p, c.part.p);
   }
   c.time_end(s, tm);
   BP_CHECK_LAUNCH();
@@ -263,6 +330,10 @@ void combine(Ctx& c, const double* x, double* y, cudaStream_t s) {
 
 void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s) {
   bool fp32 = (op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE);
+  if (c.transposed) {
+    matvec_T_internal(c, x, y, op, s);
+    return;
+  }
   strengths(c, x, fp32, s);
   if (op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE)
     tree_matvec_sums(c, fp32, s);

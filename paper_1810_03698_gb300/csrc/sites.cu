@@ -37,19 +37,25 @@ struct SiteSrc {   // one multipole, 13 values
 };
 
 // ---------------------------------------------------------------- RHS
+// One block per direct target block (<= 128 panels of one body): the panels see the
+// sites of their own body only.
 template <typename Real>
-__global__ void rhs_kernel(const double4* __restrict__ tgt, int n, const double4* __restrict__ spos,
+__global__ void rhs_kernel(const double4* __restrict__ tgt, const int4* __restrict__ blk,
+                           const int* __restrict__ gsite, const double4* __restrict__ spos,
                            const double* __restrict__ sq, const double* __restrict__ sp,
-                           const double* __restrict__ sQ, int ns, double scale, double* __restrict__ b) {
+                           const double* __restrict__ sQ, double scale, double* __restrict__ b) {
   constexpr int T = 128;
   __shared__ Real sh[13][T];
-  int i = blockIdx.x * T + threadIdx.x;
-  double4 xd = i < n ? tgt[i] : make_double4(0, 0, 0, 0);
+  const int4 B = blk[blockIdx.x];
+  const int i = B.x + threadIdx.x;
+  const bool act = (int)threadIdx.x < B.y;
+  const int k0 = gsite[B.z], k1 = gsite[B.z + 1];
+  double4 xd = act ? tgt[i] : make_double4(0, 0, 0, 0);
   Real x = (Real)xd.x, y = (Real)xd.y, z = (Real)xd.z;
   double acc = 0.0;
-  for (int t0 = 0; t0 < ns; t0 += T) {
+  for (int t0 = k0; t0 < k1; t0 += T) {
     int k = t0 + threadIdx.x;
-    if (k < ns) {
+    if (k < k1) {
       double4 p = spos[k];
       sh[0][threadIdx.x] = (Real)p.x;
       sh[1][threadIdx.x] = (Real)p.y;
@@ -61,7 +67,7 @@ __global__ void rhs_kernel(const double4* __restrict__ tgt, int n, const double4
       for (int c = 0; c < 6; ++c) sh[7 + c][threadIdx.x] = (Real)sQ[6 * k + c];
     }
     __syncthreads();
-    int lim = min(T, ns - t0);
+    int lim = min(T, k1 - t0);
     Real a = 0;
     for (int kk = 0; kk < lim; ++kk) {
       Real Rx = x - sh[0][kk], Ry = y - sh[1][kk], Rz = z - sh[2][kk];
@@ -77,22 +83,30 @@ __global__ void rhs_kernel(const double4* __restrict__ tgt, int n, const double4
     acc += (double)a;
     __syncthreads();
   }
-  if (i < n) b[i] = acc * scale;
+  if (act) b[i] = acc * scale;
 }
 
 // ---------------------------------------------------------------- reaction at sites
-// warp per site; the block's 8 warps share source tiles staged in shared memory.
+// warp per site; the block's (up to 8) sites belong to one body, whose Gauss nodes
+// (its own surface: the Laplace layers) are the sources, staged in shared memory.
+// blockIdx.y takes an equal share of them.
 template <typename Real, typename R4, bool HESS>
 __global__ void __launch_bounds__(256) site_reaction_kernel(const double4* __restrict__ spos_site, int ns,
+                                                            const int4* __restrict__ sblk,
+                                                            const int* __restrict__ gpan, int K,
                                                             const R4* __restrict__ src, const R4* __restrict__ str,
-                                                            int nsrc, int per_split, double* __restrict__ part) {
+                                                            double* __restrict__ part) {
   constexpr int T = 256;
   __shared__ R4 tp[T];
   __shared__ R4 ts[T];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int site = blockIdx.x * 8 + warp;
-  const int s0 = blockIdx.y * per_split, s1 = min(nsrc, s0 + per_split);
-  double4 sd = site < ns ? spos_site[site] : make_double4(0, 0, 0, 0);
+  const int4 B = sblk[blockIdx.x];
+  const bool act = warp < B.y;
+  const int site = B.x + warp;
+  const int r0 = K * gpan[B.z], r1 = K * gpan[B.z + 1];
+  const int per = ((r1 - r0 + (int)gridDim.y - 1) / (int)gridDim.y + T - 1) / T * T;
+  const int s0 = r0 + blockIdx.y * per, s1 = min(r1, s0 + per);
+  double4 sd = act ? spos_site[site] : make_double4(0, 0, 0, 0);
   const Real X = (Real)sd.x, Y = (Real)sd.y, Z = (Real)sd.z;
   double acc[10];
 #pragma unroll
@@ -147,7 +161,7 @@ __global__ void __launch_bounds__(256) site_reaction_kernel(const double4* __res
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     acc[c] = v;
   }
-  if (lane == 0 && site < ns) {
+  if (lane == 0 && act) {
     double* o = part + ((size_t)blockIdx.y * ns + site) * 10;
     for (int c = 0; c < 10; ++c) o[c] = c < nc ? acc[c] : 0.0;
   }
@@ -164,19 +178,32 @@ __global__ void site_reduce_kernel(const double* __restrict__ part, int S, int n
 // ---------------------------------------------------------------- multipole-multipole
 // mode 0: polarising field E (3 per site): permanent masked by group, induced damped.
 // mode 1: energy potentials (10 per site): permanent unmasked, induced damped.
+// Modes 0 and 1 sum over the sites of the site's own body (dissolved state: each
+// cavity holds its own multipoles), modes 2 and 3 are the same over every site of
+// its system (vacuum state).  Adding 4 to the mode drops the permanent moments
+// (the damped field of the dipoles `mu` alone).
 __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restrict__ pos, const double* __restrict__ q,
                                                         const double* __restrict__ d, const double* __restrict__ Q,
                                                         const double* __restrict__ mu, const int* __restrict__ group,
-                                                        int ns, int mode, double thole_a, double scale,
-                                                        double* __restrict__ out) {
+                                                        const int* __restrict__ stag, const int* __restrict__ gsite,
+                                                        const int* __restrict__ grp_sys,
+                                                        const int* __restrict__ sys_site, int ns, int mode,
+                                                        double thole_a, double scale, double* __restrict__ out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + warp;
   if (l >= ns) return;
   const double4 pl = pos[l];
   const int gl = group[l];
+  const int tg = stag[l];
+  const bool ind_only = (mode & 4) != 0;  // induced dipoles only (no permanent moments)
+  mode &= 3;
+  const bool whole = mode >= 2;
+  const int m0 = whole ? sys_site[grp_sys[tg]] : gsite[tg];
+  const int m1 = whole ? sys_site[grp_sys[tg] + 1] : gsite[tg + 1];
+  mode &= 1;
   double acc[10];
   for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-  for (int m = lane; m < ns; m += 32) {
+  for (int m = m0 + lane; m < m1; m += 32) {
     if (m == l) continue;
     double4 pm = pos[m];
     double Rx = pl.x - pm.x, Ry = pl.y - pm.y, Rz = pl.z - pm.z;
@@ -185,7 +212,7 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
     double i2 = rinv * rinv, i3 = i2 * rinv, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
     double R[3] = {Rx, Ry, Rz};
     double g[3] = {0, 0, 0}, H[6] = {0, 0, 0, 0, 0, 0}, P = 0;
-    bool perm = (mode == 1) || (group[m] != gl);
+    bool perm = !ind_only && ((mode == 1) || (group[m] != gl));
     if (perm) {
       double qm = q[m];
       double pv[3] = {d[3 * m], d[3 * m + 1], d[3 * m + 2]};
@@ -250,12 +277,15 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
 }
 
 // ---------------------------------------------------------------- energy and SOR
+// one block per system: outE[s] = 1/2 sum over the system's sites
 __global__ void energy_kernel(const double* __restrict__ q, const double* __restrict__ d,
                               const double* __restrict__ Q, const double* __restrict__ r10,
-                              const double* __restrict__ m10, int ns, double* __restrict__ outE) {
+                              const double* __restrict__ m10, const int* __restrict__ sys_site,
+                              double* __restrict__ outE) {
   __shared__ double sh[256];
+  const int l0 = sys_site[blockIdx.x], l1 = sys_site[blockIdx.x + 1];
   double v = 0.0;
-  for (int l = threadIdx.x; l < ns; l += 256) {
+  for (int l = l0 + threadIdx.x; l < l1; l += 256) {
     double f[10];
     for (int c = 0; c < 10; ++c) f[c] = (r10 ? r10[10 * l + c] : 0.0) + (m10 ? m10[10 * l + c] : 0.0);
     const double* Ql = Q + 6 * l;
@@ -268,16 +298,20 @@ __global__ void energy_kernel(const double* __restrict__ q, const double* __rest
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *outE = 0.5 * sh[0];
+  if (threadIdx.x == 0) outE[blockIdx.x] = 0.5 * sh[0];
 }
 
-// mu_new = (1 - w) mu + w 4 pi alpha (E_solv + E_mult); returns sum |mu_new - mu|^2
+// One block per system: mu_new = (1 - w) mu + w 4 pi alpha (E_solv + E_mult) for the
+// system's sites when active[s] (NULL = every system); out_sq[s] = sum |mu_new - mu|^2.
 __global__ void sor_kernel(double* __restrict__ mu, const double4* __restrict__ pos,
-                           const double* __restrict__ react10, const double* __restrict__ emult, int ns,
-                           double omega, double* __restrict__ out_sq) {
+                           const double* __restrict__ react10, const double* __restrict__ emult,
+                           const int* __restrict__ sys_site, const int* __restrict__ active, double omega,
+                           double* __restrict__ out_sq) {
   __shared__ double sh[256];
+  const int l0 = sys_site[blockIdx.x], l1 = sys_site[blockIdx.x + 1];
+  const bool on = !active || active[blockIdx.x];
   double v = 0.0;
-  for (int l = threadIdx.x; l < ns; l += 256) {
+  for (int l = l0 + threadIdx.x; on && l < l1; l += 256) {
     double fa = 4.0 * M_PI * pos[l].w;
     for (int a = 0; a < 3; ++a) {
       double E = emult[3 * l + a] - (react10 ? react10[10 * l + 1 + a] : 0.0);
@@ -293,94 +327,126 @@ __global__ void sor_kernel(double* __restrict__ mu, const double4* __restrict__ 
     if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *out_sq = sh[0];
+  if (threadIdx.x == 0) out_sq[blockIdx.x] = sh[0];
 }
 
 // ---------------------------------------------------------------- validation
-// flag[l] = 1 if site l is within the near radius of a panel centroid, 2 if outside the surface
-__global__ void site_check_kernel(const double4* __restrict__ spos, int ns, const double4* __restrict__ tgt64,
-                                  const float4* __restrict__ src32, const double4* __restrict__ nrm64, int n,
-                                  int K, double nf2, int* __restrict__ flag) {
+// flag[l] = 1 if site l is within the near radius of a panel centroid of its
+// system, 2 if outside its own body's surface, 3 if inside another body's surface
+__global__ void site_check_kernel(const double4* __restrict__ spos, int ns, const int* __restrict__ stag,
+                                  const int* __restrict__ grp_sys, const int* __restrict__ sys_pan,
+                                  const int* __restrict__ ptag, const double4* __restrict__ tgt64,
+                                  const float4* __restrict__ src32, const double4* __restrict__ nrm64, int K,
+                                  double nf2, int* __restrict__ flag) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + warp;
   if (l >= ns) return;
   double4 p = spos[l];
+  const int g = stag[l];
+  const int j0 = sys_pan[grp_sys[g]], j1 = sys_pan[grp_sys[g] + 1];
   int near = 0;
-  double dl = 0.0;
-  for (int j = lane; j < n; j += 32) {
+  double dl = 0.0, dother = 0.0;
+  for (int j = j0 + lane; j < j1; j += 32) {
     double4 c = tgt64[j];
     double dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
     if (dx * dx + dy * dy + dz * dz < nf2 * c.w) near = 1;
-    // inside test in FP32: -K_L[1] is 1 inside and 0 outside, compared with 1/2
+    // inside test in FP32: -K_L[1] is 1 inside a closed surface and 0 outside, compared with 1/2
     double4 nj = nrm64[j];
     const float nx = (float)nj.x, ny = (float)nj.y, nz = (float)nj.z;
     float part = 0.f;
-    for (int g = 0; g < K; ++g) {
-      float4 y = src32[(size_t)K * j + g];
+    for (int q = 0; q < K; ++q) {
+      float4 y = src32[(size_t)K * j + q];
       float rx = (float)p.x - y.x, ry = (float)p.y - y.y, rz = (float)p.z - y.z;
       float r2 = rx * rx + ry * ry + rz * rz;
       float ri = rsqrtf(r2);
       part += y.w * (nx * rx + ny * ry + nz * rz) * ri * ri * ri;
     }
-    dl += (double)part;
+    if (ptag[j] == g)
+      dl += (double)part;
+    else
+      dother += (double)part;
   }
   for (int o = 16; o > 0; o >>= 1) {
     dl += __shfl_down_sync(0xffffffffu, dl, o);
+    dother += __shfl_down_sync(0xffffffffu, dother, o);
     near |= __shfl_down_sync(0xffffffffu, near, o);
   }
   if (lane == 0) {
-    // -K_L[1] = 1 inside a closed surface, 0 outside
-    double inside = -dl * INV4PI;
-    flag[l] = near ? 1 : (inside > 0.5 ? 0 : 2);
+    const double inside = -dl * INV4PI, inside_other = -dother * INV4PI;
+    flag[l] = near ? 1 : (inside > 0.5 ? (inside_other > 0.5 ? 3 : 0) : 2);
   }
 }
 
-int site_splits(Ctx& c, int ns, int nsrc) {
-  int bx = cdiv(ns, 8);
+int site_splits(Ctx& c, int max_range) {
   int want = num_sms(c.device) * 6;
-  int S = std::max(1, cdiv(want, bx));
-  S = std::min(S, std::max(1, nsrc / 1024));
-  return std::min(S, 256);
+  int S = std::max(1, cdiv(want, std::max(1, c.nsblk)));
+  S = std::min(S, std::max(1, max_range / 1024));
+  S = std::min(S, 256);
+  int per = cdiv(cdiv(max_range, S), 256) * 256;
+  return std::max(1, cdiv(max_range, per));
+}
+
+int max_group_sources(const Ctx& c) {
+  int m = 1;
+  for (int g = 0; g < c.ngroup; ++g) m = std::max(m, c.K * (c.h_gpan[g + 1] - c.h_gpan[g]));
+  return m;
+}
+
+template <typename Real, typename R4, bool HESS>
+void launch_site_reaction(Ctx& c, int S, const R4* src, const R4* str, double* part, cudaStream_t s) {
+  launch(site_reaction_kernel<Real, R4, HESS>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p, c.gpan.p,
+         c.K, src, str, part);
+}
+
+void site_reaction_launch(Ctx& c, int S, bool fp32, bool hessian, double* part, cudaStream_t s) {
+  if (fp32) {
+    if (hessian)
+      launch_site_reaction<float, float4, true>(c, S, c.src32.p, c.str32.p, part, s);
+    else
+      launch_site_reaction<float, float4, false>(c, S, c.src32.p, c.str32.p, part, s);
+  } else {
+    if (hessian)
+      launch_site_reaction<double, double4, true>(c, S, c.src64.p, c.str64.p, part, s);
+    else
+      launch_site_reaction<double, double4, false>(c, S, c.src64.p, c.str64.p, part, s);
+  }
 }
 
 }  // namespace
+
+// Potential, gradient and Hessian (10 per site, x 1/(4 pi)) at every site of the
+// field of point charges str[j].x at positions src[j] (K per panel), over the
+// panels of the site's own body, in FP64.
+void site_field_of_charges(Ctx& c, const double4* src, const double4* str, int K, double* out10, cudaStream_t s) {
+  int mr = 1;
+  for (int g = 0; g < c.ngroup; ++g) mr = std::max(mr, K * (c.h_gpan[g + 1] - c.h_gpan[g]));
+  const int S = site_splits(c, mr);
+  size_t need = (size_t)S * c.ns * 10;
+  if (c.site_part.n < need) c.site_part.alloc(need);
+  launch(site_reaction_kernel<double, double4, true>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p,
+         c.gpan.p, K, src, str, c.site_part.p);
+  launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, c.site_part.p, S, c.ns, out10);
+  BP_CHECK_LAUNCH();
+}
 
 void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s) {
   const double* pp = p ? p : c.site_d.p;
   double scale = INV4PI / c.par.eps_in;
   if (fp32)
-    launch(rhs_kernel<float>, cdiv(c.n, 128), 128, 0, s, c.tgt64.p, c.n, c.site_pos.p, c.site_q.p, pp, c.site_Q.p,
-                                                     c.ns, scale, b);
+    launch(rhs_kernel<float>, c.ndblk, 128, 0, s, c.tgt64.p, c.dblk.p, c.gsite.p, c.site_pos.p, c.site_q.p, pp,
+           c.site_Q.p, scale, b);
   else
-    launch(rhs_kernel<double>, cdiv(c.n, 128), 128, 0, s, c.tgt64.p, c.n, c.site_pos.p, c.site_q.p, pp, c.site_Q.p,
-                                                      c.ns, scale, b);
+    launch(rhs_kernel<double>, c.ndblk, 128, 0, s, c.tgt64.p, c.dblk.p, c.gsite.p, c.site_pos.p, c.site_q.p, pp,
+           c.site_Q.p, scale, b);
   BP_CHECK_LAUNCH();
 }
 
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s) {
   strengths(c, x, fp32, s);
-  const int nsrc = c.n * c.K;
-  int S = site_splits(c, c.ns, nsrc);
-  int per = cdiv(cdiv(nsrc, S), 256) * 256;
-  S = cdiv(nsrc, per);
+  const int S = site_splits(c, max_group_sources(c));
   size_t need = (size_t)S * c.ns * 10;
   if (c.site_part.n < need) c.site_part.alloc(need);
-  dim3 grid(cdiv(c.ns, 8), S);
-  if (fp32) {
-    if (hessian)
-      launch(site_reaction_kernel<float, float4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
-                                                                    nsrc, per, c.site_part.p);
-    else
-      launch(site_reaction_kernel<float, float4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
-                                                                     nsrc, per, c.site_part.p);
-  } else {
-    if (hessian)
-      launch(site_reaction_kernel<double, double4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p, c.str64.p,
-                                                                      nsrc, per, c.site_part.p);
-    else
-      launch(site_reaction_kernel<double, double4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
-                                                                       c.str64.p, nsrc, per, c.site_part.p);
-  }
+  site_reaction_launch(c, S, fp32, hessian, c.site_part.p, s);
   BP_CHECK_LAUNCH();
   launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, c.site_part.p, S, c.ns, out);
   BP_CHECK_LAUNCH();
@@ -388,34 +454,42 @@ void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, boo
 
 void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s) {
   launch(multipole_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
-                                                  c.site_group.p, c.ns, mode, c.par.thole_a,
-                                                  INV4PI / c.par.eps_in, out);
+         c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
+         INV4PI / c.par.eps_in, out);
   BP_CHECK_LAUNCH();
 }
 
-double energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s) {
-  launch(energy_kernel, 1, 256, 0, s, c.site_q.p, c.site_d.p, c.site_Q.p, react10, mult10, c.ns, c.scal.p);
+std::vector<double> energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s) {
+  launch(energy_kernel, c.nsys, 256, 0, s, c.site_q.p, c.site_d.p, c.site_Q.p, react10, mult10, c.sys_site.p,
+         c.scal.p);
   BP_CHECK_LAUNCH();
-  BP_CUDA(cudaMemcpyAsync(c.h_pinned, c.scal.p, sizeof(double), cudaMemcpyDeviceToHost, s));
+  std::vector<double> e(c.nsys);
+  BP_CUDA(cudaMemcpyAsync(c.h_pinned, c.scal.p, sizeof(double) * c.nsys, cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
-  return c.h_pinned[0];
+  for (int q = 0; q < c.nsys; ++q) e[q] = c.h_pinned[q];
+  return e;
 }
 
-double sor_update(Ctx& c, double* mu, const double* react10, const double* emult3, bool vacuum, cudaStream_t s) {
-  launch(sor_kernel, 1, 256, 0, s, mu, c.site_pos.p, vacuum ? nullptr : react10, emult3, c.ns, c.par.sor_omega,
-                               c.scal.p + 1);
+std::vector<double> sor_update(Ctx& c, double* mu, const double* react10, const double* emult3, bool vacuum,
+                               const int* d_active, cudaStream_t s) {
+  launch(sor_kernel, c.nsys, 256, 0, s, mu, c.site_pos.p, vacuum ? nullptr : react10, emult3, c.sys_site.p, d_active,
+         c.par.sor_omega, c.scal.p + c.nsys);
   BP_CHECK_LAUNCH();
-  BP_CUDA(cudaMemcpyAsync(c.h_pinned + 1, c.scal.p + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaMemcpyAsync(c.h_pinned + c.nsys, c.scal.p + c.nsys, sizeof(double) * c.nsys, cudaMemcpyDeviceToHost,
+                          s));
   BP_CUDA(cudaStreamSynchronize(s));
-  return std::sqrt(c.h_pinned[1] / std::max(1, c.ns));
+  std::vector<double> r(c.nsys);
+  for (int q = 0; q < c.nsys; ++q)
+    r[q] = std::sqrt(c.h_pinned[c.nsys + q] / std::max(1, c.h_sys_site[q + 1] - c.h_sys_site[q]));
+  return r;
 }
 
 void site_validation(Ctx& c, cudaStream_t s) {
   DBuf<int> flag;
   flag.alloc(c.ns);
   double nf2 = c.par.near_factor * c.par.near_factor;
-  launch(site_check_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.ns, c.tgt64.p, c.src32.p, c.nrm64.p, c.n, c.K,
-                                                  nf2, flag.p);
+  launch(site_check_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.ns, c.stag.p, c.grp_sys.p, c.sys_pan.p,
+         c.ptag.p, c.tgt64.p, c.src32.p, c.nrm64.p, c.K, nf2, flag.p);
   BP_CHECK_LAUNCH();
   std::vector<int> h(c.ns);
   BP_CUDA(cudaMemcpyAsync(h.data(), flag.p, sizeof(int) * c.ns, cudaMemcpyDeviceToHost, s));
@@ -424,6 +498,7 @@ void site_validation(Ctx& c, cudaStream_t s) {
     if (h[l] == 1)
       fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies within the near-singular radius of a panel");
     if (h[l] == 2) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies outside the surface");
+    if (h[l] == 3) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies inside the surface of another body");
   }
 }
 
@@ -434,29 +509,14 @@ void site_validation(Ctx& c, cudaStream_t s) {
 // launches nothing) when even one split does not fit.
 bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool hessian, double* scratch,
                            size_t cap, cudaStream_t s) {
-  const int nsrc = c.n * c.K;
   if ((size_t)c.ns * 10 > cap) return false;
-  int S = site_splits(c, c.ns, nsrc);
+  const int mr = max_group_sources(c);
+  int S = site_splits(c, mr);
   S = std::max(1, std::min<int>(S, (int)(cap / ((size_t)c.ns * 10))));
-  int per = cdiv(cdiv(nsrc, S), 256) * 256;
-  S = cdiv(nsrc, per);
+  int per = cdiv(cdiv(mr, S), 256) * 256;
+  S = cdiv(mr, per);
   strengths(c, x, fp32, s);
-  dim3 grid(cdiv(c.ns, 8), S);
-  if (fp32) {
-    if (hessian)
-      launch(site_reaction_kernel<float, float4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
-             nsrc, per, scratch);
-    else
-      launch(site_reaction_kernel<float, float4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src32.p, c.str32.p,
-             nsrc, per, scratch);
-  } else {
-    if (hessian)
-      launch(site_reaction_kernel<double, double4, true>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
-             c.str64.p, nsrc, per, scratch);
-    else
-      launch(site_reaction_kernel<double, double4, false>, grid, 256, 0, s, c.site_pos.p, c.ns, c.src64.p,
-             c.str64.p, nsrc, per, scratch);
-  }
+  site_reaction_launch(c, S, fp32, hessian, scratch, s);
   launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, scratch, S, c.ns, out);
   return true;
 }
