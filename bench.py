@@ -18,6 +18,11 @@ Launch: python bench.py [--gpus N --steps K --warmup W] ; for N > 1 under
 torch.distributed.run each rank solves its own replica (independent problems, no
 collective in the data path: weak scaling).  --impl reference times the oracle.
 
+--workload gradient times the adjoint gradient dDelta G_solv/d(positions, q, d, Q)
+after a forward solve on workload 5 (327,680 panels, 10,000 sites; --grad-config 3
+for workload 3) and reports gradient cost / forward cost, with Euler's identity
+sum_l m_l . dG/dm_l = 2 Delta G_solv as a consistency check of the gradient.
+
 --workload binding times the binding workload instead: 16 triples (A, B, AB) of
 bumpy bodies (subdivisions 3-6, R 6-14 A) = 48 systems solved together in one
 context (one set of launches per matrix-vector product, per-system GMRES and SCF),
@@ -74,7 +79,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=384)
-    ap.add_argument("--workload", default="solvation", choices=["solvation", "binding"])
+    ap.add_argument("--workload", default="solvation", choices=["solvation", "binding", "gradient"])
+    ap.add_argument("--grad-config", type=int, default=5, choices=[3, 5])
     ap.add_argument("--triples", type=int, default=16)
     return ap.parse_args()
 
@@ -267,6 +273,58 @@ def run_binding(args, local):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------- gradient workload
+def run_gradient(args, local):
+    import torch
+    import gen
+    build_library()
+    import paper_1810_03698_gb300 as bp
+
+    pr = gen.config5() if args.grad_config == 5 else gen.config3()
+    res_op = args.residual_op or args.op
+    s = bp.problem_solver(pr, device=local, op=args.op, residual_op=res_op)
+    stream = torch.cuda.current_stream()
+
+    def ev_time(fn):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b), r
+
+    for _ in range(args.warmup):
+        s.solve()
+        s.gradient()
+    sampler = ClockSampler(local)
+    sampler.start()
+    fw, gr = [], []
+    for _ in range(args.steps):
+        ms_f, out = ev_time(lambda: s.solve())
+        ms_g, g = ev_time(lambda: s.gradient())
+        fw.append(ms_f)
+        gr.append(ms_g)
+    clocks = sampler.stop()
+    st = pr.sites
+    dG = out["G_diss"] - out["G_vac"]
+    euler = float(np.sum(st.q * g["q"]) + np.sum(st.d * g["d"]) + np.sum(st.Q * g["Q"]))
+    line = {
+        "metric": "time per adjoint gradient dΔG_solv/d(r, q, d, Q) and gradient cost / forward cost",
+        "value": float(np.mean(gr)) / 1e3, "unit": "s/gradient", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": float(np.mean(fw) + np.mean(gr)), "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if "fp32" in args.op else "f64",
+        "data": "synthetic",
+        "config": {"workload": pr.name, "panels": pr.n_panels, "sites": st.n, "op": args.op, "residual_op": res_op,
+                   "theta": pr.params.theta, "order": pr.params.order, "gmres_tol": pr.params.gmres_tol,
+                   "scf_tol": pr.params.scf_tol},
+        "forward_s": float(np.mean(fw)) / 1e3, "gradient_over_forward": float(np.mean(gr) / np.mean(fw)),
+        "adjoint": g["info"], "dG_solv_kcal": out["dG_solv_kcal"],
+        "euler_rel_err": abs(euler - 2.0 * dG) / abs(2.0 * dG), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---------------------------------------------------------------------------- native arm
 def main():
     args = parse()
@@ -281,6 +339,10 @@ def main():
     if args.workload == "binding":
         if rank == 0:
             run_binding(args, local)
+        return
+    if args.workload == "gradient":
+        if rank == 0:
+            run_gradient(args, local)
         return
     dist = None
     if world > 1:

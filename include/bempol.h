@@ -282,8 +282,10 @@ bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, v
 /* y = A^T x, the transpose of the operator of bempol_matvec (used by the adjoint;
  * the paper has no counterpart): charges x_phi (Laplace) and x_psi (Yukawa) at the
  * collocation points evaluated at every panel's Gauss nodes, plus the near
- * corrections by columns.  The tree forms use the same octree and lists, with
- * charge moments and coefficients to order P + 1 for the nodes' potential gradient.
+ * corrections by columns.  BEMPOL_OP_FP32_TREE uses the same octree and lists
+ * with charge moments of order 5 whatever params.order (the nodes' potential
+ * gradient takes coefficients to order 6); BEMPOL_OP_FP64_TREE is applied as
+ * BEMPOL_OP_FP64_DIRECT.
  * x, y: device float64 [2N] in the caller's order (y may not alias x).  Enqueued
  * on `stream`, no synchronisation. */
 bempol_status bempol_matvec_transposed(bempol_ctx* c, const double* x, double* y, int op, void* stream);

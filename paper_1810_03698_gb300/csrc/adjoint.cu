@@ -200,70 +200,81 @@ __global__ void combineT_kernel(const double* __restrict__ part, int S, int n, c
 // R^T w: per panel j, the potential U and its gradient at the Gauss nodes of point
 // multipoles (charge wq, dipole wd, traceless quadrupole wQ in the convention of
 // Eq. pot_multipole) at the sites of j's body; out[j] = -(1/4 pi) sum_g W_g n_j . grad U,
-// out[n + j] = (1/4 pi) sum_g W_g U.
+// out[n + j] = (1/4 pi) sum_g W_g U.  Real = float: pair arithmetic in FP32 with
+// coordinates relative to the block's centre, per-tile sums added in FP64.
+template <typename Real>
 __global__ void __launch_bounds__(TPB) adj_reaction_kernel(const double4* __restrict__ node,
                                                            const double4* __restrict__ nrm, int K, int n,
-                                                           const int4* __restrict__ blk, const int* __restrict__ gsite,
+                                                           const int4* __restrict__ blk,
+                                                           const double4* __restrict__ blk_center,
+                                                           const int* __restrict__ gsite,
                                                            const double4* __restrict__ spos,
                                                            const double* __restrict__ wq, const double* __restrict__ wd,
                                                            const double* __restrict__ wQ, double* __restrict__ out) {
-  __shared__ double sh[13][TPB];
+  __shared__ Real sh[13][TPB];
   const int4 B = blk[blockIdx.x];
   const int j = B.x + threadIdx.x;
   const bool act = (int)threadIdx.x < B.y;
   const int k0 = gsite[B.z], k1 = gsite[B.z + 1];
-  double ny[4][4];
-  double3 nj = make_double3(0, 0, 0);
+  const double4 c = blk_center[blockIdx.x];
+  Real ny[4][4];
+  Real nj[3] = {0, 0, 0};
+  for (int g = 0; g < 4; ++g) ny[g][0] = ny[g][1] = ny[g][2] = ny[g][3] = 0;
   if (act) {
     for (int g = 0; g < K; ++g) {
       const double4 y = node[(size_t)K * j + g];
-      ny[g][0] = y.x;
-      ny[g][1] = y.y;
-      ny[g][2] = y.z;
-      ny[g][3] = y.w;
+      ny[g][0] = (Real)(y.x - c.x);
+      ny[g][1] = (Real)(y.y - c.y);
+      ny[g][2] = (Real)(y.z - c.z);
+      ny[g][3] = (Real)y.w;
     }
     const double4 nn = nrm[j];
-    nj = make_double3(nn.x, nn.y, nn.z);
+    nj[0] = (Real)nn.x;
+    nj[1] = (Real)nn.y;
+    nj[2] = (Real)nn.z;
   }
   double aU = 0.0, aG = 0.0;
   for (int t0 = k0; t0 < k1; t0 += TPB) {
     const int k = t0 + threadIdx.x;
     if (k < k1) {
       const double4 p = spos[k];
-      sh[0][threadIdx.x] = p.x;
-      sh[1][threadIdx.x] = p.y;
-      sh[2][threadIdx.x] = p.z;
-      sh[3][threadIdx.x] = wq[k];
-      for (int a = 0; a < 3; ++a) sh[4 + a][threadIdx.x] = wd[3 * k + a];
-      for (int a = 0; a < 6; ++a) sh[7 + a][threadIdx.x] = wQ[6 * k + a];
+      sh[0][threadIdx.x] = (Real)(p.x - c.x);
+      sh[1][threadIdx.x] = (Real)(p.y - c.y);
+      sh[2][threadIdx.x] = (Real)(p.z - c.z);
+      sh[3][threadIdx.x] = (Real)wq[k];
+      for (int a = 0; a < 3; ++a) sh[4 + a][threadIdx.x] = (Real)wd[3 * k + a];
+      for (int a = 0; a < 6; ++a) sh[7 + a][threadIdx.x] = (Real)wQ[6 * k + a];
     }
     __syncthreads();
     const int lim = min(TPB, k1 - t0);
+    Real tU = 0, tG = 0;
     if (act) {
       for (int kk = 0; kk < lim; ++kk) {
-        const double q = sh[3][kk], px = sh[4][kk], py = sh[5][kk], pz = sh[6][kk];
-        const double Qxx = sh[7][kk], Qxy = sh[8][kk], Qxz = sh[9][kk], Qyy = sh[10][kk], Qyz = sh[11][kk],
-                     Qzz = sh[12][kk];
+        const Real q = sh[3][kk], px = sh[4][kk], py = sh[5][kk], pz = sh[6][kk];
+        const Real Qxx = sh[7][kk], Qxy = sh[8][kk], Qxz = sh[9][kk], Qyy = sh[10][kk], Qyz = sh[11][kk],
+                   Qzz = sh[12][kk];
         for (int g = 0; g < K; ++g) {
-          const double Rx = ny[g][0] - sh[0][kk], Ry = ny[g][1] - sh[1][kk], Rz = ny[g][2] - sh[2][kk];
-          const double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-          const double ri = 1.0 / sqrt(r2);
-          const double i2 = ri * ri, i3 = i2 * ri, i5 = i3 * i2, i7 = i5 * i2;
-          const double pR = px * Rx + py * Ry + pz * Rz;
-          const double QRx = Qxx * Rx + Qxy * Ry + Qxz * Rz;
-          const double QRy = Qxy * Rx + Qyy * Ry + Qyz * Rz;
-          const double QRz = Qxz * Rx + Qyz * Ry + Qzz * Rz;
-          const double RQR = QRx * Rx + QRy * Ry + QRz * Rz;
-          const double U = q * ri + pR * i3 + 0.5 * RQR * i5;
-          const double cR = -q * i3 - 3.0 * pR * i5 - 2.5 * RQR * i7;  // coefficient of R in grad U
-          const double gx = cR * Rx + px * i3 + QRx * i5;
-          const double gy = cR * Ry + py * i3 + QRy * i5;
-          const double gz = cR * Rz + pz * i3 + QRz * i5;
-          aU += ny[g][3] * U;
-          aG += ny[g][3] * (nj.x * gx + nj.y * gy + nj.z * gz);
+          const Real Rx = ny[g][0] - sh[0][kk], Ry = ny[g][1] - sh[1][kk], Rz = ny[g][2] - sh[2][kk];
+          const Real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+          const Real ri = (Real)1 / sqrt(r2);
+          const Real i2 = ri * ri, i3 = i2 * ri, i5 = i3 * i2, i7 = i5 * i2;
+          const Real pR = px * Rx + py * Ry + pz * Rz;
+          const Real QRx = Qxx * Rx + Qxy * Ry + Qxz * Rz;
+          const Real QRy = Qxy * Rx + Qyy * Ry + Qyz * Rz;
+          const Real QRz = Qxz * Rx + Qyz * Ry + Qzz * Rz;
+          const Real RQR = QRx * Rx + QRy * Ry + QRz * Rz;
+          const Real U = q * ri + pR * i3 + (Real)0.5 * RQR * i5;
+          const Real cR = -q * i3 - (Real)3 * pR * i5 - (Real)2.5 * RQR * i7;  // coefficient of R in grad U
+          const Real gx = cR * Rx + px * i3 + QRx * i5;
+          const Real gy = cR * Ry + py * i3 + QRy * i5;
+          const Real gz = cR * Rz + pz * i3 + QRz * i5;
+          tU += ny[g][3] * U;
+          tG += ny[g][3] * (nj[0] * gx + nj[1] * gy + nj[2] * gz);
         }
       }
     }
+    aU += (double)tU;
+    aG += (double)tG;
     __syncthreads();
   }
   if (act) {
@@ -435,9 +446,12 @@ __global__ void adj_weights_kernel(int ns, const double* __restrict__ q, const d
 }
 
 // charges lambda_1 / eps_in at the collocation points, as (x, 0, 0, 0) strengths
-__global__ void lam_strength_kernel(const double* __restrict__ lam, int n, double inv_eps, double4* __restrict__ str) {
+__global__ void lam_strength_kernel(const double* __restrict__ lam, int n, double inv_eps, double4* __restrict__ str,
+                                    float4* __restrict__ str32) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) str[i] = make_double4(lam[i] * inv_eps, 0.0, 0.0, 0.0);
+  if (i >= n) return;
+  str[i] = make_double4(lam[i] * inv_eps, 0.0, 0.0, 0.0);
+  str32[i] = make_float4((float)(lam[i] * inv_eps), 0.f, 0.f, 0.f);
 }
 
 // gradient from the combined 10-vectors: g_q = f[0], g_d = f[1..3], g_Q = traceless(H) / 6
@@ -696,9 +710,9 @@ void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s) {
 void matvec_T_internal(Ctx& c, const double* u, double* y, int op, cudaStream_t s) {
   const int n = c.n;
   const bool fp32 = (op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE);
-  if (op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE) {
-    tree_matvec_T_sums(c, u, fp32, s);
-  } else {
+  if (op == BEMPOL_OP_FP32_TREE) {
+    tree_matvec_T_sums(c, u, s);
+  } else {  // the direct forms; the FP64 tree form is applied as the FP64 direct product
     int maxr = 1;
     for (int g = 0; g < c.ngroup; ++g) {
       const int sy = c.h_grp_sys[g];
@@ -764,10 +778,13 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   const int n = c.n, ns = c.ns, S = c.nsys, len = 2 * n;
   const bempol_params& P = c.par;
   const double scale = INV4PI / P.eps_in;
+  // site-side sums in FP32 pairs (FP64 sums) when the solves' residual is an FP32 form
+  const bool f32 = (P.residual_op == BEMPOL_OP_FP32_DIRECT || P.residual_op == BEMPOL_OP_FP32_TREE);
   AdjointOut ao;
   DBuf<double> F_s, P_mu, P_0, Pv_mu, Pv_0, cmu, cmuv, nu, nuv, tn, psi, phinu, phinuv, g10, gv10, wq, wd, wQ, rT,
       lam;
   DBuf<double4> lstr;
+  DBuf<float4> lstr32;
   DBuf<int> d_act;
   for (auto* b : {&F_s, &P_mu, &P_0, &Pv_mu, &Pv_0, &psi, &phinu, &phinuv, &g10, &gv10}) b->alloc(10 * (size_t)ns);
   for (auto* b : {&cmu, &cmuv, &nu, &nuv, &tn, &wd}) b->alloc(3 * (size_t)ns);
@@ -776,6 +793,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   rT.alloc(len);
   lam.alloc(len);
   lstr.alloc(n);
+  lstr32.alloc(n);
   d_act.alloc(S);
   nu.zero(s);
   nuv.zero(s);
@@ -784,7 +802,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   zero3.alloc(3 * (size_t)ns);
   zero3.zero(s);
   // forward quantities at the solution: reaction fields (FP64) and energy-form multipole potentials
-  site_reaction_internal(c, c.sol_x.p, F_s.p, false, true, s);
+  site_reaction_internal(c, c.sol_x.p, F_s.p, f32, true, s);
   multipole_internal(c, c.sol_mu.p, 1, P_mu.p, s);
   multipole_internal(c, zero3.p, 1, P_0.p, s);
   multipole_internal(c, c.sol_mu_v.p, 3, Pv_mu.p, s);
@@ -815,8 +833,12 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   auto adj_bem = [&](const std::vector<char>& want) {
     launch(adj_weights_kernel, cdiv(ns, 128), 128, 0, s, ns, c.site_q.p, c.site_d.p, c.site_Q.p, nu.p, wq.p, wd.p,
            wQ.p);
-    launch(adj_reaction_kernel, c.ndblk, TPB, 0, s, c.src64.p, c.nrm64.p, c.K, n, c.dblk.p, c.gsite.p,
-           c.site_pos.p, wq.p, wd.p, wQ.p, rT.p);
+    if (f32)
+      launch(adj_reaction_kernel<float>, c.ndblk, TPB, 0, s, c.src64.p, c.nrm64.p, c.K, n, c.dblk.p, c.blk_center.p,
+             c.gsite.p, c.site_pos.p, wq.p, wd.p, wQ.p, rT.p);
+    else
+      launch(adj_reaction_kernel<double>, c.ndblk, TPB, 0, s, c.src64.p, c.nrm64.p, c.K, n, c.dblk.p,
+             c.blk_center.p, c.gsite.p, c.site_pos.p, wq.p, wd.p, wQ.p, rT.p);
     BP_CHECK_LAUNCH();
     GmresOut g;
     {
@@ -826,8 +848,8 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
     ao.gmres_iters += g.iters;
     ++ao.solves;
     if (!g.converged) ao.converged = false;
-    launch(lam_strength_kernel, cdiv(n, 256), 256, 0, s, lam.p, n, 1.0 / P.eps_in, lstr.p);
-    site_field_of_charges(c, c.tgt64.p, lstr.p, 1, psi.p, s);
+    launch(lam_strength_kernel, cdiv(n, 256), 256, 0, s, lam.p, n, 1.0 / P.eps_in, lstr.p, lstr32.p);
+    site_field_of_charges(c, c.tgt64.p, lstr.p, c.tgt32.p, lstr32.p, 1, f32, psi.p, s);
   };
   // dissolved: relaxed transposed SCF
   {

@@ -254,7 +254,7 @@ void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s)
 // tree.cu
 void build_tree(Ctx& c, cudaStream_t s);
 void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
-void tree_matvec_T_sums(Ctx& c, const double* u, bool fp32, cudaStream_t s);
+void tree_matvec_T_sums(Ctx& c, const double* u, cudaStream_t s);
 void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells);
 // adjoint.cu
 void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s);
@@ -265,7 +265,8 @@ struct AdjointOut {
 };
 AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, double* g_pos, cudaStream_t s);
 // sites.cu
-void site_field_of_charges(Ctx& c, const double4* src, const double4* str, int K, double* out10, cudaStream_t s);
+void site_field_of_charges(Ctx& c, const double4* src, const double4* str, const float4* src32, const float4* str32,
+                           int K, bool fp32, double* out10, cudaStream_t s);
 void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s);
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s);
 void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s);

@@ -416,15 +416,20 @@ void site_reaction_launch(Ctx& c, int S, bool fp32, bool hessian, double* part, 
 
 // Potential, gradient and Hessian (10 per site, x 1/(4 pi)) at every site of the
 // field of point charges str[j].x at positions src[j] (K per panel), over the
-// panels of the site's own body, in FP64.
-void site_field_of_charges(Ctx& c, const double4* src, const double4* str, int K, double* out10, cudaStream_t s) {
+// panels of the site's own body; FP64, or FP32 pairs with FP64 sums (src32, str32).
+void site_field_of_charges(Ctx& c, const double4* src, const double4* str, const float4* src32, const float4* str32,
+                           int K, bool fp32, double* out10, cudaStream_t s) {
   int mr = 1;
   for (int g = 0; g < c.ngroup; ++g) mr = std::max(mr, K * (c.h_gpan[g + 1] - c.h_gpan[g]));
   const int S = site_splits(c, mr);
   size_t need = (size_t)S * c.ns * 10;
   if (c.site_part.n < need) c.site_part.alloc(need);
-  launch(site_reaction_kernel<double, double4, true>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p,
-         c.gpan.p, K, src, str, c.site_part.p);
+  if (fp32)
+    launch(site_reaction_kernel<float, float4, true>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p,
+           c.gpan.p, K, src32, str32, c.site_part.p);
+  else
+    launch(site_reaction_kernel<double, double4, true>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p,
+           c.gpan.p, K, src, str, c.site_part.p);
   launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, c.site_part.p, S, c.ns, out10);
   BP_CHECK_LAUNCH();
 }

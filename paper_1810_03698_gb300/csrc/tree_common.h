@@ -1,0 +1,293 @@
+// Shared pieces of the treecode (tree.cu: the matrix-vector product; treeT.cu: its
+// transpose): launch constants, the multi-index tables of the Taylor expansions,
+// FP32 approximate rsqrt/exp2, the cell-geometry and leaf-relative position kernels,
+// and the moment kernels (leaf moments from sources, exact M2M shifts).
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.h"
+
+namespace bp {
+
+namespace {
+
+
+constexpr int TB = 128;      // threads per block of the moment kernels
+constexpr int TBT = 128;     // targets per block of the near/far kernels (up to four warps of one
+                             // leaf); warps with no target skip the arithmetic and only help
+                             // stage shared data, so only the last warp of a leaf has idle lanes
+constexpr int MAXP = 6;      // highest Taylor order compiled
+
+// ---------------------------------------------------------------- multi-index tables
+template <int P>
+struct MI {
+  static constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+  int k[NC][3];
+  int ord[NC];
+  int m1[NC][3];  // index of k - e_j, or -1
+  int m2[NC][3];  // index of k - 2 e_j, or -1
+  int p1[NC][3];  // index of k + e_j, or -1 above order P
+  int idx[P + 1][P + 1][P + 1];
+  constexpr MI() : k{}, ord{}, m1{}, m2{}, p1{}, idx{} {
+    int t = 0;
+    for (int a = 0; a <= P; ++a)
+      for (int b = 0; b <= P; ++b)
+        for (int c = 0; c <= P; ++c) idx[a][b][c] = -1;
+    for (int n = 0; n <= P; ++n)
+      for (int a = n; a >= 0; --a)
+        for (int b = n - a; b >= 0; --b) {
+          k[t][0] = a;
+          k[t][1] = b;
+          k[t][2] = n - a - b;
+          ord[t] = n;
+          idx[a][b][n - a - b] = t;
+          ++t;
+        }
+    for (int u = 0; u < NC; ++u)
+      for (int j = 0; j < 3; ++j) {
+        int q[3] = {k[u][0], k[u][1], k[u][2]};
+        m1[u][j] = -1;
+        m2[u][j] = -1;
+        if (q[j] >= 1) {
+          q[j] -= 1;
+          m1[u][j] = idx[q[0]][q[1]][q[2]];
+          q[j] += 1;
+        }
+        if (q[j] >= 2) {
+          q[j] -= 2;
+          m2[u][j] = idx[q[0]][q[1]][q[2]];
+          q[j] += 2;
+        }
+        p1[u][j] = -1;
+        if (ord[u] < P) {
+          q[j] += 1;
+          p1[u][j] = idx[q[0]][q[1]][q[2]];
+          q[j] -= 1;
+        }
+      }
+  }
+};
+
+__host__ __device__ constexpr int ncoef(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
+
+// constant-memory copies for kernels that index the tables at run time
+template <int P>
+__constant__ MI<P> c_mi{};
+
+struct Binom {
+  int b[MAXP + 1][MAXP + 1];
+  constexpr Binom() : b{} {
+    for (int a = 0; a <= MAXP; ++a) {
+      b[a][0] = 1;
+      for (int q = 1; q <= a; ++q) b[a][q] = b[a - 1][q - 1] + (q <= a - 1 ? b[a - 1][q] : 0);
+    }
+  }
+};
+__constant__ Binom c_binom{};
+
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float exp2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float inv_sqrt(float x) { return rsqrt_approx(x); }
+__device__ __forceinline__ double inv_sqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float exp_neg(float kr) { return exp2_approx(-1.4426950408889634f * kr); }
+__device__ __forceinline__ double exp_neg(double kr) { return exp(-kr); }
+
+template <typename R4>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  typedef float4 T;
+};
+template <>
+struct Vec4<double> {
+  typedef double4 T;
+};
+
+// ---------------------------------------------------------------- cell geometry
+// centre = midpoint of the bounding box of the cell's Gauss nodes; radius = max distance to them
+__global__ void cell_geometry_kernel(const int* __restrict__ begin, const int* __restrict__ end, int K,
+                                     const double4* __restrict__ src64, double4* __restrict__ center) {
+  __shared__ double sh[6][256];
+  const int cidx = blockIdx.x;
+  const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int j = s0 + threadIdx.x; j < s1; j += 256) {
+    double4 y = src64[j];
+    lo[0] = fmin(lo[0], y.x); hi[0] = fmax(hi[0], y.x);
+    lo[1] = fmin(lo[1], y.y); hi[1] = fmax(hi[1], y.y);
+    lo[2] = fmin(lo[2], y.z); hi[2] = fmax(hi[2], y.z);
+  }
+  for (int d = 0; d < 3; ++d) {
+    sh[d][threadIdx.x] = lo[d];
+    sh[3 + d][threadIdx.x] = hi[d];
+  }
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s)
+      for (int d = 0; d < 3; ++d) {
+        sh[d][threadIdx.x] = fmin(sh[d][threadIdx.x], sh[d][threadIdx.x + s]);
+        sh[3 + d][threadIdx.x] = fmax(sh[3 + d][threadIdx.x], sh[3 + d][threadIdx.x + s]);
+      }
+    __syncthreads();
+  }
+  const double cx = 0.5 * (sh[0][0] + sh[3][0]), cy = 0.5 * (sh[1][0] + sh[4][0]), cz = 0.5 * (sh[2][0] + sh[5][0]);
+  __syncthreads();
+  double r2 = 0.0;
+  for (int j = s0 + threadIdx.x; j < s1; j += 256) {
+    double4 y = src64[j];
+    double dx = y.x - cx, dy = y.y - cy, dz = y.z - cz;
+    r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+  }
+  sh[0][threadIdx.x] = r2;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if (threadIdx.x < s) sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) center[cidx] = make_double4(cx, cy, cz, sqrt(sh[0][0]));
+}
+
+// FP32 position of every Gauss node relative to the centre of its leaf (FP64 subtraction)
+__global__ void src_rel_kernel(const int* __restrict__ leaf_cell, int nleaf, const int* __restrict__ begin,
+                               const int* __restrict__ end, const double4* __restrict__ center, int K,
+                               const double4* __restrict__ src64, float4* __restrict__ rel) {
+  const int l = blockIdx.x;
+  if (l >= nleaf) return;
+  const int cl = leaf_cell[l];
+  const double4 c = center[cl];
+  for (int j = begin[cl] * K + threadIdx.x; j < end[cl] * K; j += blockDim.x) {
+    const double4 y = src64[j];
+    rel[j] = make_float4((float)(y.x - c.x), (float)(y.y - c.y), (float)(y.z - c.z), 0.f);
+  }
+}
+
+// ---------------------------------------------------------------- moments
+// Leaf moments from the sources: one block per leaf, thread o owns moments o, o + TB, ...
+template <int P, typename Real>
+__global__ void __launch_bounds__(TB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
+                                                          const int* __restrict__ begin, const int* __restrict__ end,
+                                                          const double4* __restrict__ center, int K,
+                                                          const double4* __restrict__ src64,
+                                                          const typename Vec4<Real>::T* __restrict__ str,
+                                                          const int* __restrict__ active,
+                                                          const int* __restrict__ leaf_sys, Real* __restrict__ mom) {
+  const MI<P>& mi = c_mi<P>;
+  constexpr int NC = MI<P>::NC;
+  __shared__ Real pw[TB][3][P + 1];
+  __shared__ Real sd[TB][4];
+  if (active && !active[leaf_sys[blockIdx.x]]) return;  // system not being solved
+  const int cidx = leaf_cell[blockIdx.x];
+  const double4 c = center[cidx];
+  const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
+  Real acc[(2 * NC + TB - 1) / TB];
+  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) acc[u] = 0;
+  for (int t0 = s0; t0 < s1; t0 += TB) {
+    int j = t0 + threadIdx.x;
+    if (j < s1) {
+      double4 y = src64[j];
+      Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
+      for (int d = 0; d < 3; ++d) {
+        Real p = 1;
+        for (int e = 0; e <= P; ++e) {
+          pw[threadIdx.x][d][e] = p;
+          p *= h[d];
+        }
+      }
+      auto s = str[j];
+      sd[threadIdx.x][0] = s.x;
+      sd[threadIdx.x][1] = s.y;
+      sd[threadIdx.x][2] = s.z;
+      sd[threadIdx.x][3] = s.w;
+    }
+    __syncthreads();
+    const int lim = min(TB, s1 - t0);
+    for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
+      const int o = threadIdx.x + u * TB;
+      if (o >= 2 * NC) break;
+      const bool dbl = o >= NC;
+      const int t = dbl ? o - NC : o;
+      const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
+      Real a = 0;
+      for (int q = 0; q < lim; ++q) {
+        if (!dbl) {
+          a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
+        } else {
+          Real v = 0;
+          if (kx) v += (Real)kx * sd[q][1] * pw[q][0][kx - 1] * pw[q][1][ky] * pw[q][2][kz];
+          if (ky) v += (Real)ky * sd[q][2] * pw[q][0][kx] * pw[q][1][ky - 1] * pw[q][2][kz];
+          if (kz) v += (Real)kz * sd[q][3] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz - 1];
+          a += v;
+        }
+      }
+      acc[u] += a;
+    }
+    __syncthreads();
+  }
+  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
+    const int o = threadIdx.x + u * TB;
+    if (o < 2 * NC) mom[(size_t)cidx * 2 * NC + o] = acc[u];
+  }
+}
+
+// Parent moments by shifting the children's: one block per parent cell of one depth.
+template <int P, typename Real>
+__global__ void __launch_bounds__(TB) m2m_kernel(int first_cell, const int* __restrict__ child0,
+                                                 const int* __restrict__ nchild, const double4* __restrict__ center,
+                                                 Real* __restrict__ mom) {
+  const MI<P>& mi = c_mi<P>;
+  constexpr int NC = MI<P>::NC;
+  __shared__ Real dp[8][3][P + 1];
+  __shared__ Real cm[8][2 * NC];
+  const int pc = first_cell + blockIdx.x;
+  const int nch = nchild[pc];
+  if (nch == 0) return;  // leaf (uniform across the block)
+  const int c0 = child0[pc];
+  const double4 cp = center[pc];
+  if (threadIdx.x < nch) {
+    double4 cc = center[c0 + threadIdx.x];
+    Real dl[3] = {(Real)(cc.x - cp.x), (Real)(cc.y - cp.y), (Real)(cc.z - cp.z)};
+    for (int d = 0; d < 3; ++d) {
+      Real p = 1;
+      for (int e = 0; e <= P; ++e) {
+        dp[threadIdx.x][d][e] = p;
+        p *= dl[d];
+      }
+    }
+  }
+  for (int q = threadIdx.x; q < nch * 2 * NC; q += TB) cm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)(c0 + q / (2 * NC)) * 2 * NC + q % (2 * NC)];
+  __syncthreads();
+  const auto& binom = c_binom.b;
+  for (int o = threadIdx.x; o < 2 * NC; o += TB) {
+    const int t = o < NC ? o : o - NC;
+    const int off = o < NC ? 0 : NC;
+    const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
+    Real a = 0;
+    for (int ch = 0; ch < nch; ++ch)
+      for (int lx = 0; lx <= kx; ++lx)
+        for (int ly = 0; ly <= ky; ++ly)
+          for (int lz = 0; lz <= kz; ++lz) {
+            const int l = mi.idx[lx][ly][lz];
+            a += (Real)(binom[kx][lx] * binom[ky][ly] * binom[kz][lz]) * dp[ch][0][kx - lx] * dp[ch][1][ky - ly] *
+                 dp[ch][2][kz - lz] * cm[ch][off + l];
+          }
+    mom[(size_t)pc * 2 * NC + o] = a;
+  }
+}
+
+constexpr int FCH = 8;   // far cells staged in shared memory per pass
+constexpr int NTB = 32;  // targets (one warp) per near-field block
+
+}  // namespace
+
+}  // namespace bp

@@ -71,6 +71,22 @@ def _sample(pr):
     return np.array(sorted({0, n // 2, n - 1}))
 
 
+@pytest.mark.parametrize("theta,bar", [(1e-3, 2e-5), (0.5, 5e-4)])
+def test_transposed_tree(bp, theta, bar):
+    """FP32 treecode A^T u (order 5): theta -> 0 reduces it to the FP32 direct sum; at
+    theta = 0.5 it is within the forward treecode's bar of the dense A^T u."""
+    pr = gen.small_bumpy(3, 8, 8.0, seed_index=108)
+    par = pr.params
+    mesh = bem.build_mesh(pr.verts, pr.tris, par.gauss_k, par.near_factor)
+    A = bem.system_matrix(bem.assemble_layers(mesh, par.kappa), par.eps_in, par.eps_out)
+    s = bp.problem_solver(pr, leaf=32, theta=theta, order=5)
+    u = np.random.default_rng(32).normal(size=2 * mesh.n)
+    y = torch.zeros(2 * mesh.n, dtype=torch.float64, device="cuda")
+    s.matvec_transposed(_dev(u), y, op="fp32_tree")
+    assert s.sizes()["n_leaves"] > 8
+    assert _relmax(y.cpu().numpy(), A.T @ u) < bar
+
+
 @pytest.fixture(scope="module")
 def oracle_grad(prob):
     """Oracle derivatives for three sites (first, middle, last: both bodies of the complex)."""
@@ -96,6 +112,17 @@ def test_moment_gradient_fp64(bp, prob, oracle_grad):
 def test_moment_gradient_fp32_refined(bp, prob, oracle_grad):
     _, pr = prob
     s = bp.problem_solver(pr, op="fp32_direct", residual_op="fp64_direct")
+    s.solve()
+    g = s.gradient()
+    idx = _sample(pr)
+    for k in ("q", "d", "Q", "pos"):
+        assert _relmax(g[k][idx], oracle_grad[k]) < 1e-6, k
+
+
+def test_moment_gradient_tree(bp, prob, oracle_grad):
+    """FP32 treecode forward and transposed solves with FP64 direct refinement."""
+    _, pr = prob
+    s = bp.problem_solver(pr, op="fp32_tree", residual_op="fp64_direct", leaf=32, theta=0.5, order=5)
     s.solve()
     g = s.gradient()
     idx = _sample(pr)
