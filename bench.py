@@ -300,12 +300,20 @@ def run_gradient(args, local):
     sampler = ClockSampler(local)
     sampler.start()
     fw, gr = [], []
+    s.stats_enable(True)
+    kst = {"forward": None, "gradient": None}
     for _ in range(args.steps):
+        s.stats(reset=True)
         ms_f, out = ev_time(lambda: s.solve())
+        kst["forward"] = s.stats(reset=True)
         ms_g, g = ev_time(lambda: s.gradient())
+        kst["gradient"] = s.stats(reset=True)
         fw.append(ms_f)
         gr.append(ms_g)
     clocks = sampler.stop()
+    for k, v in kst.items():   # per-step kernel times of the last step (pair / near and far-field kernels)
+        kst[k] = {"pair_ms": v["pair_ms"], "pair_launches": v["pair_launches"], "far_ms": v["far_ms"],
+                  "far_launches": v["far_launches"], "kernel_launches": v["kernel_launches"]}
     st = pr.sites
     dG = out["G_diss"] - out["G_vac"]
     euler = float(np.sum(st.q * g["q"]) + np.sum(st.d * g["d"]) + np.sum(st.Q * g["Q"]))
@@ -319,7 +327,7 @@ def run_gradient(args, local):
                    "theta": pr.params.theta, "order": pr.params.order, "gmres_tol": pr.params.gmres_tol,
                    "scf_tol": pr.params.scf_tol},
         "forward_s": float(np.mean(fw)) / 1e3, "gradient_over_forward": float(np.mean(gr) / np.mean(fw)),
-        "adjoint": g["info"], "dG_solv_kcal": out["dG_solv_kcal"],
+        "adjoint": g["info"], "kernels": kst, "dG_solv_kcal": out["dG_solv_kcal"],
         "euler_rel_err": abs(euler - 2.0 * dG) / abs(2.0 * dG), "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -520,6 +528,11 @@ def main():
                    "performed_pairs": mv_stats["pair_interactions"] / max(1, args.matvec_reps),
                    "fp64_direct_ms": f64_ms,
                    "fp64_direct_ginter_s": (inter / (f64_ms * 1e-3) / 1e9) if f64_ms else None,
+                   # FP64 direct at the same 28 algorithmic flops per pair, against GB300's nominal
+                   # FP64 rate (1.25 TFLOP/s; FP64 sqrt, divide and exp run as instruction sequences)
+                   "fp64_direct_tflops_algorithmic": (inter * FLOPS_PER_PAIR / (f64_ms * 1e-3) / 1e12)
+                   if f64_ms else None,
+                   "fp64_peak_nominal_tflops": 1.25,
                    "interactions_per_matvec": inter},
         "roofline": roofline,
         "cpu_baseline": cpu,

@@ -283,8 +283,8 @@ bempol_status bempol_matvec(bempol_ctx* c, const double* x, double* y, int op, v
  * the paper has no counterpart): charges x_phi (Laplace) and x_psi (Yukawa) at the
  * collocation points evaluated at every panel's Gauss nodes, plus the near
  * corrections by columns.  BEMPOL_OP_FP32_TREE uses the same octree and lists
- * with charge moments of order 5 whatever params.order (the nodes' potential
- * gradient takes coefficients to order 6); BEMPOL_OP_FP64_TREE is applied as
+ * with charge moments of order 4 whatever params.order (the nodes' potential
+ * gradient takes coefficients to order 5); BEMPOL_OP_FP64_TREE is applied as
  * BEMPOL_OP_FP64_DIRECT.
  * x, y: device float64 [2N] in the caller's order (y may not alias x).  Enqueued
  * on `stream`, no synchronisation. */
@@ -331,6 +331,26 @@ bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const double* x, doubl
  *   modes 2 and 3 are modes 0 and 1 summed over every site of its system (vacuum).
  * FP64.  Enqueued on `stream`. */
 bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, double* out, void* stream);
+
+/* Autotuner of the treecode (not a step of the paper's method): for the current mesh,
+ * times the FP32 treecode product (CUDA events, mean of 3 after a warm-up) for every
+ * leaf in {128, 192, 256, 384}, theta in {0.4, 0.5, 0.6} and order in {4, 5, 6}, measures
+ * its error ||y - y_ref|| / ||y_ref|| against the FP32 direct product y_ref on a fixed
+ * pseudo-random vector, and keeps in the context's parameters the fastest candidate
+ * whose error is <= target_err (the tree is rebuilt for it).  `out` (host, may be
+ * NULL) receives the choice, its time and error and the number of candidates.
+ * BEMPOL_ERR_NOT_CONVERGED (parameters unchanged) if no candidate reaches the target.
+ * Synchronises `stream`. */
+typedef struct {
+  int leaf;
+  double theta;
+  int order;
+  double matvec_ms;   /* FP32 treecode product time of the choice */
+  double rel_err;     /* its error against the FP32 direct product */
+  int candidates;
+} bempol_tune_result;
+
+bempol_status bempol_autotune(bempol_ctx* c, double target_err, bempol_tune_result* out, void* stream);
 
 /* Sizes of the library's tables: number of panels, Gauss nodes per panel,
  * sites, near pairs, treecode cells and leaves (any pointer may be NULL). */

@@ -64,6 +64,11 @@ class GradientInfo(C.Structure):
     ]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("leaf", C.c_int), ("theta", C.c_double), ("order", C.c_int), ("matvec_ms", C.c_double),
+                ("rel_err", C.c_double), ("candidates", C.c_int)]
+
+
 class Stats(C.Structure):
     _fields_ = [
         ("kernel_launches", C.c_int64), ("pair_launches", C.c_int64), ("pair_ms", C.c_double),
@@ -92,6 +97,7 @@ def _load():
         "bempol_solve_systems": (i32, [vp, vp, C.POINTER(Result), C.POINTER(SystemResult), i64]),
         "bempol_matvec": (i32, [vp, vp, vp, i32, vp]),
         "bempol_matvec_transposed": (i32, [vp, vp, vp, i32, vp]),
+        "bempol_autotune": (i32, [vp, dp, C.POINTER(TuneResult), vp]),
         "bempol_gradient": (i32, [vp, vp, vp, vp, vp, vp, C.POINTER(GradientInfo)]),
         "bempol_rhs": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction": (i32, [vp, vp, vp, i32, vp]),
@@ -313,6 +319,14 @@ class Solver:
     def multipole_field(self, out, mu=None, mode=0, stream=None):
         self._chk(_lib.bempol_multipole_field(self._h, _ptr(mu)[0], mode, _ptr(out)[0], _stream(stream)))
 
+    def autotune(self, target_err=1e-5, stream=None):
+        """Pick leaf, theta and order for the current mesh (bempol_autotune); returns the
+        choice and updates this Solver's parameters."""
+        r = TuneResult()
+        self._chk(_lib.bempol_autotune(self._h, float(target_err), C.byref(r), _stream(stream)))
+        self.params.leaf, self.params.theta, self.params.order = r.leaf, r.theta, r.order
+        return {k: getattr(r, k) for k, _ in TuneResult._fields_}
+
     def stats_enable(self, on=True):
         self._chk(_lib.bempol_stats_enable(self._h, 1 if on else 0))
 
@@ -333,6 +347,45 @@ class Solver:
         out["near_col"] = out["near_col"][:nnz]
         out["near_corr"] = out["near_corr"][:nnz]
         return out
+
+
+KCAL_PER_UNIT = 4.0 * 3.141592653589793 * 332.0637132991921  # kcal/mol per e^2/A (vacuum permittivity 1)
+
+
+def _torch_function():
+    import torch
+
+    class SolvationEnergy(torch.autograd.Function):
+        """Delta G_solv (kcal/mol) of a Solver's mesh with sites (pos, q, d, Q) as a
+        differentiable function: forward = bempol_set_sites + bempol_solve, backward =
+        bempol_gradient (the adjoint of the BEM solve and of the induced-dipole
+        relaxation).  alpha and the polarisation groups are fixed inputs; the quadrupole
+        gradient is the symmetric traceless one.  The backward uses the Solver's last
+        solve, so no other solve may run on that Solver between forward and backward."""
+
+        @staticmethod
+        def forward(ctx, solver, pos, q, d, Q, alpha, group=None):
+            c = lambda t: t.detach().to(torch.float64).contiguous()
+            solver.set_sites(c(pos), c(q), c(d), c(Q).reshape(-1, 9), c(alpha),
+                             None if group is None else group.to(torch.int32).contiguous())
+            r = solver.solve()
+            ctx.solver = solver
+            ctx.dev = pos.device
+            return torch.tensor(r["dG_solv_kcal"], dtype=torch.float64, device=pos.device)
+
+        @staticmethod
+        def backward(ctx, g):
+            gr = ctx.solver.gradient()
+            k = g.to(torch.float64) * KCAL_PER_UNIT
+            t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=ctx.dev) * k
+            return None, t(gr["pos"]), t(gr["q"]), t(gr["d"]), t(gr["Q"]), None, None
+
+    return SolvationEnergy
+
+
+def solvation_energy(solver, pos, q, d, Q, alpha, group=None):
+    """Differentiable Delta G_solv in kcal/mol (torch.autograd), see ``SolvationEnergy``."""
+    return _torch_function().apply(solver, pos, q, d, Q, alpha, group)
 
 
 def _param_kw(par, overrides):

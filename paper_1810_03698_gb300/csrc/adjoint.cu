@@ -622,6 +622,9 @@ __global__ void __launch_bounds__(256) pair_force_kernel(const double4* __restri
 // d/dr_l <w_l, F(r_l)> of the field F of surface sources (charge s.x, dipole s.y..w,
 // at K positions per panel of l's body), warp per site, sources staged in shared
 // memory; blockIdx.y takes an equal share; part[(y * ns + l) * 3 ..] (x 4 pi).
+// S = float: dual arithmetic in FP32 (sites are at least a near radius from every
+// panel), per-lane sums in FP64.
+template <typename S>
 __global__ void __launch_bounds__(256) site_force_kernel(const double4* __restrict__ spos, int ns,
                                                          const int4* __restrict__ sblk, const int* __restrict__ gpan,
                                                          int K, const double4* __restrict__ src,
@@ -645,7 +648,7 @@ __global__ void __launch_bounds__(256) site_force_kernel(const double4* __restri
     for (int a = 0; a < 3; ++a) w1[a] = wd[3 * site + a];
     for (int a = 0; a < 6; ++a) w2[a] = wQ[6 * site + a];
   }
-  const Dual3 X[3] = {seed(sd.x, 0), seed(sd.y, 1), seed(sd.z, 2)};
+  const Dual3T<S> X[3] = {seed_of<S>((S)sd.x, 0), seed_of<S>((S)sd.y, 1), seed_of<S>((S)sd.z, 2)};
   double acc[3] = {0, 0, 0};
   for (int t0 = s0; t0 < s1; t0 += T) {
     const int j = t0 + threadIdx.x;
@@ -658,13 +661,13 @@ __global__ void __launch_bounds__(256) site_force_kernel(const double4* __restri
     if (act) {
       for (int k = lane; k < lim; k += 32) {
         const double4 p = tp[k], sv = ts[k];
-        const Dual3 R[3] = {X[0] - p.x, X[1] - p.y, X[2] - p.z};
-        Dual3 P, g[3], H[6];
+        const Dual3T<S> R[3] = {X[0] - (S)p.x, X[1] - (S)p.y, X[2] - (S)p.z};
+        Dual3T<S> P, g[3], H[6];
         field_cd(sv.x, -sv.y, -sv.z, -sv.w, R, P, g, H);
-        const Dual3 e = contract(w0, w1, w2, P, g, H);
-        acc[0] += e.d0;
-        acc[1] += e.d1;
-        acc[2] += e.d2;
+        const Dual3T<S> e = contract(w0, w1, w2, P, g, H);
+        acc[0] += (double)e.d0;
+        acc[1] += (double)e.d1;
+        acc[2] += (double)e.d2;
       }
     }
     __syncthreads();
@@ -755,7 +758,7 @@ namespace {
 
 // d/dr_l <w_l, F(r_l)> / (4 pi) for surface sources (src, str, K per panel) of l's body
 void site_force(Ctx& c, const double4* src, const double4* str, int K, const double* wq, const double* wd,
-                const double* wQ, double* out3, cudaStream_t s) {
+                const double* wQ, double* out3, bool f32, cudaStream_t s) {
   int mr = 1;
   for (int g = 0; g < c.ngroup; ++g) mr = std::max(mr, K * (c.h_gpan[g + 1] - c.h_gpan[g]));
   int S = std::max(1, cdiv((long long)num_sms(c.device) * 6, std::max(1, c.nsblk)));
@@ -765,8 +768,12 @@ void site_force(Ctx& c, const double4* src, const double4* str, int K, const dou
   S = std::max(1, cdiv(mr, per));
   DBuf<double> part;
   part.alloc((size_t)S * c.ns * 3);
-  launch(site_force_kernel, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p, c.gpan.p, K, src, str, wq,
-         wd, wQ, part.p);
+  if (f32)
+    launch(site_force_kernel<float>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p, c.gpan.p, K, src,
+           str, wq, wd, wQ, part.p);
+  else
+    launch(site_force_kernel<double>, dim3(c.nsblk, S), 256, 0, s, c.site_pos.p, c.ns, c.sblk.p, c.gpan.p, K, src,
+           str, wq, wd, wQ, part.p);
   launch(force_reduce_kernel, cdiv(c.ns * 3, 256), 256, 0, s, part.p, S, c.ns, INV4PI, out3);
   BP_CHECK_LAUNCH();
   BP_CUDA(cudaStreamSynchronize(s));  // `part` is released on return
@@ -930,10 +937,10 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
     wq2.alloc(ns);
     wQ2.alloc(6 * (size_t)ns);
     strengths(c, c.sol_x.p, false, s);
-    site_force(c, c.src64.p, c.str64.p, c.K, wq.p, wd.p, wQ.p, fA.p, s);
+    site_force(c, c.src64.p, c.str64.p, c.K, wq.p, wd.p, wQ.p, fA.p, f32, s);
     launch(rhs_weights_kernel, cdiv(ns, 128), 128, 0, s, ns, c.site_q.p, c.site_d.p, c.sol_mu.p, c.site_Q.p, wq2.p,
            wd2.p, wQ2.p);
-    site_force(c, c.tgt64.p, lstr.p, 1, wq2.p, wd2.p, wQ2.p, fB.p, s);
+    site_force(c, c.tgt64.p, lstr.p, 1, wq2.p, wd2.p, wQ2.p, fB.p, f32, s);
     launch(pair_force_kernel, cdiv(ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, c.sol_mu.p,
            nu.p, c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, ns, 0, P.thole_a, scale, pd.p);
     launch(pair_force_kernel, cdiv(ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p,

@@ -186,9 +186,28 @@ void ensure_tree(Ctx& c, int op, cudaStream_t s) {
   if (op_tree(op) && !c.tree_ready) build_tree(c, s);
 }
 
+__global__ void add_vec_scaled(const double* __restrict__ a, const double* __restrict__ b, double sb,
+                               double* __restrict__ o, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) o[i] = a[i] + sb * b[i];
+}
+
 __global__ void add_vec(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = a[i] + (b ? b[i] : 0.0);
+}
+
+// x[i] = a fixed pseudo-random value in [-1, 1) (integer hash of i and the seed)
+__global__ void hash_vector_kernel(double* __restrict__ x, int len, unsigned seed) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  unsigned h = (unsigned)i * 2654435761u ^ seed;
+  h ^= h >> 16;
+  h *= 2246822519u;
+  h ^= h >> 13;
+  h *= 3266489917u;
+  h ^= h >> 16;
+  x[i] = (double)h * (2.0 / 4294967296.0) - 1.0;
 }
 
 __global__ void pack_sites(const double* __restrict__ pos, const double* __restrict__ alpha, int ns,
@@ -510,6 +529,79 @@ bempol_status bempol_multipole_field(bempol_ctx* c, const double* mu, int mode, 
     }
     multipole_internal(*c, m, mode, out, s);
     if (!mu) BP_CUDA(cudaStreamSynchronize(s));
+  });
+}
+
+bempol_status bempol_autotune(bempol_ctx* c, double target_err, bempol_tune_result* out, void* stream) {
+  return guard(c, [&] {
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "no mesh");
+    if (!(target_err > 0.0)) fail(BEMPOL_ERR_ARG, "target_err must be > 0");
+    const int len = 2 * c->n;
+    const bempol_params saved = c->par;
+    DBuf<double> x, yref, y, d;
+    x.alloc(len);
+    yref.alloc(len);
+    y.alloc(len);
+    d.alloc(len);
+    launch(hash_vector_kernel, cdiv(len, 256), 256, 0, s, x.p, len, 1810036980u);
+    // reference: the FP32 direct product (every Gauss node, FP64 sums)
+    matvec_internal(*c, x.p, yref.p, BEMPOL_OP_FP32_DIRECT, s);
+    const double nref = std::sqrt(dot_dev(*c, yref.p, yref.p, len, s));
+    const int leaves[] = {128, 192, 256, 384};
+    const double thetas[] = {0.4, 0.5, 0.6};
+    const int orders[] = {4, 5, 6};
+    int best_leaf = saved.leaf, best_order = saved.order, tried = 0;
+    double best_theta = saved.theta, best_ms = 1e300, best_err = -1.0;
+    cudaEvent_t e0, e1;
+    BP_CUDA(cudaEventCreate(&e0));
+    BP_CUDA(cudaEventCreate(&e1));
+    for (int lf : leaves)
+      for (double th : thetas) {
+        c->par.leaf = lf;
+        c->par.theta = th;
+        build_tree(*c, s);
+        for (int P : orders) {
+          c->par.order = P;
+          matvec_internal(*c, x.p, y.p, BEMPOL_OP_FP32_TREE, s);  // warm (moment buffers)
+          BP_CUDA(cudaEventRecord(e0, s));
+          for (int r = 0; r < 3; ++r) matvec_internal(*c, x.p, y.p, BEMPOL_OP_FP32_TREE, s);
+          BP_CUDA(cudaEventRecord(e1, s));
+          BP_CUDA(cudaEventSynchronize(e1));
+          float ms = 0;
+          BP_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          ms /= 3.0f;
+          launch(add_vec_scaled, cdiv(len, 256), 256, 0, s, y.p, yref.p, -1.0, d.p, len);
+          const double err = std::sqrt(dot_dev(*c, d.p, d.p, len, s)) / nref;
+          ++tried;
+          if (err <= target_err && ms < best_ms) {
+            best_ms = ms;
+            best_err = err;
+            best_leaf = lf;
+            best_theta = th;
+            best_order = P;
+          }
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->par = saved;
+    if (best_err >= 0.0) {
+      c->par.leaf = best_leaf;
+      c->par.theta = best_theta;
+      c->par.order = best_order;
+    }
+    build_tree(*c, s);
+    c->have_solution = false;
+    if (out) {
+      out->leaf = c->par.leaf;
+      out->theta = c->par.theta;
+      out->order = c->par.order;
+      out->matvec_ms = best_err >= 0.0 ? best_ms : -1.0;
+      out->rel_err = best_err;
+      out->candidates = tried;
+    }
+    if (best_err < 0.0) fail(BEMPOL_ERR_NOT_CONVERGED, "no candidate reached target_err; parameters unchanged");
   });
 }
 

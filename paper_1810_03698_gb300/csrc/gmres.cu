@@ -27,14 +27,15 @@ namespace bp {
 namespace {
 
 constexpr int DOT_TPB = 256;
-constexpr int MAXV = 16;  // basis vectors handled per multi-dot pass
 
 // out[s * ldo + k] = sum over the elements of system s of V_k . w, for k < nv, in one
-// launch.  Block b handles chunks b, b + gridDim.x, ... and writes the partial sums
-// partial[chunk][k]; the last block to finish (atomic ticket) adds, for every
-// system, its chunks' partials in chunk order -- so the result does not depend on
-// scheduling -- and resets the ticket for the next call.  Systems with
-// active[s] == 0 are skipped (NULL = all active).
+// launch.  Work items are (chunk, vector) pairs, one warp each (grid-stride over the
+// items): the lanes sum the chunk's products with a fixed stride and a shuffle tree
+// gives partial[chunk][k]; the last block to finish (atomic ticket) adds, for every
+// system, its chunks' partials in a fixed order (a warp per sum: strided lane sums,
+// then a shuffle tree) -- so the result does not depend on scheduling -- and resets
+// the ticket for the next call.  Systems with active[s] == 0 are skipped (NULL = all
+// active).
 __global__ void __launch_bounds__(DOT_TPB) multidot_kernel(const double* __restrict__ V, size_t ld, int nv,
                                                            const double* __restrict__ w,
                                                            const int4* __restrict__ chunks, int nchunk,
@@ -43,49 +44,44 @@ __global__ void __launch_bounds__(DOT_TPB) multidot_kernel(const double* __restr
                                                            double* __restrict__ partial, int ldp,
                                                            unsigned* __restrict__ ticket, double* __restrict__ out,
                                                            int ldo, int accumulate) {
-  __shared__ double sh[MAXV][DOT_TPB / 32];
   __shared__ bool last;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int ci = blockIdx.x; ci < nchunk; ci += gridDim.x) {
+  const long long items = (long long)nchunk * nv;
+  const long long nwarps = (long long)gridDim.x * (DOT_TPB / 32);
+  for (long long it = (long long)blockIdx.x * (DOT_TPB / 32) + warp; it < items; it += nwarps) {
+    const int ci = (int)(it / nv), k = (int)(it - (long long)ci * nv);
     const int4 C = chunks[ci];
-    if (active && !active[C.x]) continue;  // uniform across the block
-    for (int k0 = 0; k0 < nv; k0 += MAXV) {
-      const int cnt = min(MAXV, nv - k0);
-      double acc[MAXV];
-#pragma unroll
-      for (int k = 0; k < MAXV; ++k) acc[k] = 0.0;
-      for (int i = C.y + threadIdx.x; i < C.z; i += DOT_TPB) {
-        const double wi = w[i];
-#pragma unroll
-        for (int k = 0; k < MAXV; ++k)
-          if (k < cnt) acc[k] += V[(size_t)(k0 + k) * ld + i] * wi;
-      }
-#pragma unroll
-      for (int k = 0; k < MAXV; ++k) {
-        double v = acc[k];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[k][warp] = v;
-      }
-      __syncthreads();
-      if ((int)threadIdx.x < cnt) {
-        double v = 0.0;
-        for (int wv = 0; wv < DOT_TPB / 32; ++wv) v += sh[threadIdx.x][wv];
-        partial[(size_t)ci * ldp + k0 + threadIdx.x] = v;
-      }
-      __syncthreads();
+    if (active && !active[C.x]) continue;  // uniform across the warp
+    const double* __restrict__ vk = V + (size_t)k * ld;
+    double a0 = 0.0, a1 = 0.0;
+    int i = C.y + lane;
+    for (; i + 32 < C.z; i += 64) {
+      a0 += vk[i] * w[i];
+      a1 += vk[i + 32] * w[i + 32];
     }
+    if (i < C.z) a0 += vk[i] * w[i];
+    double v = a0 + a1;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) partial[(size_t)ci * ldp + k] = v;
   }
+  // every writer makes its partials visible device-wide, and the whole block has done
+  // so, before the block takes its ticket
   __threadfence();
+  __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
   __syncthreads();
   if (!last) return;
-  for (int t = threadIdx.x; t < nsys * nv; t += DOT_TPB) {
+  // one warp per (system, vector): lanes take every 32nd chunk, then a fixed shuffle tree
+  for (int t = warp; t < nsys * nv; t += DOT_TPB / 32) {
     const int sy = t / nv, k = t - sy * nv;
     if (active && !active[sy]) continue;
     double v = 0.0;
-    for (int ci = chunk_ptr[sy]; ci < chunk_ptr[sy + 1]; ++ci) v += __ldcg(partial + (size_t)ci * ldp + k);
-    double* o = out + (size_t)sy * ldo + k;
-    *o = accumulate ? *o + v : v;
+    for (int ci = chunk_ptr[sy] + lane; ci < chunk_ptr[sy + 1]; ci += 32) v += __ldcg(partial + (size_t)ci * ldp + k);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) {
+      double* o = out + (size_t)sy * ldo + k;
+      *o = accumulate ? *o + v : v;
+    }
   }
   if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -224,7 +220,9 @@ struct Work {
 
 void multidot(Ctx& c, const Work& w, const double* V, int nv, const double* vec, double* out, const int* active,
               cudaStream_t s) {
-  launch(multidot_kernel, std::min(c.nchunk, 1024), DOT_TPB, 0, s, V, w.ld, nv, vec, c.chunks.p, c.nchunk,
+  const long long items = (long long)c.nchunk * nv;
+  const int blocks = (int)std::min<long long>(2048, std::max<long long>(1, (items + DOT_TPB / 32 - 1) / (DOT_TPB / 32)));
+  launch(multidot_kernel, blocks, DOT_TPB, 0, s, V, w.ld, nv, vec, c.chunks.p, c.nchunk,
          c.chunk_ptr.p, c.nsys, active, w.partial, w.ldp, w.ticket, out, w.lds, 0);
 }
 

@@ -139,8 +139,11 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
                                                  const int* __restrict__ active, const int* __restrict__ leaf_sys,
                                                  double* __restrict__ out) {
   constexpr int NC = MI<P>::NC;
-  __shared__ Real sm[FCH][2 * NC];
-  __shared__ Real so[FCH][3];
+  // two buffers of staged cells: the next batch's moments are loaded while the current
+  // batch is evaluated (one barrier per batch; FP64 batches are smaller to fit)
+  constexpr int FB = sizeof(Real) == 4 ? FCH : FCH / 4;
+  __shared__ Real sm[2][FB][2 * NC];
+  __shared__ Real so[2][FB][3];
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
   if (active && !active[leaf_sys[leaf]]) return;
@@ -156,25 +159,31 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
   }
   double aV = 0, aK = 0;
   const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
-  for (int fb = f0; fb < f1; fb += FCH) {
-    const int cnt = min(FCH, f1 - fb);
+  auto stage = [&](int b, int fb) {
+    const int cnt = min(FB, f1 - fb);
     for (int q = threadIdx.x; q < cnt * 2 * NC; q += TBT)
-      sm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+      sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
     if ((int)threadIdx.x < cnt) {
       double4 cc = center[far_list[fb + threadIdx.x]];
-      so[threadIdx.x][0] = (Real)(ct.x - cc.x);
-      so[threadIdx.x][1] = (Real)(ct.y - cc.y);
-      so[threadIdx.x][2] = (Real)(ct.z - cc.z);
+      so[b][threadIdx.x][0] = (Real)(ct.x - cc.x);
+      so[b][threadIdx.x][1] = (Real)(ct.y - cc.y);
+      so[b][threadIdx.x][2] = (Real)(ct.z - cc.z);
     }
-    __syncthreads();
+  };
+  if (f0 < f1) stage(0, f0);
+  __syncthreads();
+  int b = 0;
+  for (int fb = f0; fb < f1; fb += FB, b ^= 1) {
+    const int cnt = min(FB, f1 - fb);
+    if (fb + FB < f1) stage(b ^ 1, fb + FB);  // buffer b ^ 1 was last read before the previous barrier
     Real v = 0, k = 0;
     if ((int)(threadIdx.x & ~31u) < B.z) {  // warp holds at least one target
       for (int q = 0; q < cnt; ++q) {
-        const Real D[3] = {xr[0] + so[q][0], xr[1] + so[q][1], xr[2] + so[q][2]};
+        const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
         if (YUK)
-          far_eval_yukawa<P, Real>(D, sm[q], sm[q] + NC, kappa, v, k);
+          far_eval_yukawa<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
         else
-          far_eval_laplace<P, Real>(D, sm[q], sm[q] + NC, v, k);
+          far_eval_laplace<P, Real>(D, sm[b][q], sm[b][q] + NC, v, k);
       }
     }
     aV += (double)v;
@@ -282,6 +291,9 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
     }
     __syncthreads();
     const int total = lc[cnt];
+    // per-pair sums in Real over up to four tiles (128 sources), then into FP64
+    Real vl = 0, kl = 0, vy = 0, ky = 0;
+    int ntile = 0;
     for (int t0 = 0; t0 < total; t0 += NTB) {
       const int j = t0 + threadIdx.x;
       R4 pz, sz;
@@ -315,7 +327,6 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
       sp[threadIdx.x] = pz;
       ss[threadIdx.x] = sz;
       __syncthreads();
-      Real vl = 0, kl = 0, vy = 0, ky = 0;
       if (t0 + NTB <= total) {
 #pragma unroll 8
         for (int k = 0; k < NTB; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
@@ -323,12 +334,20 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
         const int lim = total - t0;
         for (int k = 0; k < lim; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
       }
-      acc[0] += (double)vl;
-      acc[1] += (double)kl;
-      acc[2] += (double)vy;
-      acc[3] += (double)ky;
+      if (++ntile == 4) {
+        acc[0] += (double)vl;
+        acc[1] += (double)kl;
+        acc[2] += (double)vy;
+        acc[3] += (double)ky;
+        vl = kl = vy = ky = 0;
+        ntile = 0;
+      }
       __syncthreads();
     }
+    acc[0] += (double)vl;
+    acc[1] += (double)kl;
+    acc[2] += (double)vy;
+    acc[3] += (double)ky;
   }
   if (act) {
     double* o = out + (size_t)blockIdx.y * 4 * n;
@@ -522,11 +541,11 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str32.p);
   else
     str = reinterpret_cast<const R4*>(c.str64.p);
-  launch(leaf_moments_kernel<P, Real>, T.nleaf, TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
+  launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
          c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
   for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
-    launch(m2m_kernel<P, Real>, cnt, TB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
+    launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
   const int S = T.near_splits;
   const size_t need = (size_t)(S + 1) * 4 * c.n;

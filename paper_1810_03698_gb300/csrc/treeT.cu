@@ -359,11 +359,11 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   launch(centroid_charges_kernel<R4>, cdiv(c.n, 256), 256, 0, s, u, c.n, sL.p, sY.p);
   for (int w = 0; w < 2; ++w) {
     DBuf<Real>& m = w ? mY : mL;
-    launch(leaf_moments_kernel<P, Real>, T.nleaf, TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
+    launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
            c.tgt64.p, (const R4*)(w ? sY.p : sL.p), c.mv_active, T.leaf_sys.p, m.p);
     for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {
       const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
-      launch(m2m_kernel<P, Real>, cnt, TB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, m.p);
+      launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, m.p);
     }
   }
   const int S = T.near_splits;
@@ -391,11 +391,11 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   BP_CUDA(cudaStreamSynchronize(s));  // the strength buffers are released on return
 }
 
-// The transposed far field runs in FP32 at order 5 whatever the forward order: the
-// adjoint needs A^T to about the forward treecode's accuracy (orders 1-5 are matched
-// or exceeded; order 6 is approximated at 5), and one compiled order keeps the
-// build short (the order-P transposed kernel carries coefficients to order P + 1).
-void dispatchT(Ctx& c, const double* u, cudaStream_t s) { runT_tree<5, float>(c, u, s); }
+// The transposed far field runs in FP32 at order 4 whatever the forward order: the
+// adjoint needs A^T only to about the accuracy of the forward treecode (theta^(P+1)
+// bounds both), the order-P transposed kernel carries coefficients to order P + 1 at
+// four Gauss nodes per panel, and one compiled order keeps the build short.
+void dispatchT(Ctx& c, const double* u, cudaStream_t s) { runT_tree<4, float>(c, u, s); }
 
 }  // namespace
 

@@ -173,53 +173,65 @@ __global__ void src_rel_kernel(const int* __restrict__ leaf_cell, int nleaf, con
 }
 
 // ---------------------------------------------------------------- moments
-// Leaf moments from the sources: one block per leaf, thread o owns moments o, o + TB, ...
+// Leaf moments from the sources: one block of LMG groups x TB threads per leaf.  A tile
+// of TB sources is staged (powers of the offsets, strengths); group g sums sources
+// [g TB/LMG, (g+1) TB/LMG) of every tile for the moments o, o + TB, ... of its thread;
+// the groups' partial moments are then added in group order.
+constexpr int LMG = 4;
 template <int P, typename Real>
-__global__ void __launch_bounds__(TB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
-                                                          const int* __restrict__ begin, const int* __restrict__ end,
-                                                          const double4* __restrict__ center, int K,
-                                                          const double4* __restrict__ src64,
-                                                          const typename Vec4<Real>::T* __restrict__ str,
-                                                          const int* __restrict__ active,
-                                                          const int* __restrict__ leaf_sys, Real* __restrict__ mom) {
+__global__ void __launch_bounds__(LMG * TB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
+                                                                const int* __restrict__ begin,
+                                                                const int* __restrict__ end,
+                                                                const double4* __restrict__ center, int K,
+                                                                const double4* __restrict__ src64,
+                                                                const typename Vec4<Real>::T* __restrict__ str,
+                                                                const int* __restrict__ active,
+                                                                const int* __restrict__ leaf_sys,
+                                                                Real* __restrict__ mom) {
   const MI<P>& mi = c_mi<P>;
   constexpr int NC = MI<P>::NC;
+  constexpr int NU = (2 * NC + TB - 1) / TB;
   __shared__ Real pw[TB][3][P + 1];
   __shared__ Real sd[TB][4];
+  __shared__ Real red[LMG][2 * NC];
   if (active && !active[leaf_sys[blockIdx.x]]) return;  // system not being solved
   const int cidx = leaf_cell[blockIdx.x];
   const double4 c = center[cidx];
   const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
-  Real acc[(2 * NC + TB - 1) / TB];
-  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) acc[u] = 0;
+  const int grp = threadIdx.x / TB, tl = threadIdx.x % TB;
+  Real acc[NU];
+  for (int u = 0; u < NU; ++u) acc[u] = 0;
   for (int t0 = s0; t0 < s1; t0 += TB) {
-    int j = t0 + threadIdx.x;
-    if (j < s1) {
-      double4 y = src64[j];
-      Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
-      for (int d = 0; d < 3; ++d) {
-        Real p = 1;
-        for (int e = 0; e <= P; ++e) {
-          pw[threadIdx.x][d][e] = p;
-          p *= h[d];
+    if (threadIdx.x < TB) {
+      const int j = t0 + threadIdx.x;
+      if (j < s1) {
+        double4 y = src64[j];
+        Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
+        for (int d = 0; d < 3; ++d) {
+          Real p = 1;
+          for (int e = 0; e <= P; ++e) {
+            pw[threadIdx.x][d][e] = p;
+            p *= h[d];
+          }
         }
+        auto sv = str[j];
+        sd[threadIdx.x][0] = sv.x;
+        sd[threadIdx.x][1] = sv.y;
+        sd[threadIdx.x][2] = sv.z;
+        sd[threadIdx.x][3] = sv.w;
       }
-      auto s = str[j];
-      sd[threadIdx.x][0] = s.x;
-      sd[threadIdx.x][1] = s.y;
-      sd[threadIdx.x][2] = s.z;
-      sd[threadIdx.x][3] = s.w;
     }
     __syncthreads();
     const int lim = min(TB, s1 - t0);
-    for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
-      const int o = threadIdx.x + u * TB;
+    const int q0 = grp * (TB / LMG), q1 = min(lim, q0 + TB / LMG);
+    for (int u = 0; u < NU; ++u) {
+      const int o = tl + u * TB;
       if (o >= 2 * NC) break;
       const bool dbl = o >= NC;
       const int t = dbl ? o - NC : o;
       const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
       Real a = 0;
-      for (int q = 0; q < lim; ++q) {
+      for (int q = q0; q < q1; ++q) {
         if (!dbl) {
           a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
         } else {
@@ -234,21 +246,31 @@ __global__ void __launch_bounds__(TB) leaf_moments_kernel(const int* __restrict_
     }
     __syncthreads();
   }
-  for (int u = 0; u < (2 * NC + TB - 1) / TB; ++u) {
-    const int o = threadIdx.x + u * TB;
-    if (o < 2 * NC) mom[(size_t)cidx * 2 * NC + o] = acc[u];
+  for (int u = 0; u < NU; ++u) {
+    const int o = tl + u * TB;
+    if (o < 2 * NC) red[grp][o] = acc[u];
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 2 * NC; o += LMG * TB) {
+    Real v = 0;
+    for (int g = 0; g < LMG; ++g) v += red[g][o];
+    mom[(size_t)cidx * 2 * NC + o] = v;
   }
 }
 
-// Parent moments by shifting the children's: one block per parent cell of one depth.
+// Parent moments by shifting the children's: one block per parent cell of one depth,
+// one thread per (moment, child) shift; the children's shifted moments are then
+// added in child order.
+constexpr int M2M_TPB = 256;
 template <int P, typename Real>
-__global__ void __launch_bounds__(TB) m2m_kernel(int first_cell, const int* __restrict__ child0,
-                                                 const int* __restrict__ nchild, const double4* __restrict__ center,
-                                                 Real* __restrict__ mom) {
+__global__ void __launch_bounds__(M2M_TPB) m2m_kernel(int first_cell, const int* __restrict__ child0,
+                                                      const int* __restrict__ nchild,
+                                                      const double4* __restrict__ center, Real* __restrict__ mom) {
   const MI<P>& mi = c_mi<P>;
   constexpr int NC = MI<P>::NC;
   __shared__ Real dp[8][3][P + 1];
   __shared__ Real cm[8][2 * NC];
+  __shared__ Real red[8][2 * NC];
   const int pc = first_cell + blockIdx.x;
   const int nch = nchild[pc];
   if (nch == 0) return;  // leaf (uniform across the block)
@@ -265,27 +287,34 @@ __global__ void __launch_bounds__(TB) m2m_kernel(int first_cell, const int* __re
       }
     }
   }
-  for (int q = threadIdx.x; q < nch * 2 * NC; q += TB) cm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)(c0 + q / (2 * NC)) * 2 * NC + q % (2 * NC)];
+  for (int q = threadIdx.x; q < nch * 2 * NC; q += M2M_TPB)
+    cm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)(c0 + q / (2 * NC)) * 2 * NC + q % (2 * NC)];
   __syncthreads();
   const auto& binom = c_binom.b;
-  for (int o = threadIdx.x; o < 2 * NC; o += TB) {
+  for (int w = threadIdx.x; w < nch * 2 * NC; w += M2M_TPB) {
+    const int ch = w / (2 * NC), o = w - ch * 2 * NC;
     const int t = o < NC ? o : o - NC;
     const int off = o < NC ? 0 : NC;
     const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
     Real a = 0;
-    for (int ch = 0; ch < nch; ++ch)
-      for (int lx = 0; lx <= kx; ++lx)
-        for (int ly = 0; ly <= ky; ++ly)
-          for (int lz = 0; lz <= kz; ++lz) {
-            const int l = mi.idx[lx][ly][lz];
-            a += (Real)(binom[kx][lx] * binom[ky][ly] * binom[kz][lz]) * dp[ch][0][kx - lx] * dp[ch][1][ky - ly] *
-                 dp[ch][2][kz - lz] * cm[ch][off + l];
-          }
+    for (int lx = 0; lx <= kx; ++lx)
+      for (int ly = 0; ly <= ky; ++ly)
+        for (int lz = 0; lz <= kz; ++lz) {
+          const int l = mi.idx[lx][ly][lz];
+          a += (Real)(binom[kx][lx] * binom[ky][ly] * binom[kz][lz]) * dp[ch][0][kx - lx] * dp[ch][1][ky - ly] *
+               dp[ch][2][kz - lz] * cm[ch][off + l];
+        }
+    red[ch][o] = a;
+  }
+  __syncthreads();
+  for (int o = threadIdx.x; o < 2 * NC; o += M2M_TPB) {
+    Real a = 0;
+    for (int ch = 0; ch < nch; ++ch) a += red[ch][o];
     mom[(size_t)pc * 2 * NC + o] = a;
   }
 }
 
-constexpr int FCH = 8;   // far cells staged in shared memory per pass
+constexpr int FCH = 32;  // far cells staged in shared memory per pass (fewer barriers)
 constexpr int NTB = 32;  // targets (one warp) per near-field block
 
 }  // namespace

@@ -73,7 +73,7 @@ def _sample(pr):
 
 @pytest.mark.parametrize("theta,bar", [(1e-3, 2e-5), (0.5, 5e-4)])
 def test_transposed_tree(bp, theta, bar):
-    """FP32 treecode A^T u (order 5): theta -> 0 reduces it to the FP32 direct sum; at
+    """FP32 treecode A^T u (order 4): theta -> 0 reduces it to the FP32 direct sum; at
     theta = 0.5 it is within the forward treecode's bar of the dense A^T u."""
     pr = gen.small_bumpy(3, 8, 8.0, seed_index=108)
     par = pr.params
@@ -128,6 +128,26 @@ def test_moment_gradient_tree(bp, prob, oracle_grad):
     idx = _sample(pr)
     for k in ("q", "d", "Q", "pos"):
         assert _relmax(g[k][idx], oracle_grad[k]) < 1e-6, k
+
+
+def test_autograd_function(bp, prob, oracle_grad):
+    """torch.autograd through solvation_energy: backward = the adjoint gradient in kcal/mol."""
+    _, pr = prob
+    if pr.panel_body is not None:
+        pytest.skip("single-body problems only (the helper sets sites without bodies)")
+    s = bp.problem_solver(pr)
+    st = pr.sites
+    dev = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda").requires_grad_(True)
+    pos, q, d, Q = dev(st.pos), dev(st.q), dev(st.d), dev(st.Q)
+    alpha = torch.as_tensor(st.alpha, dtype=torch.float64, device="cuda")
+    group = torch.as_tensor(st.group, dtype=torch.int32, device="cuda")
+    G = bp.solvation_energy(s, pos, q, d, Q, alpha, group)
+    G.backward()
+    assert G.item() == pytest.approx(oracle_grad["dG"] * bp.KCAL_PER_UNIT, rel=1e-10)
+    idx = _sample(pr)
+    for k, t in (("pos", pos), ("q", q), ("d", d), ("Q", Q)):
+        got = t.grad.cpu().numpy()[idx] / bp.KCAL_PER_UNIT
+        assert _relmax(got, oracle_grad[k]) < 1e-8, k
 
 
 def test_gradient_needs_a_solve(bp):

@@ -107,3 +107,20 @@ def test_fp32_tree_with_fp64_tree_refinement(bp):
     b = s64.solve()
     # refinement converges to the FP64 tree operator's solution
     assert abs(a["dG_solv_kcal"] - b["dG_solv_kcal"]) < 1e-8 * abs(b["dG_solv_kcal"])
+
+
+def test_autotune_meets_its_target(bp):
+    """The autotuner's choice reproduces the direct product within the target."""
+    pr = gen.small_bumpy(4, 10, 8.0, seed_index=109)
+    s = bp.problem_solver(pr)
+    r = s.autotune(target_err=1e-4)
+    assert r["candidates"] == 36 and 0 <= r["rel_err"] <= 1e-4
+    assert (s.params.leaf, s.params.theta, s.params.order) == (r["leaf"], r["theta"], r["order"])
+    n = pr.n_panels
+    x = torch.as_tensor(np.random.default_rng(33).normal(size=2 * n), dtype=torch.float64, device="cuda")
+    y = torch.zeros_like(x)
+    yd = torch.zeros_like(x)
+    s.matvec(x, y, op="fp32_tree")
+    s.matvec(x, yd, op="fp64_direct")
+    err = float(torch.linalg.norm(y - yd) / torch.linalg.norm(yd))
+    assert err < 1e-4 + 1e-5   # the target plus the FP32 direct product's own rounding
