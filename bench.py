@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--workload", default="solvation", choices=["solvation", "binding", "gradient"])
     ap.add_argument("--grad-config", type=int, default=5, choices=[3, 5])
     ap.add_argument("--triples", type=int, default=16)
+    ap.add_argument("--autotune", type=float, default=0.0,
+                    help="pick leaf/theta/order with bempol_autotune at this error target first (0 = off)")
     return ap.parse_args()
 
 
@@ -139,6 +141,23 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------- helpers
+def job_time_ms(local_ms, dist=None, device="cpu"):
+    """Whole-job time: the largest of the ranks' timed-region durations (one replica per
+    rank, no collective in the data path; this max-reduction is only for timing)."""
+    if dist is None:
+        return float(local_ms)
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def seconds_per_unit(total_ms, steps, world):
+    """Every rank solves `steps` independent problems in the timed region: the job
+    completes steps * world of them in the (max-over-ranks) time."""
+    return total_ms / 1e3 / (steps * world)
+
+
 def build_library():
     import importlib.util
     spec = importlib.util.spec_from_file_location("bempol_build", os.path.join(ROOT, "paper_1810_03698_gb300",
@@ -221,6 +240,7 @@ def run_binding(args, local):
     kw = dict(op=args.op, residual_op=res_op)
     stream = torch.cuda.current_stream()
     s = bp.batch_solver(probs, device=local, **kw)
+    tuned = s.autotune(args.autotune) if args.autotune > 0 else None
 
     def ev_time(fn):
         a = torch.cuda.Event(enable_timing=True)
@@ -264,7 +284,7 @@ def run_binding(args, local):
         "config": {"workload": f"binding_{len(triples)}_triples", "systems": len(probs),
                    "panels": int(sum(p.n_panels for p in probs)), "sites": int(sum(p.sites.n for p in probs)),
                    "op": args.op, "residual_op": res_op, "gmres_tol": probs[0].params.gmres_tol,
-                   "scf_tol": probs[0].params.scf_tol},
+                   "scf_tol": probs[0].params.scf_tol, "autotuned": tuned},
         "sequential_s": seq_ms / 1e3, "batch_speedup": seq_ms / 1e3 / value,
         "ddG_bind_kcal": ddg, "lockstep_gmres_iters": r["gmres_iters_total"], "matvecs": r["matvecs_total"],
         "converged": all(x["converged"] for x in sy), "gpu_launches": int(stats["kernel_launches"]),
@@ -377,6 +397,11 @@ def main():
         s.set_sites(*d_site, group=d_group)
         return s.solve()
 
+    tuned = None
+    if args.autotune > 0:
+        s.set_mesh(d_verts, d_tris)
+        tuned = s.autotune(args.autotune)
+
     for _ in range(args.warmup):
         out = step()
     s.stats_enable(True)
@@ -406,12 +431,8 @@ def main():
     wall = time.time() - t_wall0
     clocks = sampler.stop()
     stats = s.stats(reset=True)
-    total_ms = float(np.sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = total_ms / 1e3 / (args.steps * world)
+    total_ms = job_time_ms(float(np.sum(step_ms)), dist, dev)
+    value = seconds_per_unit(total_ms, args.steps, world)
     out = outs[-1]
 
     # ---- one more step split into its phases (not part of the timed value)
@@ -518,7 +539,8 @@ def main():
         "config": {"workload": pr.name, "panels": n, "gauss_k": K, "sites": st.n, "op": args.op,
                    "residual_op": res_op, "theta": pr.params.theta, "order": pr.params.order,
                    "gmres_tol": pr.params.gmres_tol, "scf_tol": pr.params.scf_tol,
-                   "l2": "flushed (512 MiB write) between timed steps, flush not timed"},
+                   "l2": "flushed (512 MiB write) between timed steps, flush not timed",
+                   "autotuned": tuned},
         "solve": {"dG_solv_kcal": out["dG_solv_kcal"], "scf_iters_diss": out["scf_iters_diss"],
                   "scf_iters_vac": out["scf_iters_vac"], "gmres_iters": out["gmres_iters_total"],
                   "matvecs": out["matvecs_total"], "bem_solves": out["n_solves"],

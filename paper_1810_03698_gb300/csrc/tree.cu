@@ -294,20 +294,14 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
     // per-pair sums in Real over up to four tiles (128 sources), then into FP64
     Real vl = 0, kl = 0, vy = 0, ky = 0;
     int ntile = 0;
+    int lo = 0;  // leaf of this lane's source: largest q with lc[q] <= j (j only grows)
     for (int t0 = 0; t0 < total; t0 += NTB) {
       const int j = t0 + threadIdx.x;
       R4 pz, sz;
       pz.x = pz.y = pz.z = pz.w = 0;
       sz = pz;
       if (j < total) {
-        int lo = 0, hi = cnt - 1;  // largest q with lc[q] <= j
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (lc[mid] <= j)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
+        while (lc[lo + 1] <= j) ++lo;
         const int src = lb[lo] + (j - lc[lo]);
         if constexpr (sizeof(Real) == 4) {
           // leaf-relative FP32 position plus the leaf-pair offset: no FP64 work per source

@@ -237,20 +237,14 @@ __global__ void __launch_bounds__(NTB) nearT_kernel(const int4* __restrict__ blk
     }
     __syncthreads();
     const int total = lc[cnt];
+    int lo = 0;  // leaf of this lane's source (j only grows)
     for (int t0 = 0; t0 < total; t0 += NTB) {
       const int j = t0 + threadIdx.x;
       R4 pz;
       pz.x = pz.y = pz.z = pz.w = 0;
       Real a1 = 0;
       if (j < total) {
-        int lo = 0, hi = cnt - 1;
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (lc[mid] <= j)
-            lo = mid;
-          else
-            hi = mid - 1;
-        }
+        while (lc[lo + 1] <= j) ++lo;
         const int src = lb[lo] + (j - lc[lo]);
         if constexpr (sizeof(Real) == 4) {
           const float4 r = cen_rel[src];
