@@ -810,10 +810,10 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   zero3.zero(s);
   // forward quantities at the solution: reaction fields (FP64) and energy-form multipole potentials
   site_reaction_internal(c, c.sol_x.p, F_s.p, f32, true, s);
-  multipole_internal(c, c.sol_mu.p, 1, P_mu.p, s);
-  multipole_internal(c, zero3.p, 1, P_0.p, s);
-  multipole_internal(c, c.sol_mu_v.p, 3, Pv_mu.p, s);
-  multipole_internal(c, zero3.p, 3, Pv_0.p, s);
+  multipole_internal(c, c.sol_mu.p, 1, P_mu.p, s, f32);
+  multipole_internal(c, zero3.p, 1, P_0.p, s, f32);
+  multipole_internal(c, c.sol_mu_v.p, 3, Pv_mu.p, s, f32);
+  multipole_internal(c, zero3.p, 3, Pv_0.p, s, f32);
   // c_mu = -1/2 (damped unmasked field of the permanent moments), dissolved (body) and vacuum (system)
   launch(site_adjoint_kernel, cdiv(ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, zero3.p,
          c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, ns, 0, 0, P.thole_a, -0.5 * scale, cmu.p);
@@ -865,7 +865,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
     for (int it = 1; it <= P.scf_maxit; ++it) {
       for (int q = 0; q < S; ++q) want[q] = (char)act[q];
       adj_bem(want);
-      multipole_internal(c, nu.p, 0 | 4, tn.p, s);  // T nu~: damped field of the dipoles nu~ alone
+      multipole_internal(c, nu.p, 0 | 4, tn.p, s, f32);  // T nu~: damped field of the dipoles nu~ alone
       upload_act(act);
       launch(adj_sor_kernel, S, 256, 0, s, nu.p, c.site_pos.p, cmu.p, psi.p, tn.p, c.sys_site.p, d_act.p,
              P.sor_omega, c.scal.p);
@@ -891,7 +891,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   {
     std::vector<int> act(S, 1);
     for (int it = 1; it <= P.scf_maxit; ++it) {
-      multipole_internal(c, nuv.p, 2 | 4, tn.p, s);
+      multipole_internal(c, nuv.p, 2 | 4, tn.p, s, f32);
       upload_act(act);
       launch(adj_sor_kernel, S, 256, 0, s, nuv.p, c.site_pos.p, cmuv.p, (const double*)nullptr, tn.p, c.sys_site.p,
              d_act.p, P.sor_omega, c.scal.p);

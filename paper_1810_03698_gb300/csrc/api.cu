@@ -771,7 +771,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
       std::vector<Guard> gv(S);
       for (int it = 1; it <= P.scf_maxit; ++it) {
         upload_act(act);
-        multipole_internal(*c, mu_v.p, 2, emult.p, s);
+        multipole_internal(*c, mu_v.p, 2, emult.p, s, f32);
         std::vector<double> rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, d_act.p, s);
         int left = 0;
         for (int q = 0; q < S; ++q) {
@@ -815,7 +815,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
         for (int q = 0; q < S; ++q) want[q] = (char)act[q];
         bem(want);
         site_reaction_internal(*c, x.p, react.p, f32, false, s);
-        multipole_internal(*c, mu.p, 0, emult.p, s);
+        multipole_internal(*c, mu.p, 0, emult.p, s, f32);
         upload_act(act);
         std::vector<double> rms = sor_update(*c, mu.p, react.p, emult.p, false, d_act.p, s);
         int left = 0;
@@ -838,9 +838,9 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     std::fill(want.begin(), want.end(), 1);
     bem(want);
     site_reaction_internal(*c, x.p, react.p, f32, true, s);
-    multipole_internal(*c, mu.p, 1, mult10.p, s);
+    multipole_internal(*c, mu.p, 1, mult10.p, s, f32);
     std::vector<double> Gd = energy_internal(*c, react.p, mult10.p, s);
-    multipole_internal(*c, mu_v.p, 3, mult10.p, s);
+    multipole_internal(*c, mu_v.p, 3, mult10.p, s, f32);
     std::vector<double> Gv = energy_internal(*c, nullptr, mult10.p, s);
     double t_scf = ts.ms();
     bool ok = true;

@@ -182,6 +182,7 @@ __global__ void site_reduce_kernel(const double* __restrict__ part, int S, int n
 // cavity holds its own multipoles), modes 2 and 3 are the same over every site of
 // its system (vacuum state).  Adding 4 to the mode drops the permanent moments
 // (the damped field of the dipoles `mu` alone).
+template <typename Real>
 __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restrict__ pos, const double* __restrict__ q,
                                                         const double* __restrict__ d, const double* __restrict__ Q,
                                                         const double* __restrict__ mu, const int* __restrict__ group,
@@ -201,67 +202,78 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
   const int m0 = whole ? sys_site[grp_sys[tg]] : gsite[tg];
   const int m1 = whole ? sys_site[grp_sys[tg] + 1] : gsite[tg + 1];
   mode &= 1;
+  const Real ta = (Real)thole_a;
+  // pair terms in Real, summed per lane in Real over up to 32 pairs, then into FP64
   double acc[10];
-  for (int c = 0; c < 10; ++c) acc[c] = 0.0;
+  Real part[10];
+  for (int c = 0; c < 10; ++c) acc[c] = 0.0, part[c] = 0;
+  int npart = 0;
   for (int m = m0 + lane; m < m1; m += 32) {
     if (m == l) continue;
     double4 pm = pos[m];
-    double Rx = pl.x - pm.x, Ry = pl.y - pm.y, Rz = pl.z - pm.z;
-    double r2 = Rx * Rx + Ry * Ry + Rz * Rz;
-    double rinv = 1.0 / sqrt(r2);
-    double i2 = rinv * rinv, i3 = i2 * rinv, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
-    double R[3] = {Rx, Ry, Rz};
-    double g[3] = {0, 0, 0}, H[6] = {0, 0, 0, 0, 0, 0}, P = 0;
+    const Real Rx = (Real)(pl.x - pm.x), Ry = (Real)(pl.y - pm.y), Rz = (Real)(pl.z - pm.z);
+    const Real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
+    const Real rinv = (Real)1 / sqrt(r2);
+    const Real i2 = rinv * rinv, i3 = i2 * rinv, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
+    const Real R[3] = {Rx, Ry, Rz};
+    Real g[3] = {0, 0, 0}, H[6] = {0, 0, 0, 0, 0, 0}, P = 0;
     bool perm = !ind_only && ((mode == 1) || (group[m] != gl));
     if (perm) {
-      double qm = q[m];
-      double pv[3] = {d[3 * m], d[3 * m + 1], d[3 * m + 2]};
+      const Real qm = (Real)q[m];
+      const Real pv[3] = {(Real)d[3 * m], (Real)d[3 * m + 1], (Real)d[3 * m + 2]};
       const double* Qm = Q + 6 * m;
-      double QM[3][3] = {{Qm[0], Qm[1], Qm[2]}, {Qm[1], Qm[3], Qm[4]}, {Qm[2], Qm[4], Qm[5]}};
-      double QR[3];
+      const Real QM[3][3] = {{(Real)Qm[0], (Real)Qm[1], (Real)Qm[2]},
+                             {(Real)Qm[1], (Real)Qm[3], (Real)Qm[4]},
+                             {(Real)Qm[2], (Real)Qm[4], (Real)Qm[5]}};
+      Real QR[3];
       for (int a = 0; a < 3; ++a) QR[a] = QM[a][0] * Rx + QM[a][1] * Ry + QM[a][2] * Rz;
-      double RQR = QR[0] * Rx + QR[1] * Ry + QR[2] * Rz;
-      double pR = pv[0] * Rx + pv[1] * Ry + pv[2] * Rz;
-      P = qm * rinv + pR * i3 + 0.5 * RQR * i5;
+      const Real RQR = QR[0] * Rx + QR[1] * Ry + QR[2] * Rz;
+      const Real pR = pv[0] * Rx + pv[1] * Ry + pv[2] * Rz;
+      P = qm * rinv + pR * i3 + (Real)0.5 * RQR * i5;
       for (int a = 0; a < 3; ++a)
-        g[a] = -qm * R[a] * i3 + pv[a] * i3 - 3.0 * pR * R[a] * i5 + QR[a] * i5 - 2.5 * RQR * R[a] * i7;
+        g[a] = -qm * R[a] * i3 + pv[a] * i3 - (Real)3 * pR * R[a] * i5 + QR[a] * i5 - (Real)2.5 * RQR * R[a] * i7;
       if (mode == 1) {
         int k = 0;
         for (int a = 0; a < 3; ++a)
           for (int b = a; b < 3; ++b, ++k) {
-            double dab = a == b ? 1.0 : 0.0;
-            H[k] = qm * (3.0 * R[a] * R[b] * i5 - dab * i3) + 15.0 * pR * R[a] * R[b] * i7 -
-                   3.0 * (pR * dab + pv[a] * R[b] + pv[b] * R[a]) * i5 + 17.5 * RQR * R[a] * R[b] * i9 -
-                   2.5 * (RQR * dab + 2.0 * QR[a] * R[b] + 2.0 * QR[b] * R[a]) * i7 + QM[a][b] * i5;
+            const Real dab = a == b ? (Real)1 : (Real)0;
+            H[k] = qm * ((Real)3 * R[a] * R[b] * i5 - dab * i3) + (Real)15 * pR * R[a] * R[b] * i7 -
+                   (Real)3 * (pR * dab + pv[a] * R[b] + pv[b] * R[a]) * i5 + (Real)17.5 * RQR * R[a] * R[b] * i9 -
+                   (Real)2.5 * (RQR * dab + (Real)2 * QR[a] * R[b] + (Real)2 * QR[b] * R[a]) * i7 + QM[a][b] * i5;
           }
       }
     }
     // induced dipole, Thole damped
-    double mv[3] = {mu[3 * m], mu[3 * m + 1], mu[3 * m + 2]};
-    double aa = pl.w * pm.w;
-    double l3 = 1.0, l5 = 1.0, l7 = 1.0;
+    const Real mv[3] = {(Real)mu[3 * m], (Real)mu[3 * m + 1], (Real)mu[3 * m + 2]};
+    const double aa = pl.w * pm.w;
+    Real l3 = 1, l5 = 1, l7 = 1;
     if (aa > 0.0) {
-      double au3 = thole_a * r2 * sqrt(r2) / sqrt(aa);
-      double e = exp(-au3);
-      l3 = 1.0 - e;
-      l5 = 1.0 - (1.0 + au3) * e;
-      l7 = 1.0 - (1.0 + au3 + 0.6 * au3 * au3) * e;
+      const Real au3 = ta * r2 * sqrt(r2) / (Real)sqrt(aa);
+      const Real e = exp(-au3);
+      l3 = (Real)1 - e;
+      l5 = (Real)1 - ((Real)1 + au3) * e;
+      l7 = (Real)1 - ((Real)1 + au3 + (Real)0.6 * au3 * au3) * e;
     }
-    double mR = mv[0] * Rx + mv[1] * Ry + mv[2] * Rz;
+    const Real mR = mv[0] * Rx + mv[1] * Ry + mv[2] * Rz;
     P += l3 * mR * i3;
-    for (int a = 0; a < 3; ++a) g[a] += l3 * mv[a] * i3 - 3.0 * l5 * mR * R[a] * i5;
+    for (int a = 0; a < 3; ++a) g[a] += l3 * mv[a] * i3 - (Real)3 * l5 * mR * R[a] * i5;
     if (mode == 1) {
       int k = 0;
       for (int a = 0; a < 3; ++a)
         for (int b = a; b < 3; ++b, ++k) {
-          double dab = a == b ? 1.0 : 0.0;
-          H[k] += 15.0 * l7 * mR * R[a] * R[b] * i7 - 3.0 * l5 * (mR * dab + mv[a] * R[b] + mv[b] * R[a]) * i5;
+          const Real dab = a == b ? (Real)1 : (Real)0;
+          H[k] += (Real)15 * l7 * mR * R[a] * R[b] * i7 - (Real)3 * l5 * (mR * dab + mv[a] * R[b] + mv[b] * R[a]) * i5;
         }
     }
-    acc[0] += P;
-    for (int a = 0; a < 3; ++a) acc[1 + a] += g[a];
-    for (int k = 0; k < 6; ++k) acc[4 + k] += H[k];
+    part[0] += P;
+    for (int a = 0; a < 3; ++a) part[1 + a] += g[a];
+    for (int k = 0; k < 6; ++k) part[4 + k] += H[k];
+    if (++npart == 32) {
+      for (int c = 0; c < 10; ++c) acc[c] += (double)part[c], part[c] = 0;
+      npart = 0;
+    }
   }
+  for (int c = 0; c < 10; ++c) acc[c] += (double)part[c];
   for (int c = 0; c < 10; ++c) {
     double v = acc[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -457,10 +469,15 @@ void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, boo
   BP_CHECK_LAUNCH();
 }
 
-void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s) {
-  launch(multipole_kernel, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
-         c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
-         INV4PI / c.par.eps_in, out);
+void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s, bool fp32) {
+  if (fp32)
+    launch(multipole_kernel<float>, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
+           c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
+           INV4PI / c.par.eps_in, out);
+  else
+    launch(multipole_kernel<double>, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
+           c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
+           INV4PI / c.par.eps_in, out);
   BP_CHECK_LAUNCH();
 }
 

@@ -169,7 +169,8 @@ def test_gradient_at_scale_copy(bp):
     s64 = bp.problem_solver(pr)
     r = s64.solve()
     g64 = s64.gradient()
-    s32 = bp.problem_solver(gen.with_params(pr, gmres_tol=1e-8, scf_tol=1e-8), op="fp32_tree",
+    # the FP32 treecode at the workload's tolerances (1e-6; the FP32 operator cannot reach 1e-8)
+    s32 = bp.problem_solver(gen.with_params(pr, gmres_tol=1e-6, scf_tol=1e-6), op="fp32_tree",
                             residual_op="fp32_tree", theta=0.5, order=5)
     s32.solve()
     g32 = s32.gradient()
