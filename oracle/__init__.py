@@ -13,14 +13,18 @@ panel      semi-analytical single/double-layer integrals over one flat triangle
 bem        dense BEM matrix (Eq. integral_eq), LU solve, sampled matvec rows
 multipole  multipole tensors, RHS (Eq. rhs_multipole), fields at sites, Thole
            damping, SCF (SOR) and its direct counterpart, energy (Eq.
-           energy_multipole_polarizable), solvation energy
+           energy_multipole_polarizable), solvation energy; several bodies in one
+           solvent (Sec. "Calculation of the binding energy")
 kirkwood   closed-form reaction field of a dielectric sphere in salt water
+gradient   dDelta G_solv / d(site positions, q, d, Q): five-point differences of
+           the solvation energy at the exact induced-dipole fixed point
 
 Parity pins (see tests/test_oracle_*.py): every function is checked against
 something other than itself -- closed forms (Born, Kirkwood, solid angles),
-Gauss's law, brute-force quadrature, finite differences, exact identities.
+Gauss's law, brute-force quadrature, finite differences, exact identities, the
+screened two-ion energy of two bodies, Euler's identity of the gradient.
 Parity unpinned: none of the functions here; the paper's own printed sphere
 value (-65.1131 kcal/mol) is not reproduced because it needs a Stern layer.
 """
 
-__all__ = ["geometry", "panel", "bem", "multipole", "kirkwood"]
+__all__ = ["geometry", "panel", "bem", "multipole", "kirkwood", "gradient"]

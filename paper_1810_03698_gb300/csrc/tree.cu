@@ -41,6 +41,14 @@ namespace bp {
 
 namespace {
 
+// asynchronous global -> shared copies of 16 bytes (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- far field
 // One (target, cell) interaction of one kernel: the Laplace coefficients a_k, or the
 // Yukawa a_k with their companions b_k, each dotted with the cell's single-layer (M)
@@ -139,10 +147,12 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
                                                  const int* __restrict__ active, const int* __restrict__ leaf_sys,
                                                  double* __restrict__ out) {
   constexpr int NC = MI<P>::NC;
-  // two buffers of staged cells: the next batch's moments are loaded while the current
-  // batch is evaluated (one barrier per batch; FP64 batches are smaller to fit)
+  // two buffers of staged cells: the next batch's moments are copied in (cp.async, 16-byte
+  // pieces, when a cell's moments are a whole number of them) while the current batch is
+  // evaluated; one barrier per batch.  FP64 batches are smaller to fit.
   constexpr int FB = sizeof(Real) == 4 ? FCH : FCH / 4;
-  __shared__ Real sm[2][FB][2 * NC];
+  constexpr bool ASYNC = (2 * NC * sizeof(Real)) % 16 == 0;
+  __shared__ __align__(16) Real sm[2][FB][2 * NC];
   __shared__ Real so[2][FB][3];
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
@@ -161,8 +171,18 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
   const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
   auto stage = [&](int b, int fb) {
     const int cnt = min(FB, f1 - fb);
-    for (int q = threadIdx.x; q < cnt * 2 * NC; q += TBT)
-      sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+    if constexpr (ASYNC) {
+      constexpr int CH = (int)(2 * NC * sizeof(Real) / 16);  // 16-byte pieces per cell
+      for (int q = threadIdx.x; q < cnt * CH; q += TBT) {
+        const int cell = q / CH, piece = q - cell * CH;
+        const char* g = reinterpret_cast<const char*>(mom + (size_t)far_list[fb + cell] * 2 * NC) + 16 * piece;
+        cp_async16(reinterpret_cast<char*>(&sm[b][cell][0]) + 16 * piece, g);
+      }
+      cp_async_commit();
+    } else {
+      for (int q = threadIdx.x; q < cnt * 2 * NC; q += TBT)
+        sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+    }
     if ((int)threadIdx.x < cnt) {
       double4 cc = center[far_list[fb + threadIdx.x]];
       so[b][threadIdx.x][0] = (Real)(ct.x - cc.x);
@@ -171,11 +191,12 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
     }
   };
   if (f0 < f1) stage(0, f0);
-  __syncthreads();
   int b = 0;
   for (int fb = f0; fb < f1; fb += FB, b ^= 1) {
     const int cnt = min(FB, f1 - fb);
-    if (fb + FB < f1) stage(b ^ 1, fb + FB);  // buffer b ^ 1 was last read before the previous barrier
+    if constexpr (ASYNC) cp_async_wait_all();  // this thread's pieces of batch b (the only copies in flight)
+    __syncthreads();  // batch b complete for every thread; every warp is done with the other buffer
+    if (fb + FB < f1) stage(b ^ 1, fb + FB);
     Real v = 0, k = 0;
     if ((int)(threadIdx.x & ~31u) < B.z) {  // warp holds at least one target
       for (int q = 0; q < cnt; ++q) {
@@ -188,7 +209,6 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
     }
     aV += (double)v;
     aK += (double)k;
-    __syncthreads();
   }
   if (act) {
     out[(2 * YUK) * (size_t)n + i] = aV;
