@@ -358,9 +358,13 @@ bempol_status bempol_sizes(const bempol_ctx* c, int64_t* n_panels, int32_t* gaus
                            int64_t* n_near, int64_t* n_cells, int64_t* n_leaves);
 
 /* Kernel accounting (not part of the method; for measurement).  When enabled,
- * the pair kernels (direct or treecode near field) and the treecode far-field
- * kernel are bracketed by CUDA events on their launch stream; bempol_stats_read
- * synchronises the device and reports the summed event times. */
+ * the pair kernels (direct or treecode near field), the treecode far-field
+ * kernels and whole treecode products are bracketed by CUDA events on their launch
+ * stream; bempol_stats_read synchronises the device and reports the summed event
+ * times.  In a treecode product the near-field kernel runs concurrently with the
+ * moment, M2M and far-field kernels (these on a side stream of the context), so
+ * pair_ms and far_ms then overlap and tree_ms (fork to join on the caller's stream)
+ * is the product's own duration. */
 typedef struct {
   int64_t kernel_launches;     /* kernels this library launched (all contexts) since the last reset */
   int64_t pair_launches;       /* launches of the pair kernel */
@@ -369,6 +373,8 @@ typedef struct {
   double far_ms;
   int64_t pair_interactions;   /* (target, Gauss node) pairs evaluated by the pair kernels */
   int64_t far_evaluations;     /* (target, cell) Taylor evaluations of the far-field kernel */
+  int64_t tree_products;       /* treecode products (forward or transposed) */
+  double tree_ms;              /* summed CUDA-event time of those products, fork to join */
 } bempol_stats;
 
 /* Turn event timing on (1) or off (0).  Counting is always on. */

@@ -73,7 +73,7 @@ class Stats(C.Structure):
     _fields_ = [
         ("kernel_launches", C.c_int64), ("pair_launches", C.c_int64), ("pair_ms", C.c_double),
         ("far_launches", C.c_int64), ("far_ms", C.c_double), ("pair_interactions", C.c_int64),
-        ("far_evaluations", C.c_int64),
+        ("far_evaluations", C.c_int64), ("tree_products", C.c_int64), ("tree_ms", C.c_double),
     ]
 
 

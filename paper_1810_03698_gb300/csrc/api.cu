@@ -48,9 +48,24 @@ void Ctx::collect_timers() {
   timed.clear();
 }
 
+void Ctx::ensure_aux() {
+  if (aux) return;
+  int lo = 0, hi = 0;
+  BP_CUDA(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+  BP_CUDA(cudaStreamCreateWithPriority(&aux, cudaStreamNonBlocking, hi));
+  BP_CUDA(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+  BP_CUDA(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+}
+
 Ctx::~Ctx() {
   collect_timers();
   if (h_pinned) cudaFreeHost(h_pinned);
+  if (aux) {
+    cudaStreamSynchronize(aux);
+    cudaStreamDestroy(aux);
+    cudaEventDestroy(ev_fork);
+    cudaEventDestroy(ev_join);
+  }
 }
 
 int num_sms(int device) {
@@ -633,10 +648,12 @@ bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
     out->far_ms = c->stat_ms[1];
     out->pair_interactions = c->stat_pairs;
     out->far_evaluations = c->stat_far;
+    out->tree_products = c->stat_launches[2];
+    out->tree_ms = c->stat_ms[2];
     if (reset) {
       c->launches_at_reset = g_launches.load();
-      c->stat_launches[0] = c->stat_launches[1] = 0;
-      c->stat_ms[0] = c->stat_ms[1] = 0;
+      c->stat_launches[0] = c->stat_launches[1] = c->stat_launches[2] = 0;
+      c->stat_ms[0] = c->stat_ms[1] = c->stat_ms[2] = 0;
       c->stat_pairs = c->stat_far = 0;
     }
   });

@@ -121,6 +121,8 @@ struct Tree {
   // charge moments of the transposed product (Laplace, Yukawa)
   DBuf<float> momT32[2];
   DBuf<double> momT64[2];
+  DBuf<float4> chgT32[2];   // charges (u, 0, 0, 0) at the collocation points, Laplace / Yukawa
+  DBuf<double4> chgT64[2];
   int m2m_min_depth = 0;  // shallowest depth whose cells appear in a far list
   double theta_built = -1.0;
   long long pairs_per_matvec = 0, far_per_matvec = 0, farL_per_matvec = 0;
@@ -216,15 +218,23 @@ struct Ctx {
   double* h_pinned = nullptr;  // pinned host scalars
   int gm_m = 0;
 
+  // side stream (highest priority) of a treecode product: the moments, M2M shifts and
+  // far-field kernels run on it while the near-field kernel runs on the caller's
+  // stream; fork and join events order the two.  Created with the tree.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void ensure_aux();
+
   // optional CUDA-event timing of the pair (direct / near-field) and far-field kernels
+  // and of whole treecode products (fork to join)
   bool stats_on = false;
   struct Timed {
     cudaEvent_t a, b;
-    int kind;  // 0 pair kernel, 1 far-field kernel
+    int kind;  // 0 pair kernel, 1 far-field kernels, 2 treecode product
   };
   std::vector<Timed> timed;
-  double stat_ms[2] = {0, 0};
-  long long stat_launches[2] = {0, 0};
+  double stat_ms[3] = {0, 0, 0};
+  long long stat_launches[3] = {0, 0, 0};
   long long stat_pairs = 0, stat_far = 0;
   long long launches_at_reset = 0;
   void time_begin(int kind, cudaStream_t s, Timed& t);

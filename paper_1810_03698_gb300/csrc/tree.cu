@@ -555,17 +555,38 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str32.p);
   else
     str = reinterpret_cast<const R4*>(c.str64.p);
-  launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
-         c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
-  for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
-    const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
-    launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
-  }
   const int S = T.near_splits;
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
   const Real nk = (Real)(-c.par.kappa * 1.4426950408889634);
+  // Fork: the far-field chain (moments, M2M shifts, far kernels) on the context's
+  // high-priority side stream, the near field on `s`; the near kernel needs no moments,
+  // so its blocks fill the SMs that the small M2M grids and the far kernels' last wave
+  // leave idle.  The two write disjoint pieces of c.part.
+  c.ensure_aux();
+  const cudaStream_t sf = c.aux;
+  Ctx::Timed tp;
+  c.time_begin(2, s, tp);
+  BP_CUDA(cudaEventRecord(c.ev_fork, s));
+  BP_CUDA(cudaStreamWaitEvent(sf, c.ev_fork, 0));
+  launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
+         c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
+  for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
+    const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
+    launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
+  }
+  Ctx::Timed tf;
+  c.time_begin(1, sf, tf);
+  c.stat_far += T.far_per_matvec;
+  double* far_out = c.part.p + (size_t)S * 4 * c.n;
+  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
+  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
+  launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
+         kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
+         T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  c.time_end(sf, tf);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);
   c.stat_pairs += T.pairs_per_matvec;
@@ -573,17 +594,9 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
          T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
          c.mv_active, T.leaf_sys.p, c.part.p);
   c.time_end(s, tm);
-  Ctx::Timed tf;
-  c.time_begin(1, s, tf);
-  c.stat_far += T.far_per_matvec;
-  double* far_out = c.part.p + (size_t)S * 4 * c.n;
-  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
-  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
-  launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
-         kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, s, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
-         T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  c.time_end(s, tf);
+  BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join
+  BP_CUDA(cudaStreamWaitEvent(s, c.ev_join, 0));
+  c.time_end(s, tp);
   c.part_splits = S + 1;
 }
 

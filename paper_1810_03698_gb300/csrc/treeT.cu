@@ -327,6 +327,17 @@ __global__ void centroid_charges_kernel(const double* __restrict__ u, int n, R4*
 }
 
 
+template <typename R4>
+DBuf<R4>& chgT(Tree& T, int w);
+template <>
+DBuf<float4>& chgT<float4>(Tree& T, int w) {
+  return T.chgT32[w];
+}
+template <>
+DBuf<double4>& chgT<double4>(Tree& T, int w) {
+  return T.chgT64[w];
+}
+
 template <typename Real>
 DBuf<Real>& momT(Tree& T, int w);
 template <>
@@ -347,42 +358,53 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   DBuf<Real>& mY = momT<Real>(T, 1);
   if (mL.n < (size_t)T.ncell * 2 * NC) mL.alloc((size_t)T.ncell * 2 * NC);
   if (mY.n < (size_t)T.ncell * 2 * NC) mY.alloc((size_t)T.ncell * 2 * NC);
-  DBuf<R4> sL, sY;
-  sL.alloc(c.n);
-  sY.alloc(c.n);
-  launch(centroid_charges_kernel<R4>, cdiv(c.n, 256), 256, 0, s, u, c.n, sL.p, sY.p);
-  for (int w = 0; w < 2; ++w) {
-    DBuf<Real>& m = w ? mY : mL;
-    launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, s, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
-           c.tgt64.p, (const R4*)(w ? sY.p : sL.p), c.mv_active, T.leaf_sys.p, m.p);
-    for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {
-      const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
-      launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, m.p);
-    }
-  }
+  DBuf<R4>& sL = chgT<R4>(T, 0);
+  DBuf<R4>& sY = chgT<R4>(T, 1);
+  if (sL.n < (size_t)c.n) sL.alloc(c.n);
+  if (sY.n < (size_t)c.n) sY.alloc(c.n);
   const int S = T.near_splits;
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
+  // Fork as in the forward product: charges, moments, M2M shifts and far kernels on the
+  // high-priority side stream, the near field (which reads u directly) on `s`.
+  c.ensure_aux();
+  const cudaStream_t sf = c.aux;
+  Ctx::Timed tp;
+  c.time_begin(2, s, tp);
+  BP_CUDA(cudaEventRecord(c.ev_fork, s));
+  BP_CUDA(cudaStreamWaitEvent(sf, c.ev_fork, 0));
+  launch(centroid_charges_kernel<R4>, cdiv(c.n, 256), 256, 0, sf, u, c.n, sL.p, sY.p);
+  for (int w = 0; w < 2; ++w) {
+    DBuf<Real>& m = w ? mY : mL;
+    launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
+           c.tgt64.p, (const R4*)(w ? sY.p : sL.p), c.mv_active, T.leaf_sys.p, m.p);
+    for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {
+      const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
+      launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, m.p);
+    }
+  }
+  Ctx::Timed tf;
+  c.time_begin(1, sf, tf);
+  double* far_out = c.part.p + (size_t)S * 4 * c.n;
+  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
+  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
+  launch(farT_kernel<P, Real, 0>, T.nblk32, 128, 0, sf, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
+         T.leaf_cell.p, T.center.p, lp, ll, mL.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(farT_kernel<P, Real, 1>, T.nblk32, 128, 0, sf, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
+         T.leaf_cell.p, T.center.p, T.far_ptr.p, T.far_list.p, mY.p, kappa, c.n, c.mv_active, T.leaf_sys.p,
+         far_out);
+  c.time_end(sf, tf);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);
   launch(nearT_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
          T.leaf_cell.p, T.center.p, T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, T.cen_rel32.p, c.tgt64.p, u,
          kappa, c.n, c.mv_active, T.leaf_sys.p, c.part.p);
   c.time_end(s, tm);
-  Ctx::Timed tf;
-  c.time_begin(1, s, tf);
-  double* far_out = c.part.p + (size_t)S * 4 * c.n;
-  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
-  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
-  launch(farT_kernel<P, Real, 0>, T.nblk32, 128, 0, s, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
-         T.leaf_cell.p, T.center.p, lp, ll, mL.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(farT_kernel<P, Real, 1>, T.nblk32, 128, 0, s, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
-         T.leaf_cell.p, T.center.p, T.far_ptr.p, T.far_list.p, mY.p, kappa, c.n, c.mv_active, T.leaf_sys.p,
-         far_out);
-  c.time_end(s, tf);
+  BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join
+  BP_CUDA(cudaStreamWaitEvent(s, c.ev_join, 0));
+  c.time_end(s, tp);
   c.part_splits = S + 1;
-  BP_CUDA(cudaStreamSynchronize(s));  // the strength buffers are released on return
 }
 
 // The transposed far field runs in FP32 at order 4 whatever the forward order: the

@@ -191,3 +191,24 @@ def test_gradient_at_scale_copy(bp):
                 vals.append(rr["G_diss"] - rr["G_vac"])
             fd = (vals[0] - vals[1]) / (2.0 * h)
             assert fd == pytest.approx(g64["pos"][l, a], rel=1e-5, abs=1e-7 * np.max(np.abs(g64["pos"]))), (l, a)
+
+
+@pytest.mark.parametrize("op,bar", [("fp64_direct", 1e-12), ("fp32_tree", 2e-4)])
+def test_adjoint_identity_fullsize(bp, op, bar):
+    """<y, A x> = <A^T y, x> on the 20,480-panel sphere with 100 sites: to rounding for
+    the direct form; for the treecode the two products are separate approximations, each
+    within the treecode's error."""
+    pr = gen.config2()
+    s = bp.problem_solver(pr, theta=0.5, order=5)
+    n = pr.n_panels
+    g = np.random.default_rng(34)
+    x = _dev(g.normal(size=2 * n))
+    y = _dev(g.normal(size=2 * n))
+    ax = torch.zeros_like(x)
+    aty = torch.zeros_like(x)
+    s.matvec(x, ax, op=op)
+    s.matvec_transposed(y, aty, op=op)
+    lhs = float(torch.dot(y, ax))
+    rhs = float(torch.dot(aty, x))
+    scale = float(torch.linalg.norm(y) * torch.linalg.norm(ax))
+    assert abs(lhs - rhs) <= bar * scale
