@@ -517,6 +517,16 @@ def main():
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock",
                 "share_of_step": kd["total_ms"] / max(total_ms, 1e-9), "kernels": kernels}
 
+    # ---- where a step's time goes (live CUDA-event sums over the timed steps, per step)
+    K_ = args.steps
+    prod_ms = stats["tree_ms"] if stats["tree_products"] else stats["pair_ms"] + stats["far_ms"]
+    breakdown = {"step_ms": total_ms / K_, "set_mesh_ms": phases["set_mesh_ms"], "set_sites_ms": phases["set_sites_ms"],
+                 "operator_products_ms": prod_ms / K_, "rhs_ms": stats["rhs_ms"] / K_,
+                 "reaction_field_ms": stats["reaction_ms"] / K_, "site_fields_ms": stats["site_field_ms"] / K_}
+    breakdown["other_ms"] = breakdown["step_ms"] - sum(v for k, v in breakdown.items() if k != "step_ms")
+    breakdown["note"] = ("other = GMRES orthogonalisation, near-field corrections and combines, induced-dipole "
+                         "updates, energies, host logic; set_mesh/set_sites from one untimed step")
+
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -577,6 +587,7 @@ def main():
                    "fp64_peak_nominal_tflops": 1.25,
                    "interactions_per_matvec": inter},
         "roofline": roofline,
+        "breakdown": breakdown,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(stats["kernel_launches"]),

@@ -359,7 +359,8 @@ bempol_status bempol_sizes(const bempol_ctx* c, int64_t* n_panels, int32_t* gaus
 
 /* Kernel accounting (not part of the method; for measurement).  When enabled,
  * the pair kernels (direct or treecode near field), the treecode far-field
- * kernels and whole treecode products are bracketed by CUDA events on their launch
+ * kernels, whole treecode products and the right-hand sides, reaction fields and
+ * multipole fields of bempol_solve* are bracketed by CUDA events on their launch
  * stream; bempol_stats_read synchronises the device and reports the summed event
  * times.  In a treecode product the near-field kernel runs concurrently with the
  * moment, M2M and far-field kernels (these on a side stream of the context), so
@@ -375,6 +376,12 @@ typedef struct {
   int64_t far_evaluations;     /* (target, cell) Taylor evaluations of the far-field kernel */
   int64_t tree_products;       /* treecode products (forward or transposed) */
   double tree_ms;              /* summed CUDA-event time of those products, fork to join */
+  int64_t rhs_calls;           /* right-hand sides evaluated inside bempol_solve* */
+  double rhs_ms;
+  int64_t reaction_calls;      /* reaction fields at the sites inside the induced-dipole iteration */
+  double reaction_ms;
+  int64_t site_field_calls;    /* multipole fields at the sites inside the induced-dipole iterations */
+  double site_field_ms;
 } bempol_stats;
 
 /* Turn event timing on (1) or off (0).  Counting is always on. */

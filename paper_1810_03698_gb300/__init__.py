@@ -74,6 +74,8 @@ class Stats(C.Structure):
         ("kernel_launches", C.c_int64), ("pair_launches", C.c_int64), ("pair_ms", C.c_double),
         ("far_launches", C.c_int64), ("far_ms", C.c_double), ("pair_interactions", C.c_int64),
         ("far_evaluations", C.c_int64), ("tree_products", C.c_int64), ("tree_ms", C.c_double),
+        ("rhs_calls", C.c_int64), ("rhs_ms", C.c_double), ("reaction_calls", C.c_int64), ("reaction_ms", C.c_double),
+        ("site_field_calls", C.c_int64), ("site_field_ms", C.c_double),
     ]
 
 

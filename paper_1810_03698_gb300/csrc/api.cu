@@ -36,6 +36,18 @@ void Ctx::time_end(cudaStream_t s, Timed& t) {
   timed.push_back(t);
 }
 
+void Ctx::stat_rewind(const StatMark& m) {
+  for (size_t k = m.ntimed; k < timed.size(); ++k) {
+    cudaEventSynchronize(timed[k].b);
+    cudaEventDestroy(timed[k].a);
+    cudaEventDestroy(timed[k].b);
+  }
+  if (timed.size() > m.ntimed) timed.resize(m.ntimed);
+  for (int k = 0; k < 3; ++k) stat_launches[k] = m.launches[k];
+  stat_pairs = m.pairs;
+  stat_far = m.far;
+}
+
 void Ctx::collect_timers() {
   for (auto& t : timed) {
     float ms = 0;
@@ -60,6 +72,8 @@ void Ctx::ensure_aux() {
 Ctx::~Ctx() {
   collect_timers();
   if (h_pinned) cudaFreeHost(h_pinned);
+  for (cudaEvent_t e : gm_ev)
+    if (e) cudaEventDestroy(e);
   if (aux) {
     cudaStreamSynchronize(aux);
     cudaStreamDestroy(aux);
@@ -650,10 +664,18 @@ bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
     out->far_evaluations = c->stat_far;
     out->tree_products = c->stat_launches[2];
     out->tree_ms = c->stat_ms[2];
+    out->rhs_calls = c->stat_launches[3];
+    out->rhs_ms = c->stat_ms[3];
+    out->reaction_calls = c->stat_launches[4];
+    out->reaction_ms = c->stat_ms[4];
+    out->site_field_calls = c->stat_launches[5];
+    out->site_field_ms = c->stat_ms[5];
     if (reset) {
       c->launches_at_reset = g_launches.load();
-      c->stat_launches[0] = c->stat_launches[1] = c->stat_launches[2] = 0;
-      c->stat_ms[0] = c->stat_ms[1] = c->stat_ms[2] = 0;
+      for (int k = 0; k < Ctx::NKIND; ++k) {
+        c->stat_launches[k] = 0;
+        c->stat_ms[k] = 0;
+      }
       c->stat_pairs = c->stat_far = 0;
     }
   });
@@ -788,7 +810,10 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
       std::vector<Guard> gv(S);
       for (int it = 1; it <= P.scf_maxit; ++it) {
         upload_act(act);
+        Ctx::Timed tv;
+        c->time_begin(5, s, tv);
         multipole_internal(*c, mu_v.p, 2, emult.p, s, f32);
+        c->time_end(s, tv);
         std::vector<double> rms = sor_update(*c, mu_v.p, nullptr, emult.p, true, d_act.p, s);
         int left = 0;
         for (int q = 0; q < S; ++q) {
@@ -810,7 +835,10 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     std::vector<char> want(S, 1);
     auto bem = [&](const std::vector<char>& which) {
       launch(add_vec, cdiv(3 * ns, 256), 256, 0, s, c->site_d.p, mu.p, p.p, 3 * ns);
+      Ctx::Timed tr;
+      c->time_begin(3, s, tr);
       rhs_internal(*c, p.p, b.p, f32, s);
+      c->time_end(s, tr);
       GmresOut g = solve_bem(*c, b.p, x.p, which, s);
       gm_iters += g.iters;
       matvecs += g.matvecs;
@@ -831,8 +859,13 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
       for (int it = 1; it <= P.scf_maxit; ++it) {
         for (int q = 0; q < S; ++q) want[q] = (char)act[q];
         bem(want);
+        Ctx::Timed tx, tm;
+        c->time_begin(4, s, tx);
         site_reaction_internal(*c, x.p, react.p, f32, false, s);
+        c->time_end(s, tx);
+        c->time_begin(5, s, tm);
         multipole_internal(*c, mu.p, 0, emult.p, s, f32);
+        c->time_end(s, tm);
         upload_act(act);
         std::vector<double> rms = sor_update(*c, mu.p, react.p, emult.p, false, d_act.p, s);
         int left = 0;

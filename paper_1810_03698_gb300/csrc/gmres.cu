@@ -124,6 +124,21 @@ __global__ void axpby(double a, const double* __restrict__ x, double b, const do
   if (i < len) out[i] = a * x[i] + b * y[i];
 }
 
+// Second Gram-Schmidt pass and normalisation in one sweep, for the active systems:
+// w = (w - sum_k V_k h[s][k]) / sqrt(nrm2[s * ldn]), k < nv.
+__global__ void subtract_normalize(const double* __restrict__ V, size_t ld, int nv, const double* __restrict__ h,
+                                   int ldh, const double* __restrict__ nrm2, int ldn, const int* __restrict__ psys,
+                                   const int* __restrict__ active, double* __restrict__ w, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 2 * n) return;
+  const int sy = sys_of(psys, i, n);
+  if (active && !active[sy]) return;
+  const double* hs = h + (size_t)sy * ldh;
+  double v = w[i];
+  for (int k = 0; k < nv; ++k) v -= V[(size_t)k * ld + i] * hs[k];
+  w[i] = v / sqrt(nrm2[(size_t)sy * ldn]);
+}
+
 // v_out = w / sqrt(nrm2[s * ldn]) for the active systems (the norm read on the device)
 __global__ void normalize_kernel(const double* __restrict__ w, const double* __restrict__ nrm2, int ldn,
                                  const int* __restrict__ psys, const int* __restrict__ active,
@@ -136,21 +151,33 @@ __global__ void normalize_kernel(const double* __restrict__ w, const double* __r
 }
 
 // Givens step for column j of system s's Hessenberg matrix (one thread per active
-// system).  hcol[s][0..j] = projections, nrm2[s] = |w|^2 gives h_{j+1,j}.  State
-// cs, sn [m], g [m+1] per system.  Writes |g_{j+1}| to res[s].
+// system).  Column j = hcol[s][0..j] + h2[s][0..j] (the two Gram-Schmidt passes);
+// h2[s][j + 1] = |w'|^2 of the vector after the first pass, so the vector after the
+// second pass has |w''|^2 = |w'|^2 - sum_k h2[s][k]^2 (Pythagoras: the columns of V
+// are orthonormal), stored to nrm2[s * ldc]; h_{j+1,j} = |w''|.  State cs, sn [m],
+// g [m+1] per system.  Writes |g_{j+1}| to res[s] and clears active[s] when it is no
+// longer above tol[s] (the system stops; later launches skip it).
 __global__ void givens_kernel(double* __restrict__ H, int ldh, size_t sH, int j, const double* __restrict__ hcol,
-                              int ldc, const double* __restrict__ nrm2, double* __restrict__ cs,
-                              double* __restrict__ sn, double* __restrict__ g, int ldg, double* __restrict__ res,
-                              const int* __restrict__ active, int nsys) {
+                              const double* __restrict__ h2, int ldc, double* __restrict__ nrm2,
+                              double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g, int ldg,
+                              double* __restrict__ res, const double* __restrict__ tol, int* __restrict__ active,
+                              int nsys) {
   const int sy = blockIdx.x * blockDim.x + threadIdx.x;
-  if (sy >= nsys || (active && !active[sy])) return;
+  if (sy >= nsys || !active[sy]) return;
   double* col = H + sy * sH + (size_t)j * ldh;
   const double* hc = hcol + (size_t)sy * ldc;
+  const double* hd = h2 + (size_t)sy * ldc;
   double* c_ = cs + (size_t)sy * ldg;
   double* s_ = sn + (size_t)sy * ldg;
   double* g_ = g + (size_t)sy * ldg;
-  for (int k = 0; k <= j; ++k) col[k] = hc[k];
-  col[j + 1] = sqrt(nrm2[(size_t)sy * ldc]);
+  double q2 = 0.0;
+  for (int k = 0; k <= j; ++k) {
+    col[k] = hc[k] + hd[k];
+    q2 += hd[k] * hd[k];
+  }
+  const double nn = fmax(hd[j + 1] - q2, 0.0);
+  nrm2[(size_t)sy * ldc] = nn;
+  col[j + 1] = sqrt(nn);
   for (int k = 0; k < j; ++k) {
     double t = c_[k] * col[k] + s_[k] * col[k + 1];
     col[k + 1] = -s_[k] * col[k] + c_[k] * col[k + 1];
@@ -165,7 +192,9 @@ __global__ void givens_kernel(double* __restrict__ H, int ldh, size_t sH, int j,
   col[j + 1] = 0.0;
   g_[j + 1] = -s * g_[j];
   g_[j] = c * g_[j];
-  res[sy] = fabs(g_[j + 1]);
+  const double rj = fabs(g_[j + 1]);
+  res[sy] = rj;
+  if (!(rj > tol[sy])) active[sy] = 0;
 }
 
 // solve the k[s] x k[s] upper-triangular system R y = g of every system
@@ -303,6 +332,12 @@ GmresOut gmres(Ctx& c, int op, const double* b, double* x, const std::vector<dou
   std::vector<int> todo(S, 0), act(S, 0), kk(S, 0);
   for (int q = 0; q < S; ++q) todo[q] = tol_abs[q] >= 0.0;
   rres.assign(S, 0.0);
+  if (c.gm_tol.n < (size_t)S) c.gm_tol.alloc(S);
+  for (cudaEvent_t& e : c.gm_ev)
+    if (!e) BP_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  std::copy(tol_abs.begin(), tol_abs.end(), c.h_pinned);
+  BP_CUDA(cudaMemcpyAsync(c.gm_tol.p, c.h_pinned, sizeof(double) * S, cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaStreamSynchronize(s));  // the pinned staging area is reused right away
   int total = 0;
   while (true) {
     // r = b - A x, per-system norms
@@ -331,42 +366,58 @@ GmresOut gmres(Ctx& c, int op, const double* b, double* x, const std::vector<dou
     launch(set_g0, cdiv(S, 64), 64, 0, s, w.g, w.lds, w.nrm2, w.lds, m, w.active, S);
     BP_CHECK_LAUNCH();
     std::fill(kk.begin(), kk.end(), 0);
-    for (int j = 0; j < m && total < maxit; ++j) {
-      double* vj = w.V + (size_t)j * w.ld;
-      double* wv = w.V + (size_t)(j + 1) * w.ld;
-      c.mv_active = w.active;
-      matvec_internal(c, vj, wv, op, s);
-      c.mv_active = nullptr;
-      ++out.matvecs;
-      // CGS2, per system
-      multidot(c, w, w.V, j + 1, wv, w.hcol, w.active, s);
-      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.hcol, w.lds, c.psys.p, w.active, wv, n);
-      multidot(c, w, w.V, j + 1, wv, w.h2, w.active, s);
-      launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.h2, w.lds, c.psys.p, w.active, wv, n);
-      launch(axpby, cdiv(S * w.lds, 256), 256, 0, s, 1.0, w.hcol, 1.0, w.h2, w.hcol, S * w.lds);
-      multidot(c, w, wv, 1, wv, w.nrm2, w.active, s);
-      launch(givens_kernel, cdiv(S, 64), 64, 0, s, w.H, w.ldh, w.sH, j, w.hcol, w.lds, w.nrm2, w.cs, w.sn, w.g,
-             w.lds, w.res, w.active, S);
-      launch(normalize_kernel, nb, tb, 0, s, wv, w.nrm2, w.lds, c.psys.p, w.active, wv, n);
-      BP_CHECK_LAUNCH();
-      ++total;
-      ++out.iters;
-      BP_CUDA(cudaMemcpyAsync(c.h_pinned, w.res, sizeof(double) * S, cudaMemcpyDeviceToHost, s));
-      BP_CUDA(cudaStreamSynchronize(s));
-      bool any = false, changed = false;
-      for (int q = 0; q < S; ++q) {
-        if (!act[q]) continue;
-        kk[q] = j + 1;
-        ++out.sys_iters[q];
-        if (!(c.h_pinned[q] > tol_abs[q])) {
-          act[q] = 0;
-          changed = true;
-        } else {
-          any = true;
+    // Arnoldi steps, pipelined one deep: step j is enqueued before the host waits for
+    // the residual estimates of step j - 1.  The Givens kernel clears a converged
+    // system's device flag itself, so step j already skips it; the host's flags follow
+    // the same test one step later.  After the last system stops, the step enqueued
+    // behind it finds every flag clear and does no work.
+    int pending = -1;
+    for (int j = 0;; ++j) {
+      const bool more = j < m && total + (pending >= 0 ? 1 : 0) < maxit;
+      const Ctx::StatMark mark = c.stat_mark();
+      if (more) {
+        double* vj = w.V + (size_t)j * w.ld;
+        double* wv = w.V + (size_t)(j + 1) * w.ld;
+        c.mv_active = w.active;
+        matvec_internal(c, vj, wv, op, s);
+        c.mv_active = nullptr;
+        // CGS2 per system; the second inner product also gives |w'|^2 (V_{j+1} = w')
+        multidot(c, w, w.V, j + 1, wv, w.hcol, w.active, s);
+        launch(subtract_proj, nb, tb, 0, s, w.V, w.ld, j + 1, w.hcol, w.lds, c.psys.p, w.active, wv, n);
+        multidot(c, w, w.V, j + 2, wv, w.h2, w.active, s);
+        launch(givens_kernel, cdiv(S, 64), 64, 0, s, w.H, w.ldh, w.sH, j, w.hcol, w.h2, w.lds, w.nrm2, w.cs, w.sn,
+               w.g, w.lds, w.res, c.gm_tol.p, w.active, S);
+        launch(subtract_normalize, nb, tb, 0, s, w.V, w.ld, j + 1, w.h2, w.lds, w.nrm2, w.lds, c.psys.p, w.active, wv,
+               n);
+        BP_CHECK_LAUNCH();
+        BP_CUDA(cudaMemcpyAsync(c.h_pinned + (size_t)(j & 1) * S, w.res, sizeof(double) * S, cudaMemcpyDeviceToHost,
+                                s));
+        BP_CUDA(cudaEventRecord(c.gm_ev[j & 1], s));
+      }
+      bool any = pending >= 0;
+      if (pending >= 0) {
+        BP_CUDA(cudaEventSynchronize(c.gm_ev[pending & 1]));
+        const double* hr = c.h_pinned + (size_t)(pending & 1) * S;
+        ++total;
+        ++out.iters;
+        ++out.matvecs;
+        any = false;
+        for (int q = 0; q < S; ++q) {
+          if (!act[q]) continue;
+          kk[q] = pending + 1;
+          ++out.sys_iters[q];
+          if (!(hr[q] > tol_abs[q]))
+            act[q] = 0;
+          else
+            any = true;
         }
       }
-      if (!any) break;
-      if (changed) put_flags(c, w.active, act, s);
+      if (pending >= 0 && !any) {
+        if (more) c.stat_rewind(mark);  // step j found every system stopped
+        break;
+      }
+      if (!more) break;
+      pending = j;
     }
     // x += V y per system
     put_flags(c, w.kk, kk, s);

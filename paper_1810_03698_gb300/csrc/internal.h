@@ -213,6 +213,8 @@ struct Ctx {
   bool have_solution = false;
   DBuf<double> sol_x, sol_mu, sol_mu_v;
   DBuf<unsigned> gm_ticket;  // last-block ticket of the multi-dot kernel (kept at 0 between calls)
+  DBuf<double> gm_tol;       // [S] absolute GMRES tolerances of the current solve (device copy)
+  cudaEvent_t gm_ev[2] = {nullptr, nullptr};  // residual copies of alternate GMRES iterations
   DBuf<double> vec_a, vec_b, vec_c, vec_d;   // [2n] scratch vectors
   DBuf<double> scal;         // device scalars
   double* h_pinned = nullptr;  // pinned host scalars
@@ -225,21 +227,33 @@ struct Ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   void ensure_aux();
 
-  // optional CUDA-event timing of the pair (direct / near-field) and far-field kernels
-  // and of whole treecode products (fork to join)
+  // optional CUDA-event timing of the pair (direct / near-field) and far-field kernels,
+  // of whole treecode products (fork to join) and of the solve's other phases
   bool stats_on = false;
   struct Timed {
     cudaEvent_t a, b;
-    int kind;  // 0 pair kernel, 1 far-field kernels, 2 treecode product
+    int kind;  // 0 pair kernel, 1 far-field kernels, 2 treecode product, 3 right-hand side,
+               // 4 reaction field at the sites, 5 multipole fields at the sites
   };
+  static constexpr int NKIND = 6;
   std::vector<Timed> timed;
-  double stat_ms[3] = {0, 0, 0};
-  long long stat_launches[3] = {0, 0, 0};
+  double stat_ms[NKIND] = {};
+  long long stat_launches[NKIND] = {};
   long long stat_pairs = 0, stat_far = 0;
   long long launches_at_reset = 0;
   void time_begin(int kind, cudaStream_t s, Timed& t);
   void time_end(cudaStream_t s, Timed& t);
   void collect_timers();
+  // accounting state, to drop the records of a product that turned out to have no
+  // active system (its launches still count in kernel_launches)
+  struct StatMark {
+    size_t ntimed;
+    long long launches[3], pairs, far;
+  };
+  StatMark stat_mark() const {
+    return {timed.size(), {stat_launches[0], stat_launches[1], stat_launches[2]}, stat_pairs, stat_far};
+  }
+  void stat_rewind(const StatMark& m);
 
   Ctx() = default;
   ~Ctx();
