@@ -685,9 +685,11 @@ __global__ void __launch_bounds__(256) site_force_kernel(const double4* __restri
 
 }  // namespace
 
-void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s) {
+void ensure_near_transpose(Ctx& c, cudaStream_t s) {
+  if (c.nearT_ready) return;
   const int n = c.n;
-  std::vector<int> col(std::max<int64_t>(1, c.nnz));
+  std::vector<int> ptr(n + 1), col(std::max<int64_t>(1, c.nnz));
+  BP_CUDA(cudaMemcpyAsync(ptr.data(), c.near_ptr.p, sizeof(int) * (n + 1), cudaMemcpyDeviceToHost, s));
   if (c.nnz)
     BP_CUDA(cudaMemcpyAsync(col.data(), c.near_col.p, sizeof(int) * c.nnz, cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
@@ -708,10 +710,12 @@ void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s) {
   BP_CUDA(cudaMemcpyAsync(c.near_rowT.p, rT.data(), sizeof(int) * rT.size(), cudaMemcpyHostToDevice, s));
   BP_CUDA(cudaMemcpyAsync(c.near_eT.p, eT.data(), sizeof(int) * eT.size(), cudaMemcpyHostToDevice, s));
   BP_CUDA(cudaStreamSynchronize(s));
+  c.nearT_ready = true;
 }
 
 void matvec_T_internal(Ctx& c, const double* u, double* y, int op, cudaStream_t s) {
   const int n = c.n;
+  ensure_near_transpose(c, s);
   const bool fp32 = (op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE);
   if (op == BEMPOL_OP_FP32_TREE) {
     tree_matvec_T_sums(c, u, s);

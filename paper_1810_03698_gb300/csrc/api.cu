@@ -177,15 +177,20 @@ void size_scalars(Ctx& c) {
 // Groups (bodies of systems) from per-panel system and body ids (NULL = all 0):
 // sorted (system, body) pairs; returns the group of every panel (caller order).
 std::vector<int> make_groups(Ctx& c, int64_t nt, const std::vector<int32_t>& sy, const std::vector<int32_t>& bo) {
-  std::vector<std::pair<int, int>> key(nt);
-  for (int64_t t = 0; t < nt; ++t) {
-    const int a = sy.empty() ? 0 : sy[t], b = bo.empty() ? 0 : bo[t];
-    if (a < 0 || b < 0) fail(BEMPOL_ERR_ARG, "system and body ids must be >= 0");
-    key[t] = {a, b};
+  std::vector<std::pair<int, int>> key, u;
+  if (sy.empty() && bo.empty()) {
+    u.assign(1, {0, 0});  // one system of one body
+  } else {
+    key.resize(nt);
+    for (int64_t t = 0; t < nt; ++t) {
+      const int a = sy.empty() ? 0 : sy[t], b = bo.empty() ? 0 : bo[t];
+      if (a < 0 || b < 0) fail(BEMPOL_ERR_ARG, "system and body ids must be >= 0");
+      key[t] = {a, b};
+    }
+    u = key;
+    std::sort(u.begin(), u.end());
+    u.erase(std::unique(u.begin(), u.end()), u.end());
   }
-  std::vector<std::pair<int, int>> u(key);
-  std::sort(u.begin(), u.end());
-  u.erase(std::unique(u.begin(), u.end()), u.end());
   if (u.size() > 1023) fail(BEMPOL_ERR_ARG, "at most 1023 (system, body) groups");
   const int S = u.back().first + 1;
   c.ngroup = (int)u.size();

@@ -8,6 +8,7 @@
 // (centroid = ((v0 + v1) + v2) / 3, cross = (v1 - v0) x (v2 - v0), area = |cross| / 2).
 #include <algorithm>
 #include <cstring>
+#include <climits>
 #include <unordered_map>
 
 #include "internal.h"
@@ -147,29 +148,43 @@ __global__ void gather_geometry(const int* __restrict__ perm, int n, int K, cons
 
 // Every directed edge must appear once and its reverse once, in a triangle of the
 // same group: each body is a closed, consistently oriented surface of its own.
+// Every directed edge a->b of the mesh must be used once and have its opposite b->a,
+// on a triangle of the same body.  The outgoing edges of each vertex are bucketed by a
+// counting sort and sorted by their end vertex (buckets are small), so duplicates are
+// adjacent and each opposite edge is a binary search in its start vertex's bucket.
 void validate_closed(const int* tris, int n, int nv, const std::vector<int>& grp) {
-  std::vector<std::pair<unsigned long long, int>> e;
-  e.reserve(3 * (size_t)n);
+  std::vector<int> ptr((size_t)nv + 1, 0);
   for (int t = 0; t < n; ++t) {
     for (int k = 0; k < 3; ++k) {
-      int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+      const int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
       if (a < 0 || a >= nv || b < 0 || b >= nv)
         fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " has a vertex index out of range");
       if (a == b) fail(BEMPOL_ERR_MESH, "triangle " + std::to_string(t) + " repeats a vertex");
-      e.push_back({((unsigned long long)(unsigned)a << 32) | (unsigned)b, grp.empty() ? 0 : grp[t]});
+      ++ptr[a + 1];
     }
   }
-  std::sort(e.begin(), e.end());
-  for (size_t i = 1; i < e.size(); ++i)
-    if (e[i].first == e[i - 1].first)
-      fail(BEMPOL_ERR_MESH, "a directed edge is used twice (inconsistent orientation or non-manifold mesh)");
-  for (auto& k : e) {
-    unsigned long long r = ((k.first & 0xffffffffull) << 32) | (k.first >> 32);
-    auto it = std::lower_bound(e.begin(), e.end(), std::make_pair(r, -1));
-    if (it == e.end() || it->first != r)
-      fail(BEMPOL_ERR_MESH, "the mesh is not closed: an edge has no opposite neighbour");
-    if (it->second != k.second) fail(BEMPOL_ERR_MESH, "two bodies share an edge: each body must be closed");
+  for (int v = 0; v < nv; ++v) ptr[v + 1] += ptr[v];
+  std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+  std::vector<std::pair<int, int>> out(3 * (size_t)n);  // (end vertex, body group)
+  for (int t = 0; t < n; ++t)
+    for (int k = 0; k < 3; ++k) {
+      const int a = tris[3 * t + k], b = tris[3 * t + (k + 1) % 3];
+      out[fill[a]++] = {b, grp.empty() ? 0 : grp[t]};
+    }
+  for (int v = 0; v < nv; ++v) {
+    std::sort(out.begin() + ptr[v], out.begin() + ptr[v + 1]);
+    for (int q = ptr[v] + 1; q < ptr[v + 1]; ++q)
+      if (out[q].first == out[q - 1].first)
+        fail(BEMPOL_ERR_MESH, "a directed edge is used twice (inconsistent orientation or non-manifold mesh)");
   }
+  for (int a = 0; a < nv; ++a)
+    for (int q = ptr[a]; q < ptr[a + 1]; ++q) {
+      const int b = out[q].first;
+      auto lo = out.begin() + ptr[b], hi = out.begin() + ptr[b + 1];
+      auto it = std::lower_bound(lo, hi, std::make_pair(a, INT_MIN));
+      if (it == hi || it->first != a) fail(BEMPOL_ERR_MESH, "the mesh is not closed: an edge has no opposite neighbour");
+      if (it->second != out[q].second) fail(BEMPOL_ERR_MESH, "two bodies share an edge: each body must be closed");
+    }
 }
 
 }  // namespace

@@ -162,6 +162,7 @@ struct Ctx {
   // the near table by columns: for panel j, entries [near_ptrT[j], near_ptrT[j+1])
   // hold (row i, index into near_corr) of every near pair (i, j)
   DBuf<int> near_ptrT, near_rowT, near_eT;
+  bool nearT_ready = false;  // the three above match the current near table
   double bbox_lo[3], bbox_hi[3];
   double max_area = 0.0;     // largest panel area (near-field search radius)
   std::vector<unsigned> h_morton;  // 30-bit Morton code of each internal panel (sorted)
@@ -281,7 +282,8 @@ void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
 void tree_matvec_T_sums(Ctx& c, const double* u, cudaStream_t s);
 void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells);
 // adjoint.cu
-void build_near_transpose(Ctx& c, const std::vector<int>& ptr, cudaStream_t s);
+// builds the near table by columns (near_ptrT/rowT/eT) if the current mesh has none yet
+void ensure_near_transpose(Ctx& c, cudaStream_t s);
 void matvec_T_internal(Ctx& c, const double* u, double* y, int op, cudaStream_t s);
 struct AdjointOut {
   int iters_diss = 0, iters_vac = 0, solves = 0, gmres_iters = 0;

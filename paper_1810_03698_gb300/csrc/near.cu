@@ -255,7 +255,7 @@ void build_near(Ctx& c, cudaStream_t s) {
   launch(near_corr_kernel, cdiv(c.nnz, 128), 128, 0, s, c.near_ptr.p, c.near_col.p, n, (int)c.nnz, c.tgt64.p,
          c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.ptag.p, c.near_corr.p);
   BP_CHECK_LAUNCH();
-  build_near_transpose(c, ptr, s);
+  c.nearT_ready = false;  // the table by columns is built on the first transposed product
   BP_CUDA(cudaStreamSynchronize(s));
 }
 
