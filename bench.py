@@ -19,8 +19,8 @@ torch.distributed.run each rank solves its own replica (independent problems, no
 collective in the data path: weak scaling).  --impl reference times the oracle.
 
 --workload gradient times the adjoint gradient dDelta G_solv/d(positions, q, d, Q)
-after a forward solve on workload 5 (327,680 panels, 10,000 sites; --grad-config 3
-for workload 3) and reports gradient cost / forward cost, with Euler's identity
+after a forward solve on the 327,680-panel surface with 10,000 sites (--grad-panels 81920
+for the 81,920-panel one) and reports gradient cost / forward cost, with Euler's identity
 sum_l m_l . dG/dm_l = 2 Delta G_solv as a consistency check of the gradient.
 
 --workload binding times the binding workload instead: 16 triples (A, B, AB) of
@@ -80,7 +80,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-rows", type=int, default=384)
     ap.add_argument("--workload", default="solvation", choices=["solvation", "binding", "gradient"])
-    ap.add_argument("--grad-config", type=int, default=5, choices=[3, 5])
+    ap.add_argument("--grad-panels", type=int, default=327680, choices=[81920, 327680])
     ap.add_argument("--triples", type=int, default=16)
     ap.add_argument("--leaf", type=int, default=0, help="treecode leaf size (0 = the workload's)")
     ap.add_argument("--autotune", type=float, default=0.0,
@@ -170,7 +170,7 @@ def build_library():
 
 def workload():
     import gen
-    return gen.config3()
+    return gen.bumpy_r14_81920()
 
 
 def solver_kwargs(pr, op, residual_op):
@@ -235,7 +235,7 @@ def run_binding(args, local):
     build_library()
     import paper_1810_03698_gb300 as bp
 
-    triples = gen.config4(n_triples=args.triples)
+    triples = gen.binding_triples(n_triples=args.triples)
     probs = [p for t in triples for p in t]
     res_op = args.residual_op or args.op
     kw = dict(op=args.op, residual_op=res_op)
@@ -301,7 +301,7 @@ def run_gradient(args, local):
     build_library()
     import paper_1810_03698_gb300 as bp
 
-    pr = gen.config5() if args.grad_config == 5 else gen.config3()
+    pr = gen.bumpy_r24_327680() if args.grad_panels == 327680 else gen.bumpy_r14_81920()
     res_op = args.residual_op or args.op
     s = bp.problem_solver(pr, device=local, op=args.op, residual_op=res_op)
     stream = torch.cuda.current_stream()

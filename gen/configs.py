@@ -60,7 +60,7 @@ class Problem:
         return int(self.tris.shape[0])
 
 
-def config1() -> Problem:
+def sphere_r4_1280() -> Problem:
     """Sphere R=4, subdivision 3; charge+dipole at the centre, polarizable charge at (1.5,0,0)."""
     v, f = icosphere(4.0, 3)
     sites = Sites(
@@ -87,7 +87,7 @@ def sphere_random(radius: float, subdiv: int, n_sites: int, r_sites: float, min_
                    meta={"radius": radius, "subdiv": subdiv, "kind": "sphere"})
 
 
-def config2() -> Problem:
+def sphere_r10_20480() -> Problem:
     """Sphere R=10, subdivision 5 (20,480 panels), 100 sites uniform in r <= 8, min separation 1.5."""
     pr = sphere_random(10.0, 5, 100, 8.0, 1.5, 2)
     pr.params = Params(gmres_tol=1e-8, scf_tol=1e-8, theta=0.5, order=5)
@@ -118,14 +118,14 @@ def bumpy_problem(radius: float, subdiv: int, n_sites: int, seed_index: int,
 DENSE_ALPHA = (0.25, 0.75)
 
 
-def config3() -> Problem:
+def bumpy_r14_81920() -> Problem:
     """Bumpy surface R=14, subdivision 6 (81,920 panels), 2,000 sites; tree theta=0.5, P=5."""
     pr = bumpy_problem(14.0, 6, 2000, 3, alpha_range=DENSE_ALPHA)
     pr.params = Params(gmres_tol=1e-6, scf_tol=1e-6, theta=0.5, order=5)
     return pr
 
 
-def config5() -> Problem:
+def bumpy_r24_327680() -> Problem:
     """Bumpy surface R=24, subdivision 7 (327,680 panels), 10,000 sites."""
     pr = bumpy_problem(24.0, 7, 10000, 5, alpha_range=DENSE_ALPHA)
     pr.params = Params(gmres_tol=1e-6, scf_tol=1e-6, theta=0.5, order=5)
@@ -161,11 +161,11 @@ def two_body(a: Problem, b: Problem, gap: float = 3.0) -> Problem:
 
 # Sites per body of the binding workload: 0.06 per A^3 of the ball of radius R,
 # clamped to [50, 2000].  Coarse meshes need a wider site-free shell (2 sqrt(A_max)),
-# which config 3's density of 0.17 per A^3 would not leave room for.
+# which the 81,920-panel workload's density of 0.17 per A^3 would not leave room for.
 TRIPLE_SITE_DENSITY = 0.06
 
 
-def config4(n_triples: int = 16, subdivs=(3, 4, 5, 6), radius=(6.0, 14.0)):
+def binding_triples(n_triples: int = 16, subdivs=(3, 4, 5, 6), radius=(6.0, 14.0)):
     """Binding workload: ``n_triples`` triples (A, B, AB).  Per body: subdivision uniform
     over ``subdivs``, R ~ U(radius), sites proportional to the volume; AB puts B 3 A
     from A along x.  Returns a list of (A, B, AB)."""
@@ -196,4 +196,4 @@ def with_params(pr: Problem, **kw) -> Problem:
     return replace(pr, params=replace(pr.params, **kw))
 
 
-CONFIGS = {1: config1, 2: config2, 3: config3, 5: config5}
+WORKLOADS = {f.__name__: f for f in (sphere_r4_1280, sphere_r10_20480, bumpy_r14_81920, bumpy_r24_327680)}

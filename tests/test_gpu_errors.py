@@ -76,7 +76,7 @@ def test_bad_sites(bp):
 
 
 def test_not_converged_is_reported(bp):
-    pr = gen.with_params(gen.config1(), scf_maxit=2)
+    pr = gen.with_params(gen.sphere_r4_1280(), scf_maxit=2)
     s = bp.problem_solver(pr)
     out = s.solve(allow_unconverged=True)
     assert out["status"] == 4

@@ -25,13 +25,14 @@ def bp():
     return mod
 
 
-@pytest.fixture(scope="module", params=[2, 3])
+@pytest.fixture(scope="module", params=[("sphere_r10_20480", 2), ("bumpy_r14_81920", 3)], ids=lambda p: p[0])
 def big(request, bp):
-    pr = gen.CONFIGS[request.param]()
+    name, seed = request.param
+    pr = gen.WORKLOADS[name]()
     par = pr.params
     mesh = bem.build_mesh(pr.verts, pr.tris, par.gauss_k, par.near_factor)
     s = bp.problem_solver(pr, leaf=256, theta=0.5, order=5)
-    rng = np.random.default_rng(100 + request.param)
+    rng = np.random.default_rng(100 + seed)
     rows = np.sort(rng.choice(mesh.n, size=24, replace=False))
     x = rng.normal(size=2 * mesh.n)
     y1, y2 = bem.matvec_rows(mesh, x, rows, par.eps_in, par.eps_out, par.kappa)

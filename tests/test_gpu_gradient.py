@@ -198,7 +198,7 @@ def test_adjoint_identity_fullsize(bp, op, bar):
     """<y, A x> = <A^T y, x> on the 20,480-panel sphere with 100 sites: to rounding for
     the direct form; for the treecode the two products are separate approximations, each
     within the treecode's error."""
-    pr = gen.config2()
+    pr = gen.sphere_r10_20480()
     s = bp.problem_solver(pr, theta=0.5, order=5)
     n = pr.n_panels
     g = np.random.default_rng(34)

@@ -152,7 +152,7 @@ def test_triple_as_three_systems(bp, triple, op):
 
 
 def test_uneven_batch_matches_separate_solves(bp):
-    triples = gen.config4(n_triples=2, subdivs=(3, 4), radius=(6.0, 9.0))
+    triples = gen.binding_triples(n_triples=2, subdivs=(3, 4), radius=(6.0, 9.0))
     probs = [p for t in triples for p in t]
     kw = dict(op="fp32_tree", residual_op="fp64_tree", leaf=128, gmres_tol=1e-8, scf_tol=1e-8)
     s = bp.batch_solver(probs, **kw)
@@ -164,7 +164,7 @@ def test_uneven_batch_matches_separate_solves(bp):
 
 
 def test_uneven_batch_matvec_rows_vs_oracle(bp):
-    triples = gen.config4(n_triples=2, subdivs=(3, 4), radius=(6.0, 9.0))
+    triples = gen.binding_triples(n_triples=2, subdivs=(3, 4), radius=(6.0, 9.0))
     probs = [p for t in triples for p in t]
     s = bp.batch_solver(probs)
     n_tot = sum(p.n_panels for p in probs)

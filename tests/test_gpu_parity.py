@@ -41,7 +41,7 @@ def _relmax(a, b):
 
 
 CASES = {
-    "sphere1280": lambda: gen.config1(),
+    "sphere1280": lambda: gen.sphere_r4_1280(),
     "bumpy1280": lambda: gen.small_bumpy(3, 40, 8.0),
 }
 
@@ -166,7 +166,7 @@ def test_solvation_fp64_direct_matches_oracle(bp, name):
 
 def test_sor_iterations_match_oracle_sor(bp):
     """Same SCF recursion (mu = 0, SOR w = 0.7, RMS test) gives the same iteration counts."""
-    pr = gen.with_params(gen.config1(), gmres_tol=1e-13)
+    pr = gen.with_params(gen.sphere_r4_1280(), gmres_tol=1e-13)
     ref = mp.solvation(pr)
     s = bp.problem_solver(pr, op="fp64_direct", residual_op="fp64_direct")
     out = s.solve()
@@ -177,7 +177,7 @@ def test_sor_iterations_match_oracle_sor(bp):
 
 def test_fp32_direct_with_fp64_refinement(bp):
     """FP32 pair kernels inside GMRES, FP64 residual and site kernels: FP64-level result."""
-    pr = _tight(gen.config1())
+    pr = _tight(gen.sphere_r4_1280())
     ref = mp.solvation(pr, direct_polarization=True)
     s = bp.problem_solver(pr, op="fp32_direct", residual_op="fp64_direct", inner_tol=1e-4)
     out = s.solve()
@@ -185,7 +185,7 @@ def test_fp32_direct_with_fp64_refinement(bp):
 
 
 def test_fp32_direct_plain(bp):
-    pr = gen.with_params(gen.config1(), gmres_tol=1e-7, scf_tol=1e-8)
+    pr = gen.with_params(gen.sphere_r4_1280(), gmres_tol=1e-7, scf_tol=1e-8)
     ref = mp.solvation(pr, direct_polarization=True)
     s = bp.problem_solver(pr, op="fp32_direct", residual_op="fp32_direct")
     out = s.solve()
