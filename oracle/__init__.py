@@ -15,7 +15,8 @@ multipole  multipole tensors, RHS (Eq. rhs_multipole), fields at sites, Thole
            damping, SCF (SOR) and its direct counterpart, energy (Eq.
            energy_multipole_polarizable), solvation energy; several bodies in one
            solvent (Sec. "Calculation of the binding energy")
-kirkwood   closed-form reaction field of a dielectric sphere in salt water
+kirkwood   closed-form reaction field of a dielectric sphere in salt water, with or
+           without a Stern (ion-exclusion) layer
 gradient   dDelta G_solv / d(site positions, q, d, Q): five-point differences of
            the solvation energy at the exact induced-dipole fixed point
 

@@ -3,8 +3,8 @@ and Ponder's multipole extension), used to pin the discrete BEM solution
 (Sec. "Spherical cavity": the BEM error must fall with the mean panel area).
 
 Sphere of radius a centred at the origin, permittivity eps1 inside, eps2 and
-inverse Debye length kappa outside, no Stern layer.  For a unit charge at s
-inside, the reaction potential at r inside is
+inverse Debye length kappa outside.  For a unit charge at s inside, the reaction
+potential at r inside is
 
     G_R(r, s) = 1/(4 pi a) sum_n f_n T_n(r/a, s/a),
     T_n(r, s) = (|r||s|)^n P_n(r^ . s^),
@@ -12,7 +12,16 @@ inside, the reaction potential at r inside is
     g_n = x k_n'(x) / k_n(x),  x = kappa a,
 
 (k_n the modified spherical Bessel function of the second kind), obtained by
-matching the interior and exterior solutions of Eq. (pde) at r = a.  T_n obeys
+matching the interior and exterior solutions of Eq. (pde) at r = a.  With a Stern
+(ion-exclusion) layer a < r < b of permittivity eps2 and no ions, as in the sphere
+test of Sec. "Spherical cavity" (a = 4, b = 5), the layer's solution
+C r^n + D r^-(n+1) is matched to the screened exterior at r = b and g_n becomes its
+logarithmic derivative r phi'/phi at r = a:
+
+    h_n = -(n+1) + (2n+1) u_n,   u_n = delta_n c_n / (delta_n c_n - (2n+1+delta_n)),
+    delta_n = -(n+1) - g_n(kappa b) >= 0,   c_n = (a/b)^(2n+1),
+
+which is g_n(kappa a) when b = a and -(n+1) (plain Laplace decay) when kappa = 0.  T_n obeys
 (n+1) T_{n+1} = (2n+1)(r . s) T_n - n |r|^2 |s|^2 T_{n-1}; it is a polynomial in
 r and s, so every derivative needed here is evaluated exactly by carrying
 truncated bivariate Taylor jets (in eps along a direction u for r, and in
@@ -46,8 +55,21 @@ def g_coeffs(nmax: int, x: float):
     return g
 
 
-def f_coeffs(nmax, eps1, eps2, kappa, a):
-    g = g_coeffs(nmax, kappa * a)
+def h_coeffs(nmax: int, kappa: float, a: float, b: float):
+    """r phi'/phi at r = a+ of the order-n solution in a Stern layer a < r < b (no ions)
+    matched at r = b to the screened exterior; n = 0..nmax."""
+    if not b >= a:
+        raise ValueError("the Stern radius b must be >= a")
+    n = np.arange(nmax + 1, dtype=np.float64)
+    delta = -(n + 1.0) - g_coeffs(nmax, kappa * b)
+    c = np.exp((2.0 * n + 1.0) * np.log(a / b))       # (a/b)^(2n+1), underflows to 0
+    u = delta * c / (delta * c - (2.0 * n + 1.0 + delta))
+    return -(n + 1.0) + (2.0 * n + 1.0) * u
+
+
+def f_coeffs(nmax, eps1, eps2, kappa, a, b=None):
+    """f_n of the reaction Green's function; b = Stern radius (None: no layer)."""
+    g = g_coeffs(nmax, kappa * a) if b is None else h_coeffs(nmax, kappa, a, b)
     n = np.arange(nmax + 1, dtype=np.float64)
     return ((n + 1.0) * eps1 + eps2 * g) / (eps1 * (n * eps1 - eps2 * g))
 
@@ -132,8 +154,9 @@ def _apply(pos_r, terms_r, pos_s, terms_s, f, a, pairs):
     return out
 
 
-def solvation(sites, a, eps1, eps2, kappa, thole_a, nmax=None, polarizable=True):
-    """Exact Delta G_solv (kcal/mol) of the sites in the sphere, with induced dipoles.
+def solvation(sites, a, eps1, eps2, kappa, thole_a, nmax=None, polarizable=True, b=None):
+    """Exact Delta G_solv (kcal/mol) of the sites in the sphere, with induced dipoles;
+    b = radius of the Stern layer's outer surface (None: no layer).
 
     Induced dipoles solve mu = 4 pi alpha (E_reac + E_mult) directly; the
     multipole-multipole terms use the oracle's free-space tensors.
@@ -146,7 +169,7 @@ def solvation(sites, a, eps1, eps2, kappa, thole_a, nmax=None, polarizable=True)
         nmax = 20
         while (nmax ** 4) * rmax ** (2 * nmax) > 1e-18 and nmax < 2000:
             nmax += 10
-    f = f_coeffs(nmax, eps1, eps2, kappa, a)
+    f = f_coeffs(nmax, eps1, eps2, kappa, a, b)
     four_pi_alpha = FOUR_PI * sites.alpha
     pairs = [(l, m) for l in range(ns) for m in range(ns)]
     li = np.array([p[0] for p in pairs])
@@ -205,3 +228,12 @@ def solvation(sites, a, eps1, eps2, kappa, thole_a, nmax=None, polarizable=True)
 def born(q, a, eps1, eps2, kappa):
     """Born ion at the centre: (q^2 / (8 pi a)) (1/(eps2 (1 + kappa a)) - 1/eps1), in kcal/mol."""
     return q * q / (8.0 * np.pi * a) * (1.0 / (eps2 * (1.0 + kappa * a)) - 1.0 / eps1) * mp.KCAL_PER_UNIT
+
+
+def born_stern(q, a, b, eps1, eps2, kappa):
+    """Ion at the centre of a sphere of radius a with a Stern layer to radius b (kcal/mol):
+    region potentials q/(4 pi eps r) + const matched at r = a and r = b to the screened
+    q exp(-kappa (r - b)) / (4 pi eps2 (1 + kappa b) r) outside, which leaves the
+    reaction potential (q / 4 pi) (1/(eps2 a) - 1/(eps1 a) - kappa/(eps2 (1 + kappa b)))."""
+    phi = q / (4.0 * np.pi) * (1.0 / (eps2 * a) - 1.0 / (eps1 * a) - kappa / (eps2 * (1.0 + kappa * b)))
+    return 0.5 * q * phi * mp.KCAL_PER_UNIT

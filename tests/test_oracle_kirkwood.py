@@ -141,3 +141,56 @@ def test_single_moment_off_centre_vs_kirkwood(kind):
     assert 3.0 < e[0] / e[1] < 5.0
     rich = vals[1] + (vals[1] - vals[0]) / 3.0
     assert abs(rich - exact) < 3e-3 * abs(exact)
+
+
+# ---------------------------------------------------------------- Stern layer (a < r < b, no ions)
+
+def _stern_order_n_by_linear_solve(n, eps1, eps2, kappa, a, b):
+    """Reaction coefficient B of phi_1 = r^-(n+1)/eps1 + B r^n for one Legendre order, from the
+    four interface conditions (continuity of phi and of eps dphi/dr at r = a and at r = b) solved
+    as a 4 x 4 linear system in (B, C, D, F), with phi_2 = C r^n + D r^-(n+1) in the layer and
+    phi_3 = F k_n(kappa r) outside (scipy's k_n)."""
+    kn = special.spherical_kn(n, kappa * b)
+    dkn = kappa * special.spherical_kn(n, kappa * b, derivative=True)
+    A = np.array([
+        [a ** n, -a ** n, -a ** -(n + 1.0), 0.0],
+        [eps1 * n * a ** (n - 1.0), -eps2 * n * a ** (n - 1.0), eps2 * (n + 1.0) * a ** -(n + 2.0), 0.0],
+        [0.0, b ** n, b ** -(n + 1.0), -kn],
+        [0.0, eps2 * n * b ** (n - 1.0), -eps2 * (n + 1.0) * b ** -(n + 2.0), -eps2 * dkn],
+    ])
+    rhs = np.array([-a ** -(n + 1.0) / eps1, (n + 1.0) * a ** -(n + 2.0), 0.0, 0.0])
+    return np.linalg.solve(A, rhs)[0]
+
+
+def test_stern_coefficients_vs_interface_linear_solve():
+    for eps1, eps2, kappa, a, b in ((4.0, 80.0, 0.125, 4.0, 5.0), (1.0, 78.3, 0.4, 3.0, 4.5)):
+        f = kw.f_coeffs(12, eps1, eps2, kappa, a, b)
+        for n in range(13):
+            ref = _stern_order_n_by_linear_solve(n, eps1, eps2, kappa, a, b)
+            assert f[n] * a ** -(2.0 * n + 1.0) == pytest.approx(ref, rel=1e-9), n
+
+
+def test_stern_special_cases():
+    # b = a: the layer vanishes; kappa = 0: ions absent, the layer is plain solvent
+    for kappa in (0.0, 0.125, 1.0):
+        assert np.allclose(kw.f_coeffs(60, 4.0, 80.0, kappa, 4.0, 4.0), kw.f_coeffs(60, 4.0, 80.0, kappa, 4.0),
+                           rtol=1e-13, atol=0.0)
+    assert np.allclose(kw.f_coeffs(60, 4.0, 80.0, 0.0, 4.0, 5.0), kw.f_coeffs(60, 4.0, 80.0, 0.0, 4.0),
+                       rtol=1e-13, atol=0.0)
+    # a thicker layer keeps the ions further away: the screening contribution only weakens
+    f4, f5, f9 = (kw.f_coeffs(10, 4.0, 80.0, 0.125, 4.0, b) for b in (4.0, 5.0, 9.0))
+    f_none = kw.f_coeffs(10, 4.0, 80.0, 0.0, 4.0)
+    assert np.all(f4 <= f5) and np.all(f5 <= f9) and np.all(f9 <= f_none + 1e-15)
+    with pytest.raises(ValueError):
+        kw.f_coeffs(3, 4.0, 80.0, 0.125, 4.0, 3.5)
+
+
+def test_stern_born_ion():
+    for eps1, eps2, kappa, a, b in ((4.0, 80.0, 0.125, 4.0, 5.0), (1.0, 78.3, 0.3, 2.0, 3.4)):
+        s = gen.Sites(pos=np.zeros((1, 3)), q=np.array([-0.7]), d=np.zeros((1, 3)), Q=np.zeros((1, 3, 3)),
+                      alpha=np.zeros(1))
+        got, _, _ = kw.solvation(s, a, eps1, eps2, kappa, 0.39, b=b)
+        ref = kw.born_stern(-0.7, a, b, eps1, eps2, kappa)
+        assert got == pytest.approx(ref, rel=1e-12)
+        assert kw.born_stern(-0.7, a, a, eps1, eps2, kappa) == pytest.approx(kw.born(-0.7, a, eps1, eps2, kappa),
+                                                                            rel=1e-13)
