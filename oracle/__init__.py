@@ -19,13 +19,16 @@ kirkwood   closed-form reaction field of a dielectric sphere in salt water, with
            without a Stern (ion-exclusion) layer
 gradient   dDelta G_solv / d(site positions, q, d, Q): five-point differences of
            the solvation energy at the exact induced-dipole fixed point
+stern      Stern (ion-exclusion) layer: three regions bounded by two surfaces, the
+           four Green's-representation rows solved densely (Sec. "Spherical cavity")
 
 Parity pins (see tests/test_oracle_*.py): every function is checked against
 something other than itself -- closed forms (Born, Kirkwood, solid angles),
 Gauss's law, brute-force quadrature, finite differences, exact identities, the
 screened two-ion energy of two bodies, Euler's identity of the gradient.
-Parity unpinned: none of the functions here; the paper's own printed sphere
-value (-65.1131 kcal/mol) is not reproduced because it needs a Stern layer.
+Parity unpinned: none of the functions here.  The paper's own printed sphere value
+(-65.1131 kcal/mol, with a Stern layer) is not reproduced: the orientations and units
+of its multipoles are not stated.
 """
 
-__all__ = ["geometry", "panel", "bem", "multipole", "kirkwood", "gradient"]
+__all__ = ["geometry", "panel", "bem", "multipole", "kirkwood", "gradient", "stern"]

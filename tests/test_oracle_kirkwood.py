@@ -80,7 +80,8 @@ def _problem_on(sub, sites, params, radius=4.0):
 
 @pytest.mark.slow
 def test_oracle_bem_converges_to_kirkwood_sphere_r4():
-    """Config-1 sites: error ~ A (ratio ~4 per subdivision), Richardson within 1e-4."""
+    """The two sites of the 1,280-panel sphere: error ~ A (ratio ~4 per subdivision), Richardson
+    extrapolation within 1e-4."""
     pr = gen.sphere_r4_1280()
     exact, _, _ = kw.solvation(pr.sites, 4.0, 1.0, 80.0, 0.125, 0.39)
     vals = [mp.solvation(_problem_on(s, pr.sites, pr.params)).dG_kcal for s in (2, 3, 4)]
