@@ -53,3 +53,37 @@ def test_default_params_and_validation_without_gpu(libpath):
     assert not h.value
     assert bp.lib.bempol_sizes(None, None, None, None, None, None, None) == 1
     bp.lib.bempol_destroy(None)  # no-op
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every struct of the boundary has the same field offsets and size in the binding's
+    ctypes mirror as the C compiler gives them from include/bempol.h."""
+    import paper_1810_03698_gb300 as bp
+    pairs = [("bempol_params", bp.Params), ("bempol_result", bp.Result), ("bempol_system_result", bp.SystemResult),
+             ("bempol_gradient_info", bp.GradientInfo), ("bempol_tune_result", bp.TuneResult),
+             ("bempol_stats", bp.Stats)]
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "bempol.h"', "int main(void) {"]
+    for cname, cls in pairs:
+        body = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + cname + r"\s*;", src)
+        assert body, cname
+        declared = []
+        for decl in body.group(1).split(";"):
+            parts = [t.strip() for t in decl.strip().split(",") if t.strip()]
+            if parts:
+                declared += [parts[0].split()[-1]] + parts[1:]
+        assert declared == [f for f, _ in cls._fields_], cname
+        lines.append(f'  printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["  return 0;", "}"]
+    prog = tmp_path / "layout.c"
+    prog.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, cls in pairs:
+        assert int(got[cname]) == C.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
