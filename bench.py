@@ -524,6 +524,9 @@ def main():
                  "operator_products_ms": prod_ms / K_, "rhs_ms": stats["rhs_ms"] / K_,
                  "reaction_field_ms": stats["reaction_ms"] / K_, "site_fields_ms": stats["site_field_ms"] / K_}
     breakdown["other_ms"] = breakdown["step_ms"] - sum(v for k, v in breakdown.items() if k != "step_ms")
+    mesh_stats = s.stats()
+    breakdown["set_mesh_phases_ms"] = {k: mesh_stats["mesh_" + k + "_ms"]
+                                       for k in ("validate", "geometry", "blocks", "tree", "near")}
     breakdown["note"] = ("other = GMRES orthogonalisation, near-field corrections and combines, induced-dipole "
                          "updates, energies, host logic; set_mesh/set_sites from one untimed step")
 

@@ -382,6 +382,10 @@ typedef struct {
   double reaction_ms;
   int64_t site_field_calls;    /* multipole fields at the sites inside the induced-dipole iterations */
   double site_field_ms;
+  /* host wall-clock of the last bempol_set_mesh*, by phase (the stream is synchronised at each
+     phase boundary while timing is enabled): closedness check, panel geometry and Morton
+     order, block tables, octree and interaction lists, near table and its integrals */
+  double mesh_validate_ms, mesh_geometry_ms, mesh_blocks_ms, mesh_tree_ms, mesh_near_ms;
 } bempol_stats;
 
 /* Turn event timing on (1) or off (0).  Counting is always on. */

@@ -76,6 +76,8 @@ class Stats(C.Structure):
         ("far_evaluations", C.c_int64), ("tree_products", C.c_int64), ("tree_ms", C.c_double),
         ("rhs_calls", C.c_int64), ("rhs_ms", C.c_double), ("reaction_calls", C.c_int64), ("reaction_ms", C.c_double),
         ("site_field_calls", C.c_int64), ("site_field_ms", C.c_double),
+        ("mesh_validate_ms", C.c_double), ("mesh_geometry_ms", C.c_double), ("mesh_blocks_ms", C.c_double),
+        ("mesh_tree_ms", C.c_double), ("mesh_near_ms", C.c_double),
     ]
 
 

@@ -292,10 +292,23 @@ void set_mesh_impl(Ctx* c, int64_t nv, const double* verts, int64_t nt, const in
   size_scalars(*c);
   DBuf<double> dv;
   to_device(dv, verts, 3 * (size_t)nv, where, s);
+  auto t = std::chrono::steady_clock::now();
+  auto lap = [&](int k) {
+    if (c->stats_on) BP_CUDA(cudaStreamSynchronize(s));
+    const auto now = std::chrono::steady_clock::now();
+    c->mesh_ms[k] = std::chrono::duration<double, std::milli>(now - t).count();
+    t = now;
+  };
+  validate_closed(ht.data(), c->n, c->nv, grp);
+  lap(0);
   build_geometry(*c, dv.p, ht.data(), grp, s);
+  lap(1);
   build_blocks(*c, s);
+  lap(2);
   build_tree(*c, s);  // the octree also narrows the near-pair search
+  lap(3);
   build_near(*c, s);
+  lap(4);
   size_t len = 2 * (size_t)c->n;
   c->vec_a.alloc(len);
   c->vec_b.alloc(len);
@@ -675,6 +688,11 @@ bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
     out->reaction_ms = c->stat_ms[4];
     out->site_field_calls = c->stat_launches[5];
     out->site_field_ms = c->stat_ms[5];
+    out->mesh_validate_ms = c->mesh_ms[0];
+    out->mesh_geometry_ms = c->mesh_ms[1];
+    out->mesh_blocks_ms = c->mesh_ms[2];
+    out->mesh_tree_ms = c->mesh_ms[3];
+    out->mesh_near_ms = c->mesh_ms[4];
     if (reset) {
       c->launches_at_reset = g_launches.load();
       for (int k = 0; k < Ctx::NKIND; ++k) {

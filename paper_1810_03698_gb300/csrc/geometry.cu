@@ -148,6 +148,8 @@ __global__ void gather_geometry(const int* __restrict__ perm, int n, int K, cons
 
 // Every directed edge must appear once and its reverse once, in a triangle of the
 // same group: each body is a closed, consistently oriented surface of its own.
+}  // namespace
+
 // Every directed edge a->b of the mesh must be used once and have its opposite b->a,
 // on a triangle of the same body.  The outgoing edges of each vertex are bucketed by a
 // counting sort and sorted by their end vertex (buckets are small), so duplicates are
@@ -187,13 +189,10 @@ void validate_closed(const int* tris, int n, int nv, const std::vector<int>& grp
     }
 }
 
-}  // namespace
-
 void build_geometry(Ctx& c, const double* d_verts, const int* h_tris_for_check, const std::vector<int>& h_group,
                     cudaStream_t s) {
   const int n = c.n;
   const int G = c.ngroup;
-  validate_closed(h_tris_for_check, n, c.nv, h_group);
   DBuf<int> d_tris;
   d_tris.alloc(3 * (size_t)n);
   BP_CUDA(cudaMemcpyAsync(d_tris.p, h_tris_for_check, 3 * sizeof(int) * (size_t)n, cudaMemcpyHostToDevice, s));

@@ -237,6 +237,10 @@ struct Ctx {
                // 4 reaction field at the sites, 5 multipole fields at the sites
   };
   static constexpr int NKIND = 6;
+  // host wall-clock of the phases of the last set_mesh (validation, geometry and Morton
+  // order, block tables, tree, near table); the stream is synchronised at each phase
+  // boundary only while stats are on
+  double mesh_ms[5] = {};
   std::vector<Timed> timed;
   double stat_ms[NKIND] = {};
   long long stat_launches[NKIND] = {};
@@ -265,6 +269,8 @@ inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
 int num_sms(int device);
 
 // geometry.cu
+// closed, consistently oriented surfaces, no edge shared by two bodies (fails with BEMPOL_ERR_MESH)
+void validate_closed(const int* tris, int n, int nv, const std::vector<int>& grp);
 void build_geometry(Ctx& c, const double* d_verts, const int* h_tris, const std::vector<int>& h_group,
                     cudaStream_t s);
 void build_blocks(Ctx& c, cudaStream_t s);
