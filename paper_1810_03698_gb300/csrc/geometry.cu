@@ -146,8 +146,6 @@ __global__ void gather_geometry(const int* __restrict__ perm, int n, int K, cons
   }
 }
 
-// Every directed edge must appear once and its reverse once, in a triangle of the
-// same group: each body is a closed, consistently oriented surface of its own.
 }  // namespace
 
 // Every directed edge a->b of the mesh must be used once and have its opposite b->a,
