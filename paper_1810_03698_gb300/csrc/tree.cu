@@ -656,6 +656,7 @@ void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vecto
 
 void build_tree(Ctx& c, cudaStream_t s) {
   Tree& T = c.tree;
+  c.ensure_aux();  // the products' side stream, created here rather than inside a product
   build_topology(c);
   upload(T.begin, T.h_begin, s);
   upload(T.end, T.h_end, s);
