@@ -2,9 +2,9 @@
 
 The surface is discretised into flat triangles with piecewise-constant phi and
 dphi/dn, collocated at the panel centroids.  Far-away panels are integrated
-with 1, 3 or 4 Gauss nodes; panels closer than ``near_factor * sqrt(A_i)`` to
-the collocation point x_i (A_i the area of the collocation point's own panel)
-are integrated accurately (see ``panel.py``).
+with 1, 3 or 4 Gauss nodes (19 for the paper's nearly-singular variant); panels
+closer than ``near_factor * sqrt(A_i)`` to the collocation point x_i (A_i the area of
+the collocation point's own panel) are integrated accurately (see ``panel.py``).
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 """
@@ -52,15 +52,65 @@ def gauss_rule(k: int):
     elif k == 4:
         lam = np.array([[1 / 3, 1 / 3, 1 / 3], [0.6, 0.2, 0.2], [0.2, 0.6, 0.2], [0.2, 0.2, 0.6]])
         w = np.array([-27.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0, 25.0 / 48.0])
+    elif k == 19:
+        lam, w = _rule19()
     else:
-        raise ValueError("gauss_k must be 1, 3 or 4")
+        raise ValueError("gauss_k must be 1, 3, 4 or 19")
     return lam, w
+
+
+def _rule19():
+    """A fully symmetric 19-node rule of degree 8 with positive weights and interior nodes,
+    for the paper's nearly-singular pairs ("finer quadrature rules with 19 Gauss nodes",
+    Sec. "Comparison with Tinker-APBS"; the paper gives no table).  Orbits: the centroid,
+    four (a, a, 1-2a) orbits of 3 nodes and one (b, c, 1-b-c) orbit of 6 nodes; their 12
+    parameters solve the 10 moment equations of the S3-invariant polynomials of degree
+    <= 8, int l1^i l2^j l3^k dA / A = 2 i! j! k! / (i+j+k+2)!, by least squares from seeded
+    starting points (the first solution with positive weights and interior nodes is kept;
+    the system is underdetermined, so this is one member of the degree-8 family).  Cached."""
+    global _RULE19
+    if _RULE19 is not None:
+        return _RULE19
+    from math import factorial
+    from scipy.optimize import least_squares
+
+    def nodes(p):
+        w0, a1, a2, a3, a4, w1, w2, w3, w4, b, c, w5 = p
+        lam, w = [(1 / 3, 1 / 3, 1 / 3)], [w0]
+        for a, wa in ((a1, w1), (a2, w2), (a3, w3), (a4, w4)):
+            lam += [(a, a, 1 - 2 * a), (a, 1 - 2 * a, a), (1 - 2 * a, a, a)]
+            w += [wa / 3] * 3
+        d = 1 - b - c
+        lam += [(b, c, d), (b, d, c), (c, b, d), (c, d, b), (d, b, c), (d, c, b)]
+        w += [w5 / 6] * 6
+        return np.array(lam), np.array(w)
+
+    mons = [(i, j, k) for i in range(9) for j in range(9) for k in range(9) if i + j + k <= 8 and i >= j >= k]
+    exact = np.array([2.0 * factorial(i) * factorial(j) * factorial(k) / factorial(i + j + k + 2) for i, j, k in mons])
+
+    def resid(p):
+        lam, w = nodes(p)
+        return np.array([np.sum(w * lam[:, 0] ** i * lam[:, 1] ** j * lam[:, 2] ** k) for i, j, k in mons]) - exact
+
+    rng = np.random.default_rng(0)
+    for _ in range(1000):
+        p0 = np.array([0.1, *rng.uniform(0.02, 0.49, 4), 0.15, 0.15, 0.15, 0.15, rng.uniform(0.01, 0.3),
+                       rng.uniform(0.2, 0.5), 0.2])
+        r = least_squares(resid, p0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
+        lam, w = nodes(r.x)
+        if np.abs(resid(r.x)).max() < 1e-14 and w.min() > 0 and lam.min() > 0:
+            _RULE19 = (lam, w)
+            return _RULE19
+    raise RuntimeError("no 19-node degree-8 rule found")
+
+
+_RULE19 = None
 
 
 def gauss_points(verts: np.ndarray, tris: np.ndarray, k: int):
     """Gauss-node positions y_jg [N, K, 3] and weights W_jg = w_g * A_j [N, K].
 
-    The centroid node of the K=1 and K=4 rules is placed at the panel centroid
+    The centroid node of the K=1, K=4 and K=19 rules is placed at the panel centroid
     itself, computed exactly as the collocation point ((v0 + v1) + v2) / 3: the
     node then coincides with its own panel's collocation point to the last bit,
     so that pair has r = 0 and contributes nothing (a product form
@@ -72,7 +122,7 @@ def gauss_points(verts: np.ndarray, tris: np.ndarray, k: int):
     v2 = verts[tris[:, 2]]
     y = (lam[None, :, 0, None] * v0[:, None, :] + lam[None, :, 1, None] * v1[:, None, :]
          + lam[None, :, 2, None] * v2[:, None, :])
-    if k in (1, 4):
+    if k in (1, 4, 19):
         y[:, 0, :] = (v0 + v1 + v2) / 3.0
     _, _, area = panel_geometry(verts, tris)
     return y, w[None, :] * area[:, None]

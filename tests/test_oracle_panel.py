@@ -124,12 +124,12 @@ def test_double_layer_jump_across_panel():
 
 
 def test_gauss_rules_exactness():
-    """The K=1, 3, 4 rules integrate polynomials of degree 1, 2, 3 exactly over a triangle."""
+    """The K=1, 3, 4, 19 rules integrate polynomials of degree 1, 2, 3, 8 exactly over a triangle."""
     # exact: int over the unit right triangle of x^i y^j = i! j! / (i + j + 2)!
     from math import factorial
     v = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     f = np.array([[0, 1, 2]], dtype=np.int32)
-    for k, deg in ((1, 1), (3, 2), (4, 3)):
+    for k, deg in ((1, 1), (3, 2), (4, 3), (19, 8)):
         y, w = geometry.gauss_points(v, f, k)
         for i in range(deg + 1):
             for j in range(deg + 1 - i):
@@ -139,7 +139,33 @@ def test_gauss_rules_exactness():
         # and not one degree higher (the rule is exactly of that degree)
         got = np.sum(w[0] * y[0, :, 0] ** (deg + 1))
         ref = factorial(deg + 1) / factorial(deg + 3)
-        assert abs(got - ref) > 1e-6
+        assert abs(got - ref) > 1e-8
+    lam, wb = geometry.gauss_rule(19)
+    assert lam.shape == (19, 3) and np.all(wb > 0) and np.all(lam > 0)
+    assert np.allclose(lam.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+
+
+def test_rule19_on_nearly_singular_pairs():
+    """Near a panel (the paper applies 19 nodes within 1.25 sqrt(A) of the collocation point)
+    the 19-node sums approach the exact integrals much faster than the 4-node rule."""
+    a, b, c = TRI
+    tri = np.array([[0, 1, 2]], dtype=np.int32)
+    verts = np.array([a, b, c])
+    n = np.cross(b - a, c - a)
+    area = 0.5 * np.linalg.norm(n)
+    n /= np.linalg.norm(n)
+    cen = (a + b + c) / 3.0
+    err = {}
+    for k in (4, 19):
+        y, w = geometry.gauss_points(verts, tri, k)
+        err[k] = []
+        for dist in (1.25, 2.5):
+            x = cen + dist * np.sqrt(area) * (0.6 * n + 0.8 * (b - a) / np.linalg.norm(b - a))
+            ex = panel.panel_integrals(x[None], a[None], b[None], c[None], 0.125)
+            kp = panel.kpoint_sums(x[None], y, w, n[None], 0.125)
+            err[k].append(max(abs(kp[r][0] - ex[r][0]) / abs(ex[r][0]) for r in range(4)))
+    assert err[19][0] < err[4][0] / 20 and err[19][1] < err[4][1] / 100
+    assert err[19][1] < err[19][0] / 20
 
 
 def test_kpoint_far_converges_to_exact():
