@@ -35,6 +35,7 @@ class Mesh:
     near_ptr: np.ndarray
     near_cols: np.ndarray
     body: np.ndarray       # [N] body of each panel (several closed surfaces in one solvent)
+    near_rule: str = "exact"   # near non-self pairs: "exact" panel integrals or "gauss19" nodes
 
     @property
     def n(self):
@@ -44,15 +45,36 @@ class Mesh:
         return self.body[rows] == self.body[cols]
 
 
-def build_mesh(verts, tris, gauss_k=4, near_factor=2.0, body=None) -> Mesh:
+def build_mesh(verts, tris, gauss_k=4, near_factor=2.0, body=None, near_rule="exact") -> Mesh:
     """Panels, Gauss nodes and near pairs.  With several bodies (closed surfaces
     enclosing separate solute cavities, Sec. "Calculation of the binding energy"),
-    ``body`` gives each panel's body."""
+    ``body`` gives each panel's body.  ``near_rule="gauss19"`` integrates near pairs
+    other than the self panel with the 19-node rule, as the paper's production runs do
+    (Sec. "Comparison with Tinker-APBS"); the self panel stays semi-analytical."""
+    if near_rule not in ("exact", "gauss19"):
+        raise ValueError("near_rule must be 'exact' or 'gauss19'")
     cen, normal, area = geometry.panel_geometry(verts, tris)
     y, w = geometry.gauss_points(verts, tris, gauss_k)
     ptr, cols = geometry.near_pairs(cen, area, near_factor)
     b = np.zeros(tris.shape[0], dtype=np.int32) if body is None else np.asarray(body, dtype=np.int32)
-    return Mesh(verts, tris, cen, normal, area, y, w, ptr, cols, b)
+    return Mesh(verts, tris, cen, normal, area, y, w, ptr, cols, b, near_rule)
+
+
+def near_values(mesh: Mesh, rows, cols, kappa: float):
+    """Near-pair integrals (VL, KL, VY, KY) for targets at the centroids ``rows`` and source
+    panels ``cols``: semi-analytical, or the 19-node rule off the self panel under
+    ``near_rule="gauss19"``."""
+    t = mesh.tris[cols]
+    self_p = rows == cols
+    out = panel.panel_integrals(mesh.cen[rows], mesh.verts[t[:, 0]], mesh.verts[t[:, 1]],
+                                mesh.verts[t[:, 2]], kappa, self_panel=self_p)
+    if mesh.near_rule == "gauss19":
+        off = ~self_p
+        y, w = geometry.gauss_points(mesh.verts, mesh.tris[cols[off]], 19)
+        kp = panel.kpoint_sums(mesh.cen[rows[off]], y, w, mesh.normal[cols[off]], kappa)
+        for o, v in zip(out, kp):
+            o[off] = v
+    return out
 
 
 def near_rows_cols(mesh: Mesh):
@@ -61,11 +83,9 @@ def near_rows_cols(mesh: Mesh):
 
 
 def near_exact(mesh: Mesh, kappa: float):
-    """Accurate panel integrals for every near pair, in CSR order: (VL, KL, VY, KY)."""
+    """Near-pair integrals (``near_values``) for every near pair, in CSR order: (VL, KL, VY, KY)."""
     rows, cols = near_rows_cols(mesh)
-    t = mesh.tris[cols]
-    return panel.panel_integrals(mesh.cen[rows], mesh.verts[t[:, 0]], mesh.verts[t[:, 1]],
-                                 mesh.verts[t[:, 2]], kappa, self_panel=(rows == cols))
+    return near_values(mesh, rows, cols, kappa)
 
 
 def near_kpoint(mesh: Mesh, kappa: float):
@@ -160,10 +180,7 @@ def matvec_rows(mesh: Mesh, x: np.ndarray, rows: np.ndarray, eps_in, eps_out, ka
         xi = np.repeat(mesh.cen[i][None], n, axis=0)
         vl, kl, vy, ky = panel.kpoint_sums(xi, mesh.ygauss, mesh.wgauss, mesh.normal, kappa)
         cols = mesh.near_cols[mesh.near_ptr[i]:mesh.near_ptr[i + 1]].astype(np.int64)
-        tv = mesh.tris[cols]
-        ex = panel.panel_integrals(np.repeat(mesh.cen[i][None], cols.size, axis=0),
-                                   mesh.verts[tv[:, 0]], mesh.verts[tv[:, 1]], mesh.verts[tv[:, 2]],
-                                   kappa, self_panel=(cols == i))
+        ex = near_values(mesh, np.full(cols.size, i, dtype=np.int64), cols, kappa)
         vl[cols], kl[cols], vy[cols], ky[cols] = ex
         other = mesh.body != mesh.body[i]
         vl[other] = 0.0

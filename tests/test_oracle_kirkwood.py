@@ -195,3 +195,29 @@ def test_stern_born_ion():
         assert got == pytest.approx(ref, rel=1e-12)
         assert kw.born_stern(-0.7, a, a, eps1, eps2, kappa) == pytest.approx(kw.born(-0.7, a, eps1, eps2, kappa),
                                                                             rel=1e-13)
+
+
+def test_paper_production_near_settings_converge():
+    """One far node and 19 nodes for near pairs within 1.25 sqrt(A) (Sec. "Comparison with
+    Tinker-APBS") still converge at O(A) to the closed form; with 4 far nodes the 19-node near
+    rule moves the discrete Delta G by far less than the discretisation error."""
+    from oracle import bem
+    pr = gen.sphere_r4_1280()
+    par = pr.params
+    exact, _, _ = kw.solvation(pr.sites, 4.0, par.eps_in, par.eps_out, par.kappa, par.thole_a)
+
+    def dG(sub, k, nf, rule):
+        v, f = gen.icosphere(4.0, sub)
+        m = bem.build_mesh(v, f, k, nf, near_rule=rule)
+        solver = bem.DenseSolver(m, par.eps_in, par.eps_out, par.kappa)
+        solver.mesh = m
+        return mp.solvation(gen.Problem("sphere", v, f, pr.sites, par), solver=solver,
+                            direct_polarization=True).dG_kcal
+
+    vals = [dG(s, 1, 1.25, "gauss19") for s in (2, 3)]
+    e = np.abs(np.array(vals) - exact)
+    assert 3.0 < e[0] / e[1] < 4.5
+    rich = vals[1] + (vals[1] - vals[0]) / 3.0
+    assert abs(rich - exact) < 3e-3 * abs(exact)
+    g19, gex = dG(3, 4, 2.0, "gauss19"), dG(3, 4, 2.0, "exact")
+    assert abs(g19 - gex) < 1e-2 * abs(gex - exact)
