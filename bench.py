@@ -12,7 +12,10 @@ Thole fields, SOR) and the energy.  Inputs are seeded synthetic data.
 Also measured: the matvec alone for the chosen operator and for the FP64 direct
 operator (effective interactions/s = N * N * K / t), the end-to-end step through
 the C ABI from pinned host buffers, and the FP64 oracle on the host cores on a
-bounded sample (the CPU baseline).
+bounded sample (the CPU baseline).  The roofline unit is one treecode product, fork
+to join: its near and far kernels run concurrently on two streams.  `breakdown`
+splits a step into operator products, set_mesh (with its phases), set_sites,
+right-hand sides, reaction fields, site multipole fields and the rest.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] ; for N > 1 under
 torch.distributed.run each rank solves its own replica (independent problems, no
