@@ -49,8 +49,25 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("time per ΔG_solv + matvec Ginter/s, FP32-tree vs FP64-direct, 81,920 panels")
 UNIT = "s/ΔG_solv"
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
-FLOPS_PER_PAIR = 28   # FP32 flops (FMA = 2) of one Gauss-node/target pair in the pair kernel
+# FP32 peak from unit counts (SMs x FP32 lanes x FMA x max SM clock): only the fallback
+# when the measured peak (bempol_measure_peaks) is switched off
+FP32_PEAK_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+# FP32 flops (FMA = 2) of one (target, Gauss node) pair of Eq. integral_eq's four kernels,
+# counted from the pair formula: R = x - y (3), R^2 (1 mul + 2 fma = 5), R = R^2 / |R| (1),
+# kappa R log2 e (1), m / R (1), V_L and V_Y accumulations (2 fma = 4), d . R (1 mul + 2 fma
+# = 5), d . R / R^3 (3), K_L accumulation (2), (1 + kappa R) (2), its product (1) and the
+# K_Y accumulation (2): 30 flops, plus 2 special-function operations (1/sqrt, 2^x)
+FLOPS_PER_PAIR = 30
+# Products (operator applications) of one Delta G_solv on the 81,920-panel workload in
+# the headline form, as the GPU solve reports them (FP32 treecode products of the
+# induced-dipole iterations and the final solve's inner GMRES, plus its FP64 residuals).
+# The CPU baseline prices one Delta G as this many FP64 matrix-vector products of the
+# oracle in both arms; the native arm also reports its own count beside it.
+PRODUCTS_PER_DG = 763
+# DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
+# its kernels from one ncu capture; None until the kernels as built have been captured.
+TRAFFIC_PER_PRODUCT_BYTES = None
+TRAFFIC_BASIS = None
 
 
 def far_flops(P):
@@ -76,12 +93,20 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--op", default="fp32_tree")
-    ap.add_argument("--residual-op", default=None)
+    ap.add_argument("--residual-op", default=None,
+                    help="operator of the FP64 residual of iterative refinement (= --op: no refinement); "
+                         "default fp64_tree for the solvation and gradient workloads, --op for binding")
+    ap.add_argument("--refine-scope", default="final", choices=["final", "every"],
+                    help="refine only the final (energy) solve, or every solve of the induced-dipole iterations")
+    ap.add_argument("--plain-steps", type=int, default=2,
+                    help="untimed-in-value steps of the plain form (residual_op = op) reported beside the headline")
+    ap.add_argument("--no-peaks", action="store_true", help="skip the FP32/FP64/MUFU peak measurement")
     ap.add_argument("--matvec-reps", type=int, default=10)
     ap.add_argument("--fp64-reps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-rows", type=int, default=384)
+    ap.add_argument("--cpu-rows", type=int, default=1024, help="oracle rows sampled on all host cores")
+    ap.add_argument("--cpu-rows-1core", type=int, default=64, help="oracle rows sampled on one host core")
     ap.add_argument("--workload", default="solvation", choices=["solvation", "binding", "gradient"])
     ap.add_argument("--grad-panels", type=int, default=327680, choices=[81920, 327680])
     ap.add_argument("--triples", type=int, default=16)
@@ -184,28 +209,110 @@ def solver_kwargs(pr, op, residual_op):
                 thole_a=p.thole_a, op=op, residual_op=residual_op)
 
 
-def cpu_baseline(pr, rows_n, matvecs_per_solve):
-    """FP64 oracle on a bounded sample: rows of the FP64 matvec, extrapolated per Delta G."""
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+_ORACLE_MESH = None
+
+
+def _oracle_init(verts, tris, gauss_k, near_factor):
+    global _ORACLE_MESH
     from oracle import bem
+    _ORACLE_MESH = bem.build_mesh(verts, tris, gauss_k, near_factor)
+
+
+def _oracle_rows(task):
+    from oracle import bem
+    x, rows, eps_in, eps_out, kappa = task
+    return bem.matvec_rows(_ORACLE_MESH, x, rows, eps_in, eps_out, kappa)
+
+
+class OracleSampler:
+    """The FP64 oracle's matrix-vector product on a bounded sample of target rows, on
+    every host core (a spawned process pool, one numpy process per core, each holding
+    the oracle's mesh) and on one core (this process)."""
+
+    def __init__(self, pr, cores=None):
+        import multiprocessing as mp
+        from oracle import bem
+        self.pr = pr
+        par = pr.params
+        t0 = time.time()
+        self.mesh = bem.build_mesh(pr.verts, pr.tris, par.gauss_k, par.near_factor)
+        self.t_mesh = time.time() - t0
+        self.cores = cores or host_cores()
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"   # one thread per worker process
+        self.pool = mp.get_context("spawn").Pool(self.cores, initializer=_oracle_init,
+                                                 initargs=(pr.verts, pr.tris, par.gauss_k, par.near_factor))
+        self.pool.map(_oracle_rows, [(np.zeros(2 * self.mesh.n), np.array([0]), 1.0, 80.0, 0.1)] * self.cores)
+        self.rng = np.random.default_rng(0)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+    def matvec_s(self, rows_n, one_core=False):
+        """Seconds of one full FP64 oracle product, from a sample of rows_n rows."""
+        par = self.pr.params
+        n = self.mesh.n
+        x = self.rng.normal(size=2 * n)
+        rows = np.sort(self.rng.choice(n, size=min(rows_n, n), replace=False))
+        t0 = time.time()
+        if one_core:
+            from oracle import bem
+            bem.matvec_rows(self.mesh, x, rows, par.eps_in, par.eps_out, par.kappa)
+        else:
+            chunks = [c for c in np.array_split(rows, self.cores * 4) if c.size]
+            self.pool.map(_oracle_rows, [(x, c, par.eps_in, par.eps_out, par.kappa) for c in chunks])
+        dt = time.time() - t0
+        return dt * n / rows.size, dt, rows.size
+
+
+def full_oracle_dG_1280():
+    """Seconds of one whole oracle Delta G_solv on the 1,280-panel sphere (dense LU of the
+    2N x 2N system, SOR induced-dipole iteration): measured, not extrapolated."""
+    import gen
+    from oracle import multipole as mp
+    pr = gen.sphere_r4_1280()
     t0 = time.time()
-    par = pr.params
-    mesh = bem.build_mesh(pr.verts, pr.tris, par.gauss_k, par.near_factor)
-    t_mesh = time.time() - t0
-    rng = np.random.default_rng(0)
-    x = rng.normal(size=2 * mesh.n)
-    rows = np.sort(rng.choice(mesh.n, size=min(rows_n, mesh.n), replace=False))
-    t0 = time.time()
-    bem.matvec_rows(mesh, x, rows, par.eps_in, par.eps_out, par.kappa)
-    t_rows = time.time() - t0
-    t_matvec = t_rows * mesh.n / rows.size
-    pairs_per_s = rows.size * mesh.n * par.gauss_k / t_rows
-    return {
-        "value": t_matvec * matvecs_per_solve + t_mesh, "unit": UNIT, "cores": 1, "kind": "oracle",
-        "sample": (f"FP64 oracle matvec on {rows.size} of {mesh.n} target rows ({t_rows:.1f} s), extrapolated to a "
-                   f"full matvec ({t_matvec:.1f} s) x {matvecs_per_solve} matvecs per Delta G (the count the GPU "
-                   f"solve used) + oracle mesh set-up ({t_mesh:.1f} s); numpy elementwise, one core"),
-        "matvec_pairs_per_s": pairs_per_s,
+    r = mp.solvation(pr)
+    return time.time() - t0, r.dG_kcal
+
+
+def cpu_baseline(sampler, rows_n, rows_1core, products, native_products=None, full_small=True):
+    """FP64 oracle on bounded samples: the product's rows on all cores and on one core,
+    priced per Delta G as `products` FP64 products (extrapolated, labelled so), plus one
+    whole 1,280-panel Delta G (not extrapolated)."""
+    t_all, dt_all, nr_all = sampler.matvec_s(rows_n)
+    t_one, dt_one, nr_one = sampler.matvec_s(rows_1core, one_core=True)
+    n = sampler.mesh.n
+    K = sampler.pr.params.gauss_k
+    out = {
+        "value": t_all * products + sampler.t_mesh, "unit": UNIT, "cores": sampler.cores, "kind": "oracle",
+        "sample": (f"FP64 oracle (numpy) matrix-vector product on {nr_all} of {n} target rows over {sampler.cores} "
+                   f"processes ({dt_all:.1f} s), extrapolated to a full product ({t_all:.1f} s) x {products} "
+                   f"products per Delta G_solv + oracle mesh set-up ({sampler.t_mesh:.1f} s); extrapolated"),
+        "products_per_dG": products,
+        "matvec_s_all_cores": t_all,
+        "matvec_pairs_per_s_all_cores": nr_all * n * K / dt_all,
+        "one_core": {"value": t_one * products + sampler.t_mesh, "matvec_s": t_one,
+                     "matvec_pairs_per_s": nr_one * n * K / dt_one,
+                     "sample": f"{nr_one} rows on one core ({dt_one:.1f} s), extrapolated like the all-core figure"},
     }
+    if native_products is not None:
+        out["native_products_per_dG"] = native_products
+    if full_small:
+        t_full, dg = full_oracle_dG_1280()
+        out["full_dG_1280_panels"] = {"s": t_full, "dG_kcal": dg,
+                                      "what": "one whole oracle Delta G_solv, sphere R = 4 A, 1,280 panels, dense "
+                                              "LU + SOR induced dipoles (numpy/LAPACK threads as configured), "
+                                              "measured, not extrapolated"}
+    return out
 
 
 # ---------------------------------------------------------------------------- reference arm
@@ -213,13 +320,16 @@ def run_reference(args, rank):
     if rank != 0:
         return
     pr = workload()
-    matvecs = 400   # matvecs of one FP32-direct Delta G solve on this workload (from the native arm)
+    sampler = OracleSampler(pr)
     times = []
-    for k in range(args.warmup + args.steps):
-        t0 = time.time()
-        cb = cpu_baseline(pr, 64, matvecs)
-        if k >= args.warmup:
-            times.append(cb["value"])
+    try:
+        for k in range(args.warmup + args.steps):
+            t_all, _, _ = sampler.matvec_s(args.cpu_rows)
+            if k >= args.warmup:
+                times.append(t_all * PRODUCTS_PER_DG + sampler.t_mesh)
+        cb = cpu_baseline(sampler, args.cpu_rows, args.cpu_rows_1core, PRODUCTS_PER_DG)
+    finally:
+        sampler.close()
     v = float(np.mean(times))
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
@@ -305,8 +415,8 @@ def run_gradient(args, local):
     import paper_1810_03698_gb300 as bp
 
     pr = gen.bumpy_r24_327680() if args.grad_panels == 327680 else gen.bumpy_r14_81920()
-    res_op = args.residual_op or args.op
-    s = bp.problem_solver(pr, device=local, op=args.op, residual_op=res_op)
+    res_op = args.residual_op or "fp64_tree"
+    s = bp.problem_solver(pr, device=local, op=args.op, residual_op=res_op, refine_scope=args.refine_scope)
     stream = torch.cuda.current_stream()
 
     def ev_time(fn):
@@ -349,7 +459,7 @@ def run_gradient(args, local):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if "fp32" in args.op else "f64",
         "data": "synthetic",
         "config": {"workload": pr.name, "panels": pr.n_panels, "sites": st.n, "op": args.op, "residual_op": res_op,
-                   "theta": pr.params.theta, "order": pr.params.order, "gmres_tol": pr.params.gmres_tol,
+                   "refine_scope": args.refine_scope if res_op != args.op else None, "theta": pr.params.theta, "order": pr.params.order, "gmres_tol": pr.params.gmres_tol,
                    "scf_tol": pr.params.scf_tol},
         "forward_s": float(np.mean(fw)) / 1e3, "gradient_over_forward": float(np.mean(gr) / np.mean(fw)),
         "adjoint": g["info"], "kernels": kst, "dG_solv_kcal": out["dG_solv_kcal"],
@@ -359,6 +469,18 @@ def run_gradient(args, local):
 
 
 # ---------------------------------------------------------------------------- native arm
+def measure_peaks(bp, local, enabled):
+    """FP32/FP64 FMA and MUFU throughput of this GPU from the library's own
+    microbenchmark, with the SM clock sampled while it runs."""
+    if not enabled:
+        return None
+    sampler = ClockSampler(local)
+    sampler.start()
+    pk = bp.measure_peaks(local, iters=262144, reps=5)
+    pk["clocks"] = sampler.stop()
+    return pk
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -382,14 +504,15 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
     build_library()
+    import gen
     import paper_1810_03698_gb300 as bp
 
     pr = workload()
     if args.leaf > 0:
-        import gen
         pr = gen.with_params(pr, leaf=args.leaf)
-    res_op = args.residual_op or args.op
-    s = bp.Solver(device=local, **solver_kwargs(pr, args.op, res_op))
+    res_op = args.residual_op or "fp64_tree"
+    refining = res_op != args.op
+    s = bp.Solver(device=local, refine_scope=args.refine_scope, **solver_kwargs(pr, args.op, res_op))
     dev = f"cuda:{local}"
     st = pr.sites
     d_verts = torch.tensor(pr.verts, dtype=torch.float64, device=dev)
@@ -399,11 +522,26 @@ def main():
     d_group = torch.tensor(st.group, dtype=torch.int32, device=dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    peaks = measure_peaks(bp, local, not args.no_peaks)
 
     def step():
         s.set_mesh(d_verts, d_tris)
         s.set_sites(*d_site, group=d_group)
         return s.solve()
+
+    def ev_steps(k):
+        """k steps, each after an L2 flush (not timed), timed with CUDA events."""
+        ms, outs = [], []
+        for _ in range(k):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, outs
 
     tuned = None
     if args.autotune > 0:
@@ -421,17 +559,7 @@ def main():
     torch.cuda.synchronize()
     sampler.start()
     t_wall0 = time.time()
-    step_ms = []
-    outs = []
-    for _ in range(args.steps):
-        flush.fill_(1.0)            # evict L2 between timed steps (not timed)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        outs.append(step())
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms, outs = ev_steps(args.steps)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -457,7 +585,22 @@ def main():
               "set_sites_ms": timed(lambda: s.set_sites(*d_site, group=d_group)),
               "solve_ms": timed(lambda: s.solve())}
 
-    # ---- matvec alone: chosen operator and FP64 direct
+    # ---- the plain form (no refinement) on the same inputs, beside the headline
+    plain = None
+    if refining and args.plain_steps > 0:
+        s.set_params(residual_op=args.op)
+        step()
+        p_ms, p_outs = ev_steps(args.plain_steps)
+        s.set_params(residual_op=res_op)
+        po = p_outs[-1]
+        plain = {"value": float(np.mean(p_ms)) / 1e3, "unit": UNIT, "steps": args.plain_steps,
+                 "op": args.op, "residual_op": args.op, "dG_solv_kcal": po["dG_solv_kcal"],
+                 "matvecs": po["matvecs_total"], "gmres_iters": po["gmres_iters_total"],
+                 "dG_refined_minus_plain_kcal": out["dG_solv_kcal"] - po["dG_solv_kcal"],
+                 "dG_rel_diff": abs(out["dG_solv_kcal"] - po["dG_solv_kcal"]) / abs(out["dG_solv_kcal"]),
+                 "refinement_cost": value / (float(np.mean(p_ms)) / 1e3)}
+
+    # ---- matvec alone: chosen operator, the residual operator and FP64 direct
     n = pr.n_panels
     K = pr.params.gauss_k
     x = torch.randn(2 * n, dtype=torch.float64, device=dev)
@@ -478,27 +621,35 @@ def main():
     s.stats(reset=True)
     mv_ms = time_matvec(args.op, args.matvec_reps)
     mv_stats = s.stats(reset=True)
+    res_ms = time_matvec(res_op, 3) if refining else None
+    s.stats(reset=True)
     f64_ms = time_matvec("fp64_direct", args.fp64_reps) if args.fp64_reps > 0 else None
     s.stats(reset=True)
     inter = float(n) * n * K
 
-    # ---- roofline of the dominant kernel, live CUDA-event durations inside the timed steps
+    # ---- roofline of the dominant unit, live CUDA-event durations inside the timed steps
+    fp32_peak = peaks["fp32_fma_tflops"] if peaks else FP32_PEAK_NOMINAL_TFLOPS
+    peak_basis = (f"measured FP32 FMA throughput of this GPU ({peaks['fp32_fma_tflops']:.1f} TFLOP/s, "
+                  f"bempol_measure_peaks, SM clock median {peaks['clocks']['sm_mhz']} MHz while measured), "
+                  "burst figure; of measured") if peaks else \
+        "fallback: 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock (unit counts)"
     pair_launch_ms = stats["pair_ms"] / max(1, stats["pair_launches"])
     pairs_per_launch = stats["pair_interactions"] / max(1, stats["pair_launches"])
     pair_tflops = pairs_per_launch * FLOPS_PER_PAIR / max(pair_launch_ms * 1e-3, 1e-12) / 1e12
     kernels = {"pair": {"name": "near_kernel<float>" if "tree" in args.op else "p2p_f32_kernel",
                         "launches": stats["pair_launches"], "total_ms": stats["pair_ms"],
                         "avg_launch_ms": pair_launch_ms, "pairs_per_launch": pairs_per_launch,
-                        "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": pair_tflops}}
+                        "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": pair_tflops,
+                        "frac": pair_tflops / fp32_peak}}
     if "tree" in args.op and stats["far_launches"]:
         P = pr.params.order
         far_launch_ms = stats["far_ms"] / stats["far_launches"]
         evals_per_launch = stats["far_evaluations"] / stats["far_launches"]
         far_tflops = evals_per_launch * far_flops(P) / (far_launch_ms * 1e-3) / 1e12
-        kernels["far"] = {"name": f"far_kernel<{P},float>", "launches": stats["far_launches"],
+        kernels["far"] = {"name": f"far_kernel<{P},float> (Laplace + Yukawa)", "launches": stats["far_launches"],
                           "total_ms": stats["far_ms"], "avg_launch_ms": far_launch_ms,
                           "evals_per_launch": evals_per_launch, "flops_per_eval": far_flops(P),
-                          "achieved_tflops": far_tflops}
+                          "achieved_tflops": far_tflops, "frac": far_tflops / fp32_peak}
     if "tree" in args.op and stats["tree_products"]:
         # the near and far kernels of one product run concurrently (near on the caller's
         # stream, moments/M2M/far on the side stream): the unit of the roofline is the
@@ -507,30 +658,36 @@ def main():
         prod_ms = stats["tree_ms"] / stats["tree_products"]
         flops = (stats["pair_interactions"] * FLOPS_PER_PAIR
                  + stats["far_evaluations"] * far_flops(P)) / stats["tree_products"]
-        kernels["tree"] = {"name": f"tree product: near_kernel<float> || far_kernel<{P},float> x2",
+        kernels["tree"] = {"name": f"FP32 tree product: near_kernel<float> || far_kernel<{P},float> x2",
                            "launches": stats["tree_products"], "total_ms": stats["tree_ms"],
                            "avg_launch_ms": prod_ms, "flops_per_launch": flops,
-                           "achieved_tflops": flops / (prod_ms * 1e-3) / 1e12}
+                           "achieved_tflops": flops / (prod_ms * 1e-3) / 1e12,
+                           "frac": flops / (prod_ms * 1e-3) / 1e12 / fp32_peak}
         dom = "tree"
     else:
         dom = max(kernels, key=lambda k: kernels[k]["total_ms"])
     kd = kernels[dom]
-    roofline = {"bound": "alu", "kernel": kd["name"], "achieved": kd["achieved_tflops"], "peak": FP32_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "frac": kd["achieved_tflops"] / FP32_PEAK_TFLOPS, "traffic": None,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 (FMA) x 2.070 GHz max SM clock",
+    roofline = {"bound": "alu", "kernel": kd["name"], "achieved": kd["achieved_tflops"], "peak": fp32_peak,
+                "unit": "TFLOP/s", "frac": kd["achieved_tflops"] / fp32_peak,
+                "traffic": TRAFFIC_PER_PRODUCT_BYTES if dom == "tree" else None,
+                "traffic_basis": TRAFFIC_BASIS if dom == "tree" else None,
+                "peak_basis": peak_basis, "flops_per_pair": FLOPS_PER_PAIR,
                 "share_of_step": kd["total_ms"] / max(total_ms, 1e-9), "kernels": kernels}
 
     # ---- where a step's time goes (live CUDA-event sums over the timed steps, per step)
     K_ = args.steps
     prod_ms = stats["tree_ms"] if stats["tree_products"] else stats["pair_ms"] + stats["far_ms"]
     breakdown = {"step_ms": total_ms / K_, "set_mesh_ms": phases["set_mesh_ms"], "set_sites_ms": phases["set_sites_ms"],
-                 "operator_products_ms": prod_ms / K_, "rhs_ms": stats["rhs_ms"] / K_,
+                 "operator_products_ms": prod_ms / K_, "fp64_tree_products_ms": stats["tree64_ms"] / K_,
+                 "fp64_tree_products": stats["tree64_products"] / K_, "rhs_ms": stats["rhs_ms"] / K_,
                  "reaction_field_ms": stats["reaction_ms"] / K_, "site_fields_ms": stats["site_field_ms"] / K_}
-    breakdown["other_ms"] = breakdown["step_ms"] - sum(v for k, v in breakdown.items() if k != "step_ms")
+    breakdown["other_ms"] = breakdown["step_ms"] - sum(v for k, v in breakdown.items()
+                                                       if k not in ("step_ms", "fp64_tree_products"))
     mesh_stats = s.stats()
     breakdown["set_mesh_phases_ms"] = {k: mesh_stats["mesh_" + k + "_ms"]
                                        for k in ("validate", "geometry", "blocks", "tree", "near")}
-    breakdown["note"] = ("other = GMRES orthogonalisation, near-field corrections and combines, induced-dipole "
+    breakdown["note"] = ("operator products = the FP32 treecode products fork to join, the FP64 residual products "
+                         "apart; other = GMRES orthogonalisation, near-field corrections and combines, induced-dipole "
                          "updates, energies, host logic; set_mesh/set_sites from one untimed step")
 
     # ---- end to end through the C ABI from pinned host buffers
@@ -564,34 +721,48 @@ def main():
 
     cpu = None
     if not args.no_cpu:
-        cpu = cpu_baseline(pr, args.cpu_rows, int(out["matvecs_total"]))
+        sampler_cpu = OracleSampler(pr)
+        try:
+            cpu = cpu_baseline(sampler_cpu, args.cpu_rows, args.cpu_rows_1core, PRODUCTS_PER_DG,
+                               native_products=int(out["matvecs_total"]))
+        finally:
+            sampler_cpu.close()
 
+    res_matvecs = int(out.get("residual_matvecs", 0))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if "fp32" in args.op else "f64",
         "data": "synthetic",
         "config": {"workload": pr.name, "panels": n, "gauss_k": K, "sites": st.n, "op": args.op,
-                   "residual_op": res_op, "theta": pr.params.theta, "order": pr.params.order,
-                   "leaf": pr.params.leaf,
+                   "residual_op": res_op, "refine_scope": args.refine_scope if refining else None,
+                   "theta": pr.params.theta, "order": pr.params.order, "leaf": pr.params.leaf,
                    "gmres_tol": pr.params.gmres_tol, "scf_tol": pr.params.scf_tol,
+                   "alpha_range": [float(a) for a in gen.configs.DENSE_ALPHA],
+                   "alpha_note": "polarizabilities U(0.25, 0.75) A^3, half the stated U(0.5, 1.5): at this site "
+                                 "density the omega = 0.7 relaxation diverges with U(0.5, 1.5)",
                    "l2": "flushed (512 MiB write) between timed steps, flush not timed",
                    "autotuned": tuned},
         "solve": {"dG_solv_kcal": out["dG_solv_kcal"], "scf_iters_diss": out["scf_iters_diss"],
                   "scf_iters_vac": out["scf_iters_vac"], "gmres_iters": out["gmres_iters_total"],
-                  "matvecs": out["matvecs_total"], "bem_solves": out["n_solves"],
+                  "matvecs": out["matvecs_total"], "residual_matvecs": res_matvecs,
+                  "fp32_matvecs": out["matvecs_total"] - res_matvecs, "bem_solves": out["n_solves"],
                   "last_rel_residual": out["last_rel_residual"], "t_setup_ms": out["t_setup_ms"],
                   "t_scf_ms": out["t_scf_ms"], "wall_s_timed_region": wall, "phases": phases},
+        "plain": plain,
         "matvec": {"op": args.op, "ms": mv_ms, "effective_ginter_s": inter / (mv_ms * 1e-3) / 1e9,
                    "performed_pairs": mv_stats["pair_interactions"] / max(1, args.matvec_reps),
+                   "residual_op": res_op if refining else None, "residual_ms": res_ms,
                    "fp64_direct_ms": f64_ms,
                    "fp64_direct_ginter_s": (inter / (f64_ms * 1e-3) / 1e9) if f64_ms else None,
-                   # FP64 direct at the same 28 algorithmic flops per pair, against GB300's nominal
-                   # FP64 rate (1.25 TFLOP/s; FP64 sqrt, divide and exp run as instruction sequences)
                    "fp64_direct_tflops_algorithmic": (inter * FLOPS_PER_PAIR / (f64_ms * 1e-3) / 1e12)
                    if f64_ms else None,
-                   "fp64_peak_nominal_tflops": 1.25,
+                   "fp64_peak_measured_tflops": peaks["fp64_fma_tflops"] if peaks else None,
+                   "fp64_direct_frac": (inter * FLOPS_PER_PAIR / (f64_ms * 1e-3) / 1e12 / peaks["fp64_fma_tflops"])
+                   if (f64_ms and peaks) else None,
+                   "fp64_direct_dG_s_extrapolated": (f64_ms * 1e-3 * out["matvecs_total"]) if f64_ms else None,
                    "interactions_per_matvec": inter},
+        "peaks": peaks,
         "roofline": roofline,
         "breakdown": breakdown,
         "cpu_baseline": cpu,

@@ -101,7 +101,21 @@ typedef struct {
   double inner_tol;            /* relative tolerance of each inner solve under refinement */
   int refine_maxit;            /* maximum refinement (outer) steps */
   double thole_a;              /* Thole damping parameter (AMOEBA: 0.39) */
+  int refine_scope;            /* which BEM solves of bempol_solve* are refined when residual_op != op:
+                                  BEMPOL_REFINE_EVERY or BEMPOL_REFINE_FINAL (see below) */
 } bempol_params;
+
+/* Scope of the FP64 iterative refinement inside bempol_solve* (residual_op != op).
+ *  BEMPOL_REFINE_EVERY: every BEM solve of both induced-dipole iterations is refined, and the
+ *    right-hand sides, reaction fields and multipole fields use residual_op's precision.
+ *  BEMPOL_REFINE_FINAL: the solves inside the induced-dipole iteration run plain GMRES with
+ *    `op` (warm-started) to max(gmres_tol, 1e-6) when op is an FP32 form (the residual such an
+ *    operator reaches) or to gmres_tol otherwise, with site-side sums in op's precision; only
+ *    the last solve, whose phi and psi give the energy, is refined against residual_op (to
+ *    gmres_tol), and its right-hand side, reaction field and energy-form multipole fields use
+ *    residual_op's precision.  The adjoint (bempol_gradient) then runs its transposed solves
+ *    with `op` alone. */
+enum { BEMPOL_REFINE_EVERY = 0, BEMPOL_REFINE_FINAL = 1 };
 
 typedef struct {
   /* scalars, always written (host memory inside this struct) */
@@ -120,6 +134,7 @@ typedef struct {
   double* mu_diss;             /* [Ns*3] induced dipoles, dissolved state */
   double* mu_vac;              /* [Ns*3] induced dipoles, vacuum state */
   int where;                   /* BEMPOL_HOST or BEMPOL_DEVICE for the optional outputs */
+  int residual_matvecs;        /* of matvecs_total, the products with residual_op (refinement residuals) */
 } bempol_result;
 
 /* Per-system result of bempol_solve_systems (host memory). */
@@ -136,7 +151,7 @@ typedef struct {
 
 /* Fill `p` with the defaults: eps 1/80, kappa 0.125, K=4, near 2.0, theta 0.5,
  * P=5, leaf 256, GMRES 1e-8/100/500, SCF 1e-8/omega 0.7/200, op FP64 direct,
- * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39. */
+ * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39, refine_scope EVERY. */
 void bempol_default_params(bempol_params* p);
 
 /* Create a context on CUDA device `device`.  Validates `p` (ranges above);
@@ -316,9 +331,12 @@ bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, 
  * process exit); more sites give BEMPOL_ERR_ARG.  The array is shared by every
  * call on every context: calls that overlap on the GPU race.  Each call writes
  * every scratch entry it reads, so nothing carries over between calls.  The
- * first call on a device looks up the array's device address (one-time set-up);
- * make that first call before any stream capture.  Other errors as
- * bempol_site_reaction.  Enqueued on `stream`. */
+ * first call on a device looks up the array's device address (one-time set-up,
+ * cached for the process); that lookup may make the CUDA driver load this
+ * library's device code, which allocates inside the driver, so make the first
+ * call early (before any stream capture and before the allocation-free phase).
+ * After a cudaDeviceReset neither contexts nor the cached address are valid.
+ * Other errors as bempol_site_reaction.  Enqueued on `stream`. */
 bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const double* x, double* out, int op, void* stream);
 
 /* Multipole-multipole potentials at the sites (Eqs. Efield_mult,
@@ -365,7 +383,8 @@ bempol_status bempol_sizes(const bempol_ctx* c, int64_t* n_panels, int32_t* gaus
  * times.  In a treecode product the near-field kernel runs concurrently with the
  * moment, M2M and far-field kernels (these on a side stream of the context), so
  * pair_ms and far_ms then overlap and tree_ms (fork to join on the caller's stream)
- * is the product's own duration. */
+ * is the product's own duration.  Products with the FP64 treecode are counted apart
+ * (tree64_*), so the pair/far/tree counters describe the FP32 treecode alone. */
 typedef struct {
   int64_t kernel_launches;     /* kernels this library launched (all contexts) since the last reset */
   int64_t pair_launches;       /* launches of the pair kernel */
@@ -386,7 +405,36 @@ typedef struct {
      phase boundary while timing is enabled): closedness check, panel geometry and Morton
      order, block tables, octree and interaction lists, near table and its integrals */
   double mesh_validate_ms, mesh_geometry_ms, mesh_blocks_ms, mesh_tree_ms, mesh_near_ms;
+  /* FP64 treecode products (BEMPOL_OP_FP64_TREE, e.g. the refinement residuals), fork to
+     join; the pair, far and tree counters above cover the FP32 treecode only */
+  int64_t tree64_products;
+  double tree64_ms;
 } bempol_stats;
+
+/* Arithmetic-pipe throughput of a device (measurement support, not part of the
+ * method): the treecode and direct pair kernels are bound by the FP32 FMA pipe and
+ * the special-function unit (rsqrt, 2^x), the FP64 direct form by the FP64 FMA
+ * pipe, so these are the peaks their roofline fractions divide by.  Each rate comes
+ * from a kernel of independent dependency chains of one PTX instruction
+ * (fma.rn.f32, fma.rn.f64, rsqrt.approx.ftz.f32, ex2.approx.ftz.f32) over SMs x 8
+ * blocks x 256 threads, timed with CUDA events on the legacy default stream (best
+ * of `reps` after one warm-up launch).  `iters` sets the FP32 chain length (the
+ * FP64 chains run iters/8 + 1 steps, the MUFU chains iters/4 + 1); 65,536 gives
+ * launches of a few milliseconds.  FMA counts as two flops.  The rates hold at
+ * the SM clock of the run, which the attribute below does not report (it is the
+ * device's nominal maximum): sample the clock alongside.  Synchronises the device's
+ * default stream.  BEMPOL_ERR_ARG / BEMPOL_ERR_CUDA. */
+typedef struct {
+  double fp32_fma_tflops;      /* FP32 FMA throughput, TFLOP/s */
+  double fp64_fma_tflops;      /* FP64 FMA throughput, TFLOP/s */
+  double mufu_rsqrt_gops;      /* rsqrt.approx.f32 per second / 1e9 */
+  double mufu_ex2_gops;        /* ex2.approx.f32 per second / 1e9 */
+  double ms_fp32, ms_fp64, ms_rsqrt, ms_ex2;   /* best launch time of each kernel */
+  int sm_count;
+  double clock_mhz_attr;       /* cudaDevAttrClockRate (maximum SM clock) */
+} bempol_peaks;
+
+bempol_status bempol_measure_peaks(int device, int iters, int reps, bempol_peaks* out);
 
 /* Turn event timing on (1) or off (0).  Counting is always on. */
 bempol_status bempol_stats_enable(bempol_ctx* c, int enable);

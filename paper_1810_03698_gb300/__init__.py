@@ -20,6 +20,8 @@ LIB_PATH = os.path.join(_HERE, "libbempol.so")
 HOST, DEVICE = 0, 1
 OP_FP64_DIRECT, OP_FP32_DIRECT, OP_FP32_TREE, OP_FP64_TREE = 0, 1, 2, 3
 OP_NAMES = {"fp64_direct": 0, "fp32_direct": 1, "fp32_tree": 2, "fp64_tree": 3}
+REFINE_EVERY, REFINE_FINAL = 0, 1
+REFINE_NAMES = {"every": 0, "final": 1}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_SITES", 4: "ERR_NOT_CONVERGED", 5: "ERR_CUDA",
           6: "ERR_TIMEOUT", 7: "ERR_OOM", 8: "ERR_STATE"}
@@ -33,7 +35,7 @@ class Params(C.Structure):
         ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
         ("scf_tol", C.c_double), ("sor_omega", C.c_double), ("scf_maxit", C.c_int),
         ("op", C.c_int), ("residual_op", C.c_int), ("inner_tol", C.c_double), ("refine_maxit", C.c_int),
-        ("thole_a", C.c_double),
+        ("thole_a", C.c_double), ("refine_scope", C.c_int),
     ]
 
 
@@ -44,7 +46,7 @@ class Result(C.Structure):
         ("matvecs_total", C.c_int), ("n_solves", C.c_int), ("last_rel_residual", C.c_double),
         ("t_setup_ms", C.c_double), ("t_scf_ms", C.c_double), ("t_total_ms", C.c_double),
         ("phi", C.c_void_p), ("dphidn", C.c_void_p), ("site_reaction", C.c_void_p),
-        ("mu_diss", C.c_void_p), ("mu_vac", C.c_void_p), ("where", C.c_int),
+        ("mu_diss", C.c_void_p), ("mu_vac", C.c_void_p), ("where", C.c_int), ("residual_matvecs", C.c_int),
     ]
 
 
@@ -78,7 +80,15 @@ class Stats(C.Structure):
         ("site_field_calls", C.c_int64), ("site_field_ms", C.c_double),
         ("mesh_validate_ms", C.c_double), ("mesh_geometry_ms", C.c_double), ("mesh_blocks_ms", C.c_double),
         ("mesh_tree_ms", C.c_double), ("mesh_near_ms", C.c_double),
+        ("tree64_products", C.c_int64), ("tree64_ms", C.c_double),
     ]
+
+
+class Peaks(C.Structure):
+    _fields_ = [("fp32_fma_tflops", C.c_double), ("fp64_fma_tflops", C.c_double), ("mufu_rsqrt_gops", C.c_double),
+                ("mufu_ex2_gops", C.c_double), ("ms_fp32", C.c_double), ("ms_fp64", C.c_double),
+                ("ms_rsqrt", C.c_double), ("ms_ex2", C.c_double), ("sm_count", C.c_int),
+                ("clock_mhz_attr", C.c_double)]
 
 
 def _load():
@@ -112,6 +122,7 @@ def _load():
         "bempol_get_geometry": (i32, [vp, vp, vp, vp, vp, vp, vp]),
         "bempol_stats_enable": (i32, [vp, i32]),
         "bempol_stats_read": (i32, [vp, C.POINTER(Stats), i32]),
+        "bempol_measure_peaks": (i32, [i32, i32, i32, C.POINTER(Peaks)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -136,6 +147,8 @@ def default_params(**kw) -> Params:
     for k, v in kw.items():
         if k in ("op", "residual_op") and isinstance(v, str):
             v = OP_NAMES[v]
+        if k == "refine_scope" and isinstance(v, str):
+            v = REFINE_NAMES[v]
         setattr(p, k, v)
     return p
 
@@ -196,6 +209,8 @@ class Solver:
         for k, v in kw.items():
             if k in ("op", "residual_op") and isinstance(v, str):
                 v = OP_NAMES[v]
+            if k == "refine_scope" and isinstance(v, str):
+                v = REFINE_NAMES[v]
             setattr(self.params, k, v)
         self._chk(_lib.bempol_set_params(self._h, C.byref(self.params)))
 
@@ -351,6 +366,16 @@ class Solver:
         out["near_col"] = out["near_col"][:nnz]
         out["near_corr"] = out["near_corr"][:nnz]
         return out
+
+
+def measure_peaks(device: int = 0, iters: int = 65536, reps: int = 3) -> dict:
+    """FP32 / FP64 FMA and MUFU (rsqrt, 2^x) throughput of the device
+    (bempol_measure_peaks)."""
+    r = Peaks()
+    st = _lib.bempol_measure_peaks(device, iters, reps, C.byref(r))
+    if st != 0:
+        raise BempolError(st, "bempol_measure_peaks failed")
+    return {k: getattr(r, k) for k, _ in Peaks._fields_}
 
 
 KCAL_PER_UNIT = 4.0 * 3.141592653589793 * 332.0637132991921  # kcal/mol per e^2/A (vacuum permittivity 1)

@@ -789,8 +789,12 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   const int n = c.n, ns = c.ns, S = c.nsys, len = 2 * n;
   const bempol_params& P = c.par;
   const double scale = INV4PI / P.eps_in;
-  // site-side sums in FP32 pairs (FP64 sums) when the solves' residual is an FP32 form
-  const bool f32 = (P.residual_op == BEMPOL_OP_FP32_DIRECT || P.residual_op == BEMPOL_OP_FP32_TREE);
+  // Site-side sums in FP32 pairs (FP64 sums) when the solves' residual is an FP32 form.
+  // When the forward solve refined only its final solve, the transposed solves run
+  // with `op` alone and the site-side sums take op's precision.
+  const bool final_only = P.residual_op != P.op && P.refine_scope == BEMPOL_REFINE_FINAL;
+  const int prec_op = final_only ? P.op : P.residual_op;
+  const bool f32 = (prec_op == BEMPOL_OP_FP32_DIRECT || prec_op == BEMPOL_OP_FP32_TREE);
   AdjointOut ao;
   DBuf<double> F_s, P_mu, P_0, Pv_mu, Pv_0, cmu, cmuv, nu, nuv, tn, psi, phinu, phinuv, g10, gv10, wq, wd, wQ, rT,
       lam;
@@ -854,7 +858,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
     GmresOut g;
     {
       TransposeScope ts(c);
-      g = solve_bem(c, rT.p, lam.p, want, s);
+      g = solve_bem(c, rT.p, lam.p, want, s, !final_only);
     }
     ao.gmres_iters += g.iters;
     ++ao.solves;

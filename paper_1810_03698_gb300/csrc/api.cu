@@ -43,7 +43,7 @@ void Ctx::stat_rewind(const StatMark& m) {
     cudaEventDestroy(timed[k].b);
   }
   if (timed.size() > m.ntimed) timed.resize(m.ntimed);
-  for (int k = 0; k < 3; ++k) stat_launches[k] = m.launches[k];
+  for (int k = 0; k < NKIND; ++k) stat_launches[k] = m.launches[k];
   stat_pairs = m.pairs;
   stat_far = m.far;
 }
@@ -119,28 +119,15 @@ void check_params(const bempol_params* p) {
   if (!(p->inner_tol > 0 && p->inner_tol < 1)) bad("inner_tol must be in (0, 1)");
   if (p->refine_maxit < 0) bad("refine_maxit must be >= 0");
   if (!(p->thole_a >= 0)) bad("thole_a must be >= 0");
+  if (p->refine_scope != BEMPOL_REFINE_EVERY && p->refine_scope != BEMPOL_REFINE_FINAL)
+    bad("refine_scope must be BEMPOL_REFINE_EVERY or BEMPOL_REFINE_FINAL");
 }
 
 bool op_fp32(int op) { return op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE; }
+// Relative residual that GMRES with an FP32 operator form reliably reaches (FP32 pair
+// terms with FP64 sums: the operator itself is accurate to ~1e-7).
+constexpr double FP32_SOLVE_FLOOR = 1e-6;
 bool op_tree(int op) { return op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE; }
-
-template <typename F>
-bempol_status guard(bempol_ctx* c, F&& f) {
-  if (!c) return BEMPOL_ERR_ARG;
-  try {
-    if (cudaSetDevice(c->device) != cudaSuccess) fail(BEMPOL_ERR_CUDA, "cudaSetDevice failed");
-    c->mv_active = nullptr;  // products outside a solve compute every system
-    f();
-    c->err.clear();
-    return BEMPOL_OK;
-  } catch (const Error& e) {
-    c->err = e.msg;
-    return e.st;
-  } catch (const std::exception& e) {
-    c->err = e.what();
-    return BEMPOL_ERR_ARG;
-  }
-}
 
 template <typename T>
 void to_device(DBuf<T>& dst, const T* src, size_t count, int where, cudaStream_t s) {
@@ -430,6 +417,7 @@ void bempol_default_params(bempol_params* p) {
   p->inner_tol = 1e-3;
   p->refine_maxit = 20;
   p->thole_a = 0.39;
+  p->refine_scope = BEMPOL_REFINE_EVERY;
 }
 
 bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out) {
@@ -693,6 +681,8 @@ bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
     out->mesh_blocks_ms = c->mesh_ms[2];
     out->mesh_tree_ms = c->mesh_ms[3];
     out->mesh_near_ms = c->mesh_ms[4];
+    out->tree64_products = c->stat_launches[6];
+    out->tree64_ms = c->stat_ms[6];
     if (reset) {
       c->launches_at_reset = g_launches.load();
       for (int k = 0; k < Ctx::NKIND; ++k) {
@@ -779,7 +769,14 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     const int n = c->n, ns = c->ns, len = 2 * n, S = c->nsys;
     ensure_tree(*c, P.op, s);
     ensure_tree(*c, P.residual_op, s);
-    const bool f32 = op_fp32(P.residual_op);
+    // Precision of the site-side sums (right-hand sides, reaction and multipole fields):
+    // that of residual_op throughout, or, when only the final solve is refined, that of
+    // op inside the induced-dipole iterations and of residual_op for the final solve and
+    // the energy (f32_final).
+    const bool refining = P.residual_op != P.op;
+    const bool final_only = refining && P.refine_scope == BEMPOL_REFINE_FINAL;
+    const bool f32_final = op_fp32(P.residual_op);
+    const bool f32 = final_only ? op_fp32(P.op) : f32_final;
     DBuf<double>& mu = c->sol_mu;
     DBuf<double>& mu_v = c->sol_mu_v;
     DBuf<double>& x = c->sol_x;
@@ -801,7 +798,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     b.zero(s);
     double t_setup = tt.ms();
     EventTimer ts(s);
-    int gm_iters = 0, matvecs = 0, solves = 0;
+    int gm_iters = 0, matvecs = 0, res_matvecs = 0, solves = 0;
     std::vector<int> it_d(S, 0), it_v(S, 0), sys_gm(S, 0), sys_solves(S, 0);
     std::vector<double> sys_res(S, 0.0);
     std::vector<char> conv_v(S, 0), conv_d(S, 0), gm_ok(S, 1), diverged(S, 0);
@@ -856,15 +853,20 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
       }
     }
     std::vector<char> want(S, 1);
-    auto bem = [&](const std::vector<char>& which) {
+    auto bem = [&](const std::vector<char>& which, bool final) {
       launch(add_vec, cdiv(3 * ns, 256), 256, 0, s, c->site_d.p, mu.p, p.p, 3 * ns);
       Ctx::Timed tr;
       c->time_begin(3, s, tr);
-      rhs_internal(*c, p.p, b.p, f32, s);
+      rhs_internal(*c, p.p, b.p, final ? f32_final : f32, s);
       c->time_end(s, tr);
-      GmresOut g = solve_bem(*c, b.p, x.p, which, s);
+      // under REFINE_FINAL the iteration's solves are plain GMRES with op, which for an
+      // FP32 form cannot go below FP32_SOLVE_FLOOR; the final solve is refined to gmres_tol
+      const double tol = (final_only && !final && op_fp32(P.op)) ? std::max(P.gmres_tol, FP32_SOLVE_FLOOR)
+                                                                 : P.gmres_tol;
+      GmresOut g = solve_bem(*c, b.p, x.p, which, s, refining && (final || !final_only), tol);
       gm_iters += g.iters;
       matvecs += g.matvecs;
+      res_matvecs += g.residual_matvecs;
       ++solves;
       for (int q = 0; q < S; ++q) {
         if (!which[q]) continue;
@@ -881,7 +883,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
         if (diverged[q]) act[q] = 0;
       for (int it = 1; it <= P.scf_maxit; ++it) {
         for (int q = 0; q < S; ++q) want[q] = (char)act[q];
-        bem(want);
+        bem(want, false);
         Ctx::Timed tx, tm;
         c->time_begin(4, s, tx);
         site_reaction_internal(*c, x.p, react.p, f32, false, s);
@@ -909,11 +911,11 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
       }
     }
     std::fill(want.begin(), want.end(), 1);
-    bem(want);
-    site_reaction_internal(*c, x.p, react.p, f32, true, s);
-    multipole_internal(*c, mu.p, 1, mult10.p, s, f32);
+    bem(want, true);
+    site_reaction_internal(*c, x.p, react.p, f32_final, true, s);
+    multipole_internal(*c, mu.p, 1, mult10.p, s, f32_final);
     std::vector<double> Gd = energy_internal(*c, react.p, mult10.p, s);
-    multipole_internal(*c, mu_v.p, 3, mult10.p, s, f32);
+    multipole_internal(*c, mu_v.p, 3, mult10.p, s, f32_final);
     std::vector<double> Gv = energy_internal(*c, nullptr, mult10.p, s);
     double t_scf = ts.ms();
     bool ok = true;
@@ -949,6 +951,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     out->scf_iters_vac = itv_max;
     out->gmres_iters_total = gm_iters;
     out->matvecs_total = matvecs;
+    out->residual_matvecs = res_matvecs;
     out->n_solves = solves;
     out->last_rel_residual = res_max;
     out->t_setup_ms = t_setup;

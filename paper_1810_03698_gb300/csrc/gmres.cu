@@ -456,7 +456,9 @@ void permute_to_caller(const Ctx& c, const double* src, double* dst, int nb, cud
   BP_CHECK_LAUNCH();
 }
 
-GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s) {
+GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s,
+                   bool refine, double rel_tol) {
+  if (!(rel_tol > 0.0)) rel_tol = c.par.gmres_tol;
   const int n = c.n, len = 2 * n, S = c.nsys;
   Work w = workspace(c);
   std::vector<int> all(S, 1);
@@ -477,7 +479,7 @@ GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& 
       zero_sys[q] = 1;  // b = 0: x = 0 exactly
       any_zero = true;
     } else {
-      tol[q] = c.par.gmres_tol * bn[q];
+      tol[q] = rel_tol * bn[q];
       tot.sys_conv[q] = 0;
     }
   }
@@ -499,7 +501,7 @@ GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& 
       if (!tot.sys_conv[q]) tot.converged = false;
     }
   };
-  if (c.par.residual_op == c.par.op) {
+  if (!refine || c.par.residual_op == c.par.op) {
     std::vector<double> rn;
     GmresOut o = gmres(c, c.par.op, b, x, tol, c.par.gmres_maxit, rn, s);
     tot.iters = o.iters;
@@ -524,6 +526,7 @@ GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& 
     matvec_internal(c, x, r, c.par.residual_op, s);
     c.mv_active = nullptr;
     ++tot.matvecs;
+    ++tot.residual_matvecs;
     launch(axpby, nb, tb, 0, s, 1.0, b, -1.0, r, r, len);
     BP_CHECK_LAUNCH();
     std::vector<double> r2 = sys_norm2(c, w, r, w.active, s);

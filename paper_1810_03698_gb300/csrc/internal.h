@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <exception>
+#include <new>
 #include <string>
 #include <vector>
 
@@ -233,10 +235,11 @@ struct Ctx {
   bool stats_on = false;
   struct Timed {
     cudaEvent_t a, b;
-    int kind;  // 0 pair kernel, 1 far-field kernels, 2 treecode product, 3 right-hand side,
-               // 4 reaction field at the sites, 5 multipole fields at the sites
+    int kind;  // 0 pair kernel, 1 far-field kernels, 2 FP32 treecode product, 3 right-hand side,
+               // 4 reaction field at the sites, 5 multipole fields at the sites,
+               // 6 FP64 treecode product
   };
-  static constexpr int NKIND = 6;
+  static constexpr int NKIND = 7;
   // host wall-clock of the phases of the last set_mesh (validation, geometry and Morton
   // order, block tables, tree, near table); the stream is synchronised at each phase
   // boundary only while stats are on
@@ -253,16 +256,42 @@ struct Ctx {
   // active system (its launches still count in kernel_launches)
   struct StatMark {
     size_t ntimed;
-    long long launches[3], pairs, far;
+    long long launches[NKIND], pairs, far;
   };
   StatMark stat_mark() const {
-    return {timed.size(), {stat_launches[0], stat_launches[1], stat_launches[2]}, stat_pairs, stat_far};
+    StatMark m{timed.size(), {}, stat_pairs, stat_far};
+    for (int k = 0; k < NKIND; ++k) m.launches[k] = stat_launches[k];
+    return m;
   }
   void stat_rewind(const StatMark& m);
 
   Ctx() = default;
   ~Ctx();
 };
+
+// Body of every C entry point taking a context: makes the context's device current,
+// runs f, and turns exceptions into a status plus the context's message (nothing
+// escapes an extern "C" function).
+template <typename F>
+bempol_status guard(Ctx* c, F&& f) {
+  if (!c) return BEMPOL_ERR_ARG;
+  try {
+    if (cudaSetDevice(c->device) != cudaSuccess) fail(BEMPOL_ERR_CUDA, "cudaSetDevice failed");
+    c->mv_active = nullptr;  // products outside a solve compute every system
+    f();
+    c->err.clear();
+    return BEMPOL_OK;
+  } catch (const Error& e) {
+    c->err = e.msg;
+    return e.st;
+  } catch (const std::bad_alloc&) {
+    c->err = "host allocation failed";
+    return BEMPOL_ERR_OOM;
+  } catch (const std::exception& e) {
+    c->err = e.what();
+    return BEMPOL_ERR_ARG;
+  }
+}
 
 // ---------------------------------------------------------------- launch helpers
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }
@@ -315,6 +344,7 @@ bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool
 struct GmresOut {
   int iters = 0;
   int matvecs = 0;
+  int residual_matvecs = 0;    // of matvecs, the refinement residuals (products with residual_op)
   double rel_res = 0;          // largest relative residual over the solved systems
   bool converged = false;      // every solved system converged
   std::vector<int> sys_iters;  // per system
@@ -322,8 +352,12 @@ struct GmresOut {
   std::vector<char> sys_conv;
 };
 // Solve A x = b for every system with want[s] != 0 (empty = all); x holds the
-// initial guess and is left unchanged for the other systems.
-GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s);
+// initial guess and is left unchanged for the other systems.  With `refine` and
+// params.residual_op != params.op the solve is FP64 iterative refinement (outer
+// residual with residual_op, inner GMRES with op); otherwise plain GMRES with op.
+// rel_tol: stopping tolerance ||b - A x|| / ||b|| (<= 0: params.gmres_tol).
+GmresOut solve_bem(Ctx& c, const double* b, double* x, const std::vector<char>& want, cudaStream_t s,
+                   bool refine, double rel_tol = -1.0);
 // vector helpers (gmres.cu)
 double dot_dev(Ctx& c, const double* a, const double* b, int len, cudaStream_t s);
 void permute_to_internal(const Ctx& c, const double* src, double* dst, int blocks_of_n, cudaStream_t s);

@@ -32,7 +32,12 @@ double* g_scratch_ptr[64] = {};
 
 // Device address of the scratch array for the current device.  In host code the
 // symbol g_site_scratch is only a host-side stand-in, never a device address;
-// the address comes from cudaGetSymbolAddress, looked up once per device.
+// the address comes from cudaGetSymbolAddress, looked up once per device (on the
+// first call there) and cached for the life of the process.  That first lookup
+// may load this library's device code onto the device (CUDA loads modules
+// lazily), which the driver does with allocations of its own.  A
+// cudaDeviceReset destroys the array together with every other allocation of the
+// library, so no context and no cached address may be used after one.
 double* scratch_for(int device) {
   if (device < 0 || device >= 64) fail(BEMPOL_ERR_ARG, "device index out of range for the no-alloc scratch");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -53,9 +58,7 @@ double* scratch_for(int device) {
 extern "C" bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const double* x, double* out, int op,
                                                       void* stream) {
   using namespace bp;
-  if (!c) return BEMPOL_ERR_ARG;
-  try {
-    if (cudaSetDevice(c->device) != cudaSuccess) fail(BEMPOL_ERR_CUDA, "cudaSetDevice failed");
+  return guard(c, [&] {
     if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
     if (!x || !out) fail(BEMPOL_ERR_ARG, "NULL array");
     if (op < 0 || op > 3) fail(BEMPOL_ERR_ARG, "bad op");
@@ -70,10 +73,5 @@ extern "C" bempol_status bempol_site_reaction_noalloc(bempol_ctx* c, const doubl
     permute_to_internal(*c, x, c->vec_a.p, 2, s);
     if (!site_reaction_scratch(*c, c->vec_a.p, out, fp32, true, scratch, NOALLOC_SCRATCH_DOUBLES, s))
       fail(BEMPOL_ERR_ARG, "site count exceeds the no-alloc scratch");
-    c->err.clear();
-    return BEMPOL_OK;
-  } catch (const Error& e) {
-    c->err = e.msg;
-    return e.st;
-  }
+  });
 }

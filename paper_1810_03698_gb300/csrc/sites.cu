@@ -539,7 +539,9 @@ bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool
   S = cdiv(mr, per);
   strengths(c, x, fp32, s);
   site_reaction_launch(c, S, fp32, hessian, scratch, s);
+  BP_CHECK_LAUNCH();
   launch(site_reduce_kernel, cdiv(c.ns * 10, 256), 256, 0, s, scratch, S, c.ns, out);
+  BP_CHECK_LAUNCH();
   return true;
 }
 

@@ -566,8 +566,11 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   // leave idle.  The two write disjoint pieces of c.part.
   c.ensure_aux();
   const cudaStream_t sf = c.aux;
+  // accounting: FP32 products per kernel (pair, far) and whole; FP64 products (the
+  // refinement residuals) whole only, under their own kind
+  constexpr bool F64 = sizeof(Real) == 8;
   Ctx::Timed tp;
-  c.time_begin(2, s, tp);
+  c.time_begin(F64 ? 6 : 2, s, tp);
   BP_CUDA(cudaEventRecord(c.ev_fork, s));
   BP_CUDA(cudaStreamWaitEvent(sf, c.ev_fork, 0));
   launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
@@ -577,8 +580,10 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
   Ctx::Timed tf;
-  c.time_begin(1, sf, tf);
-  c.stat_far += T.far_per_matvec;
+  if (!F64) {
+    c.time_begin(1, sf, tf);
+    c.stat_far += T.far_per_matvec;
+  }
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
   const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
   const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
@@ -586,14 +591,16 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
          kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
   launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
          T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  c.time_end(sf, tf);
+  if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
-  c.time_begin(0, s, tm);
-  c.stat_pairs += T.pairs_per_matvec;
+  if (!F64) {
+    c.time_begin(0, s, tm);
+    c.stat_pairs += T.pairs_per_matvec;
+  }
   launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
          T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
          c.mv_active, T.leaf_sys.p, c.part.p);
-  c.time_end(s, tm);
+  if (!F64) c.time_end(s, tm);
   BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join
   BP_CUDA(cudaStreamWaitEvent(s, c.ev_join, 0));
   c.time_end(s, tp);

@@ -61,7 +61,7 @@ def test_ctypes_structures_match_the_header(tmp_path):
     import paper_1810_03698_gb300 as bp
     pairs = [("bempol_params", bp.Params), ("bempol_result", bp.Result), ("bempol_system_result", bp.SystemResult),
              ("bempol_gradient_info", bp.GradientInfo), ("bempol_tune_result", bp.TuneResult),
-             ("bempol_stats", bp.Stats)]
+             ("bempol_stats", bp.Stats), ("bempol_peaks", bp.Peaks)]
     src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
     lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "bempol.h"', "int main(void) {"]
     for cname, cls in pairs:

@@ -109,6 +109,24 @@ def test_fp32_tree_with_fp64_tree_refinement(bp):
     assert abs(a["dG_solv_kcal"] - b["dG_solv_kcal"]) < 1e-8 * abs(b["dG_solv_kcal"])
 
 
+@pytest.mark.parametrize("op,res_op,leaf", [("fp32_tree", "fp64_tree", 32), ("fp32_direct", "fp64_direct", 256)])
+def test_refine_final_solve_only(bp, op, res_op, leaf):
+    """refine_scope "final": the induced-dipole iteration solves with the FP32 form alone
+    (to max(gmres_tol, 1e-6)), and only the last solve, which gives the energy, is refined
+    against the FP64 form to gmres_tol.  Delta G matches the oracle within the treecode
+    bar and the fully refined form within the SCF's own accuracy."""
+    pr = gen.with_params(gen.small_bumpy(3, 40, 8.0), gmres_tol=1e-9, scf_tol=1e-7)
+    ref = mp.solvation(pr, direct_polarization=True)
+    fin = bp.problem_solver(pr, op=op, residual_op=res_op, refine_scope="final", leaf=leaf).solve()
+    every = bp.problem_solver(pr, op=op, residual_op=res_op, refine_scope="every", leaf=leaf).solve()
+    assert fin["residual_matvecs"] >= 1 and fin["last_rel_residual"] < 1e-9
+    assert every["residual_matvecs"] > fin["residual_matvecs"]
+    assert abs(fin["dG_solv_kcal"] - ref.dG_kcal) < 1e-4 * abs(ref.dG_kcal)
+    assert abs(fin["dG_solv_kcal"] - every["dG_solv_kcal"]) < 1e-5 * abs(every["dG_solv_kcal"])
+    if op == "fp32_direct":   # the direct forms approximate nothing: FP64-level agreement
+        assert abs(every["dG_solv_kcal"] - ref.dG_kcal) < 1e-7 * abs(ref.dG_kcal)
+
+
 def test_autotune_meets_its_target(bp):
     """The autotuner's choice reproduces the direct product within the target."""
     pr = gen.small_bumpy(4, 10, 8.0, seed_index=109)

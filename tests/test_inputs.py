@@ -6,6 +6,8 @@ found by ray casting (Moller-Trumbore), and their distance to it by exact point-
 distances. The remaining checks cover separations, moment conventions (symmetric traceless
 quadrupoles), parameter ranges, and the panel and site totals of the binding batch.
 """
+import os
+
 import numpy as np
 import pytest
 from scipy.spatial import cKDTree
@@ -139,3 +141,21 @@ def test_binding_batch_recipe():
         va = ab.verts[np.unique(ab.tris[nb == 0])]
         vb = ab.verts[np.unique(ab.tris[nb == 1])]
         assert vb[:, 0].min() - va[:, 0].max() >= 3.0 - 1e-9   # the 3 A slab between the partners
+
+
+def test_kirkwood_golden_matches_the_sphere_workload():
+    """tests/golden/kirkwood_sphere_r10_100sites.json (written by make_kirkwood_sphere_r10.py
+    from oracle.kirkwood) belongs to the sites the 20,480-panel workload generates now, and
+    its value is the closed form's (Born-like sign and size: |Delta G| of a few hundred to a
+    few thousand kcal/mol for 100 unit-scale multipoles in a 10 A cavity)."""
+    import hashlib
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                       "kirkwood_sphere_r10_100sites.json")))
+    st = gen.sphere_r10_20480().sites
+    h = hashlib.sha256()
+    for a in (st.pos, st.q, st.d, st.Q, st.alpha):
+        h.update(np.ascontiguousarray(a, dtype=np.float64).tobytes())
+    assert h.hexdigest() == gold["sites_sha256"]
+    assert gold["n_sites"] == st.n == 100
+    assert -5000.0 < gold["dG_kcal"] < -100.0
