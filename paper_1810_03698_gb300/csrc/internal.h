@@ -109,10 +109,14 @@ struct Tree {
   // (Yukawa terms only)
   DBuf<int> far_ptr, far_list, farL_ptr, farL_list, near_ptr, near_list;
   bool farL_same = true;  // one group: the Laplace lists are the Yukawa lists
-  // target blocks: (leaf number, first panel, count <= 128) for the far field and
-  // (leaf number, first panel, count <= 32) for the near field
-  int nblk = 0, nblk32 = 0, near_splits = 1;
-  DBuf<int4> blk, blk32;
+  // target blocks: (leaf number, first panel, count <= 128) for the far field,
+  // (leaf number, first panel, count <= 32) for the FP64 near field and the transposed
+  // kernels, and (leaf number, first panel, count <= 16) for the FP32 near field;
+  // near_splits / near_splits16: pieces of each near list (grid y) of the 32- and
+  // 16-target near kernels
+  int nblk = 0, nblk32 = 0, nblk16 = 0, nblk16f = 0, near_splits = 1, near_splits16 = 1;
+  DBuf<int4> blk, blk32, blk16;
+  DBuf<int4> blk16f;  // the 16-target blocks in the order of the FP32 far field (most far work first)
   // multipole moments [ncell][2][NC]: single layer M_k, double layer D_k
   DBuf<float> mom32;
   DBuf<double> mom64;

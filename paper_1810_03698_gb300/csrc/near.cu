@@ -171,7 +171,8 @@ __device__ void panel_exact(double xx, double xy, double xz, const double* __res
 __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n, int nnz,
                                  const double4* __restrict__ tgt64, const double* __restrict__ vert9,
                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int K,
-                                 double kappa, const int* __restrict__ ptag, double4* __restrict__ corr) {
+                                 double kappa, const int* __restrict__ ptag, double4* __restrict__ corr,
+                                 int* __restrict__ coincide) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnz) return;
   int lo = 0, hi = n - 1;  // largest row i with ptr[i] <= k
@@ -194,7 +195,10 @@ __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restr
       double4 y = src64[(size_t)K * j + g];
       double rx = x.x - y.x, ry = x.y - y.y, rz = x.z - y.z;
       double r2 = rx * rx + ry * ry + rz * rz;
-      if (r2 == 0.0) continue;
+      if (r2 == 0.0) {
+        if (i != j) atomicExch(coincide, 1);  // only the own panel's centroid node may sit on x_i
+        continue;
+      }
       double R = sqrt(r2);
       double inv = 1.0 / R;
       double nr = nj.x * rx + nj.y * ry + nj.z * rz;
@@ -252,11 +256,21 @@ void build_near(Ctx& c, cudaStream_t s) {
   BP_CUDA(cudaMemcpyAsync(c.near_ptr.p, ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, s));
   launch(near_list_kernel<true>, T.nblk, 128, 0, s, T.blk.p, c.tgt64.p, d_cptr.p, d_ccell.p, T.begin.p, T.end.p,
          nf2, c.near_ptr.p, c.near_col.p);
+  DBuf<int> coincide;
+  coincide.alloc(1);
+  coincide.zero(s);
   launch(near_corr_kernel, cdiv(c.nnz, 128), 128, 0, s, c.near_ptr.p, c.near_col.p, n, (int)c.nnz, c.tgt64.p,
-         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.ptag.p, c.near_corr.p);
+         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.ptag.p, c.near_corr.p, coincide.p);
   BP_CHECK_LAUNCH();
   c.nearT_ready = false;  // the table by columns is built on the first transposed product
+  int bad = 0;
+  BP_CUDA(cudaMemcpyAsync(&bad, coincide.p, sizeof(int), cudaMemcpyDeviceToHost, s));
   BP_CUDA(cudaStreamSynchronize(s));
+  // Two different panels at distance 0 overlap: an invalid surface.  Those within the near
+  // radius are caught here (the FP32 treecode near field sums the sources of other panels
+  // without an r = 0 test).
+  if (bad)
+    fail(BEMPOL_ERR_MESH, "a Gauss node of one panel coincides with the centroid of another (overlapping panels)");
 }
 
 }  // namespace bp

@@ -216,6 +216,89 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
   }
 }
 
+// FP32 far field, one warp per block of <= 16 targets of one leaf.  Lane l serves target
+// (l & 15); the two half-warps take alternate cells of the leaf's far list (half h the
+// cells h, h + 2, ... of every batch) and their sums are added at the end.  Each warp
+// stages its own batches of FW cells' moments with cp.async, double-buffered, and waits
+// only for its own copies (no block-wide barrier: a warp never waits for another).
+constexpr int FW = 8;  // cells per staged batch (four per half-warp)
+
+template <int P, int YUK>
+__global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                                   const int* __restrict__ leaf_cell,
+                                                   const double4* __restrict__ center,
+                                                   const int* __restrict__ far_ptr, const int* __restrict__ far_list,
+                                                   const float* __restrict__ mom, float kappa, int n,
+                                                   const int* __restrict__ active, const int* __restrict__ leaf_sys,
+                                                   double* __restrict__ out) {
+  constexpr int NC = MI<P>::NC;
+  // cp.async when a cell's moments are a whole number of 16-byte pieces (every order but 4)
+  constexpr bool ASYNC = (2 * NC * sizeof(float)) % 16 == 0;
+  constexpr int CH = (int)(2 * NC * sizeof(float) / 16);  // 16-byte pieces per cell
+  __shared__ __align__(16) float sm[2][FW][2 * NC];
+  __shared__ float so[2][FW][3];
+  const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
+  const int4 B = blk[blockIdx.x];
+  const int leaf = B.x;
+  if (active && !active[leaf_sys[leaf]]) return;
+  const double4 ct = center[leaf_cell[leaf]];
+  const int i = B.y + tl;
+  const bool act = tl < B.z;
+  float xr[3] = {0.f, 0.f, 0.f};
+  if (act) {
+    const double4 x = tgt64[i];
+    xr[0] = (float)(x.x - ct.x);
+    xr[1] = (float)(x.y - ct.y);
+    xr[2] = (float)(x.z - ct.z);
+  }
+  double aV = 0, aK = 0;
+  const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
+  auto stage = [&](int b, int fb) {
+    const int cnt = min(FW, f1 - fb);
+    if constexpr (ASYNC) {
+      for (int q = lane; q < cnt * CH; q += 32) {
+        const int cell = q / CH, piece = q - cell * CH;
+        const char* g = reinterpret_cast<const char*>(mom + (size_t)far_list[fb + cell] * 2 * NC) + 16 * piece;
+        cp_async16(reinterpret_cast<char*>(&sm[b][cell][0]) + 16 * piece, g);
+      }
+      cp_async_commit();
+    } else {
+      for (int q = lane; q < cnt * 2 * NC; q += 32)
+        sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+    }
+    if (lane < cnt) {
+      const double4 cc = center[far_list[fb + lane]];
+      so[b][lane][0] = (float)(ct.x - cc.x);
+      so[b][lane][1] = (float)(ct.y - cc.y);
+      so[b][lane][2] = (float)(ct.z - cc.z);
+    }
+  };
+  if (f0 < f1) stage(0, f0);
+  int b = 0;
+  for (int fb = f0; fb < f1; fb += FW, b ^= 1) {
+    const int cnt = min(FW, f1 - fb);
+    if constexpr (ASYNC) cp_async_wait_all();  // this lane's pieces of batch b
+    __syncwarp();  // every lane's pieces and offsets of batch b; all done with the other buffer
+    if (fb + FW < f1) stage(b ^ 1, fb + FW);
+    float v = 0.f, k = 0.f;
+    for (int q = h; q < cnt; q += 2) {
+      const float D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
+      if (YUK)
+        far_eval_yukawa<P, float>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
+      else
+        far_eval_laplace<P, float>(D, sm[b][q], sm[b][q] + NC, v, k);
+    }
+    aV += (double)v;
+    aK += (double)k;
+  }
+  aV += __shfl_down_sync(0xffffffffu, aV, 16);
+  aK += __shfl_down_sync(0xffffffffu, aK, 16);
+  if (h == 0 && act) {
+    out[(2 * YUK) * (size_t)n + i] = aV;
+    out[(2 * YUK + 1) * (size_t)n + i] = aK;
+  }
+}
+
 // ---------------------------------------------------------------- near field
 __device__ __forceinline__ void pair_accum(const float x[3], float4 p, float4 s, float kappa, float nk_log2e,
                                            float& vl, float& kl, float& vy, float& ky) {
@@ -372,6 +455,167 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
   }
 }
 
+// FP32 near field, sixteen targets per warp.  Lane l serves target (l & 15) of a block
+// of <= 16 targets of one leaf, against one half (l >> 4) of every 64-source tile: the
+// two half-warps split the source stream and their sums are added at the end, so a
+// leaf's last, partly filled block leaves at most 15 of 32 lanes idle (with 32 targets
+// per warp the idle share at leaf size 256 is about twice as large).  The leaf's own
+// sources, the only ones that can coincide with a target (the centroid node of its own
+// panel), are summed in a pass of their own with the r = 0 test; every other near leaf
+// is summed without it (a coincident pair of different panels is rejected when the
+// near table is built).  The near list of every leaf holds the leaf itself first.
+// The leaf's near list is cut into gridDim.y consecutive pieces; piece s writes its
+// partial sums to out + s * 4n (the combine kernel adds the pieces in order).
+constexpr int NLC16 = 64;  // near leaves per pass
+constexpr int HT = 33;     // float4 stride between the two half-tiles (shifts the banks)
+
+template <bool SELF>
+__device__ __forceinline__ void half_tile(const float x[3], const float4* __restrict__ P,
+                                          const float4* __restrict__ Sg, int lim, float kappa, float nk_log2e,
+                                          float& vl, float& kl, float& vy, float& ky) {
+  if (lim == 32) {
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const float4 p = P[k], sg = Sg[k];
+      float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+      float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      float rinv = rsqrt_approx(r2);
+      if (SELF) rinv = r2 > 0.f ? rinv : 0.f;
+      float r = r2 * rinv;
+      float e = exp2_approx(r * nk_log2e);
+      float mr = sg.x * rinv;
+      vl = fmaf(mr, p.w, vl);
+      vy = fmaf(mr, e, vy);
+      float t = fmaf(sg.y, dx, fmaf(sg.z, dy, sg.w * dz)) * (rinv * rinv) * rinv;
+      kl = fmaf(t, p.w, kl);
+      ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
+    }
+  } else {
+    for (int k = 0; k < lim; ++k) {
+      const float4 p = P[k], sg = Sg[k];
+      float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
+      float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      float rinv = rsqrt_approx(r2);
+      if (SELF) rinv = r2 > 0.f ? rinv : 0.f;
+      float r = r2 * rinv;
+      float e = exp2_approx(r * nk_log2e);
+      float mr = sg.x * rinv;
+      vl = fmaf(mr, p.w, vl);
+      vy = fmaf(mr, e, vy);
+      float t = fmaf(sg.y, dx, fmaf(sg.z, dy, sg.w * dz)) * (rinv * rinv) * rinv;
+      kl = fmaf(t, p.w, kl);
+      ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                                    const int* __restrict__ leaf_cell,
+                                                    const double4* __restrict__ center, const int* __restrict__ begin,
+                                                    const int* __restrict__ end, const int* __restrict__ near_ptr,
+                                                    const int* __restrict__ near_list, int K,
+                                                    const float4* __restrict__ str, float kappa, float nk_log2e,
+                                                    int n, const float4* __restrict__ src_rel,
+                                                    const int* __restrict__ active, const int* __restrict__ leaf_sys,
+                                                    double* __restrict__ out) {
+  __shared__ __align__(16) float4 sp[2 * HT];
+  __shared__ __align__(16) float4 ss[2 * HT];
+  __shared__ int lb[NLC16];        // first source index of each leaf of the pass
+  __shared__ int lc[NLC16 + 1];    // cumulative source counts
+  __shared__ float lo3[NLC16][4];  // FP32 offset (source-leaf centre - target-leaf centre), Laplace weight
+  const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
+  const int4 B = blk[blockIdx.x];
+  const int leaf = B.x;
+  if (active && !active[leaf_sys[leaf]]) return;
+  const double4 ct = center[leaf_cell[leaf]];
+  const int i = B.y + tl;
+  const bool act = tl < B.z;
+  float xr[3] = {0.f, 0.f, 0.f};
+  if (act) {
+    const double4 x = tgt64[i];
+    xr[0] = (float)(x.x - ct.x);
+    xr[1] = (float)(x.y - ct.y);
+    xr[2] = (float)(x.z - ct.z);
+  }
+  double acc[4] = {0, 0, 0, 0};
+  const int base = near_ptr[leaf];
+  const int nl = near_ptr[leaf + 1] - base;
+  const int e0 = base + (int)(((long long)nl * blockIdx.y) / gridDim.y);
+  const int e1 = base + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
+  for (int eb = e0; eb < e1;) {
+    const bool self = eb == base && near_list[base] == leaf;  // the leaf itself, alone in its pass
+    const int cnt = self ? 1 : min(NLC16, e1 - eb);
+    __syncwarp();  // the previous pass is done with the leaf table
+    for (int q = lane; q < cnt; q += 32) {
+      const int ent = near_list[eb + q];
+      const int cl = leaf_cell[ent & ~NEAR_CROSS];
+      lb[q] = begin[cl] * K;
+      lc[q + 1] = (end[cl] - begin[cl]) * K;
+      const double4 cs = center[cl];
+      lo3[q][0] = (float)(cs.x - ct.x);
+      lo3[q][1] = (float)(cs.y - ct.y);
+      lo3[q][2] = (float)(cs.z - ct.z);
+      lo3[q][3] = (ent & NEAR_CROSS) ? 0.f : 1.f;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      lc[0] = 0;
+      for (int q = 1; q <= cnt; ++q) lc[q] += lc[q - 1];
+    }
+    __syncwarp();
+    const int total = lc[cnt];
+    float vl = 0.f, kl = 0.f, vy = 0.f, ky = 0.f;
+    int ntile = 0;
+    int lo0 = 0, lo1 = 0;  // leaf of this lane's two staged sources (indices only grow)
+    for (int t0 = 0; t0 < total; t0 += 64) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = t0 + 32 * u + lane;
+        int& lo = u ? lo1 : lo0;
+        float4 pz = make_float4(0.f, 0.f, 0.f, 0.f), sz = pz;
+        if (j < total) {
+          while (lc[lo + 1] <= j) ++lo;
+          const int src = lb[lo] + (j - lc[lo]);
+          const float4 r = src_rel[src];
+          pz = make_float4(r.x + lo3[lo][0], r.y + lo3[lo][1], r.z + lo3[lo][2], lo3[lo][3]);
+          sz = str[src];
+        }
+        sp[u * HT + lane] = pz;
+        ss[u * HT + lane] = sz;
+      }
+      __syncwarp();
+      const int lim = min(32, max(0, total - t0 - 32 * h));
+      if (self)
+        half_tile<true>(xr, sp + h * HT, ss + h * HT, lim, kappa, nk_log2e, vl, kl, vy, ky);
+      else
+        half_tile<false>(xr, sp + h * HT, ss + h * HT, lim, kappa, nk_log2e, vl, kl, vy, ky);
+      if (++ntile == 4) {  // FP32 sums over at most 128 pairs per lane, then FP64
+        acc[0] += (double)vl;
+        acc[1] += (double)kl;
+        acc[2] += (double)vy;
+        acc[3] += (double)ky;
+        vl = kl = vy = ky = 0.f;
+        ntile = 0;
+      }
+      __syncwarp();
+    }
+    acc[0] += (double)vl;
+    acc[1] += (double)kl;
+    acc[2] += (double)vy;
+    acc[3] += (double)ky;
+    eb += cnt;
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+  if (h == 0 && act) {
+    double* o = out + (size_t)blockIdx.y * 4 * n;
+    o[i] = acc[0];
+    o[n + i] = acc[1];
+    o[2 * n + i] = acc[2];
+    o[3 * n + i] = acc[3];
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -450,7 +694,7 @@ void build_lists(Ctx& c, cudaStream_t s) {
   std::vector<int> leaf_of(T.ncell, -1);
   for (int l = 0; l < T.nleaf; ++l) leaf_of[T.h_leaf_cell[l]] = l;
   std::vector<int> fptr(T.nleaf + 1, 0), lptr(T.nleaf + 1, 0), nptr(T.nleaf + 1, 0), flist, llist, nlist;
-  std::vector<int4> blk, blk32;
+  std::vector<int4> blk, blk32, blk16;
   std::vector<int> stack;
   long long pairs = 0, fars = 0, farsL = 0;
   for (int l = 0; l < T.nleaf; ++l) {
@@ -472,7 +716,9 @@ void build_lists(Ctx& c, cudaStream_t s) {
       const double4 b = T.h_center[q];
       const double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
       const double gap = std::sqrt(dx * dx + dy * dy + dz * dz) - a.w;
-      if (q != ct && gap > 0.0 && b.w < theta * gap) {
+      // a cell holding the target leaf is never accepted (possible only for theta >= 1)
+      const bool holds = T.h_begin[q] <= T.h_begin[ct] && T.h_end[ct] <= T.h_end[q];
+      if (!holds && gap > 0.0 && b.w < theta * gap) {
         flist.push_back(q);
         fars += ntgt;
         if (cg == g) {
@@ -486,6 +732,12 @@ void build_lists(Ctx& c, cudaStream_t s) {
         for (int k = T.h_nchild[q] - 1; k >= 0; --k) stack.push_back(T.h_child0[q] + k);
       }
     }
+    // the leaf itself first in its near list (the FP32 near kernel sums it in a pass of its own)
+    for (size_t e = (size_t)nptr[l]; e < nlist.size(); ++e)
+      if (nlist[e] == l) {
+        std::rotate(nlist.begin() + nptr[l], nlist.begin() + e, nlist.begin() + e + 1);
+        break;
+      }
     fptr[l + 1] = (int)flist.size();
     lptr[l + 1] = (int)llist.size();
     nptr[l + 1] = (int)nlist.size();
@@ -493,6 +745,8 @@ void build_lists(Ctx& c, cudaStream_t s) {
       blk.push_back(make_int4(l, T.h_begin[ct] + off, std::min(TBT, ntgt - off), 0));
     for (int off = 0; off < ntgt; off += 32)
       blk32.push_back(make_int4(l, T.h_begin[ct] + off, std::min(32, ntgt - off), 0));
+    for (int off = 0; off < ntgt; off += 16)
+      blk16.push_back(make_int4(l, T.h_begin[ct] + off, std::min(16, ntgt - off), 0));
   }
   // largest blocks first: the grids are only one or two waves deep, so launching the
   // long blocks early shortens the tail (each block's result does not depend on order)
@@ -510,6 +764,13 @@ void build_lists(Ctx& c, cudaStream_t s) {
   std::stable_sort(blk32.begin(), blk32.end(), [&](const int4& u, const int4& v) {
     return near_work[u.x] * u.z > near_work[v.x] * v.z;
   });
+  std::vector<int4> blk16f = blk16;
+  std::stable_sort(blk16.begin(), blk16.end(), [&](const int4& u, const int4& v) {
+    return near_work[u.x] > near_work[v.x];  // a block's time does not depend on its fill
+  });
+  std::stable_sort(blk16f.begin(), blk16f.end(), [&](const int4& u, const int4& v) {
+    return far_work[u.x] > far_work[v.x];
+  });
   // shallowest tree depth that holds an accepted cell: moments above it are never read
   T.m2m_min_depth = T.ndepth;
   for (int q : flist) {
@@ -521,7 +782,12 @@ void build_lists(Ctx& c, cudaStream_t s) {
   T.nblk32 = (int)blk32.size();
   // split each near-field block's source stream so the grid holds ~56 warps per SM
   T.near_splits = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk32))));
+  T.nblk16 = (int)blk16.size();
+  T.near_splits16 = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk16))));
   upload(T.blk32, blk32, s);
+  upload(T.blk16, blk16, s);
+  T.nblk16f = (int)blk16f.size();
+  upload(T.blk16f, blk16f, s);
   T.pairs_per_matvec = pairs;
   T.far_per_matvec = fars;
   T.farL_per_matvec = farsL;
@@ -544,6 +810,7 @@ void build_lists(Ctx& c, cudaStream_t s) {
 template <int P, typename Real>
 void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   Tree& T = c.tree;
+  constexpr bool F64 = sizeof(Real) == 8;
   constexpr int NC = MI<P>::NC;
   if (T.mom_order != P || mom.n < (size_t)T.ncell * 2 * NC) {
     mom.alloc((size_t)T.ncell * 2 * NC);
@@ -555,7 +822,7 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str32.p);
   else
     str = reinterpret_cast<const R4*>(c.str64.p);
-  const int S = T.near_splits;
+  const int S = F64 ? T.near_splits : T.near_splits16;
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
@@ -568,7 +835,6 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   const cudaStream_t sf = c.aux;
   // accounting: FP32 products per kernel (pair, far) and whole; FP64 products (the
   // refinement residuals) whole only, under their own kind
-  constexpr bool F64 = sizeof(Real) == 8;
   Ctx::Timed tp;
   c.time_begin(F64 ? 6 : 2, s, tp);
   BP_CUDA(cudaEventRecord(c.ev_fork, s));
@@ -587,19 +853,31 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
   const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
   const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
-  launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
-         kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
-         T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  if constexpr (F64) {
+    launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
+           kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+    launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
+           T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  } else {
+    launch(far16_kernel<P, 0>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll,
+           mom.p, (float)kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+    launch(far16_kernel<P, 1>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+           T.far_ptr.p, T.far_list.p, mom.p, (float)kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  }
   if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
   if (!F64) {
     c.time_begin(0, s, tm);
     c.stat_pairs += T.pairs_per_matvec;
   }
-  launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-         T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
-         c.mv_active, T.leaf_sys.p, c.part.p);
+  if constexpr (F64)
+    launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+           T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
+           c.mv_active, T.leaf_sys.p, c.part.p);
+  else
+    launch(near16_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.begin.p,
+           T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.str32.p, (float)kappa, (float)nk, c.n, T.src_rel32.p,
+           c.mv_active, T.leaf_sys.p, c.part.p);
   if (!F64) c.time_end(s, tm);
   BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join
   BP_CUDA(cudaStreamWaitEvent(s, c.ev_join, 0));
