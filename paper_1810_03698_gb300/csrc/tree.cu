@@ -455,57 +455,90 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
   }
 }
 
-// FP32 near field, sixteen targets per warp.  Lane l serves target (l & 15) of a block
-// of <= 16 targets of one leaf, against one half (l >> 4) of every 64-source tile: the
-// two half-warps split the source stream and their sums are added at the end, so a
-// leaf's last, partly filled block leaves at most 15 of 32 lanes idle (with 32 targets
-// per warp the idle share at leaf size 256 is about twice as large).  The leaf's own
-// sources, the only ones that can coincide with a target (the centroid node of its own
-// panel), are summed in a pass of their own with the r = 0 test; every other near leaf
-// is summed without it (a coincident pair of different panels is rejected when the
-// near table is built).  The near list of every leaf holds the leaf itself first.
-// The leaf's near list is cut into gridDim.y consecutive pieces; piece s writes its
-// partial sums to out + s * 4n (the combine kernel adds the pieces in order).
+// FP32 near field, sixteen targets per warp, with paired FP32 arithmetic.  Lane l
+// serves target (l & 15) of a block of <= 16 targets of one leaf, against one half
+// (l >> 4) of every 64-source tile: the two half-warps split the source stream and their
+// sums are added at the end, so a leaf's last, partly filled block leaves at most 15 of
+// 32 lanes idle (with 32 targets per warp the idle share at leaf size 256 is about twice
+// as large).  Each lane takes its sources two at a time: the staged tile holds sources
+// 2m and 2m + 1 of a half side by side in every component, so every FP32 operation of
+// the pair formula runs as one f32x2 instruction for both (sm_100 family), and only the
+// reciprocal square root and 2^x stay one per pair.  The leaf's own sources, the only
+// ones that can coincide with a target (the centroid node of its own panel), are summed
+// in a pass of their own with the r = 0 test; every other near leaf is summed without it
+// (a coincident pair of different panels is rejected when the near table is built).
+// The near list of every leaf holds the leaf itself first.  The leaf's near list is cut
+// into gridDim.y consecutive pieces; piece s writes its partial sums to out + s * 4n
+// (the combine kernel adds the pieces in order).
 constexpr int NLC16 = 64;  // near leaves per pass
-constexpr int HT = 33;     // float4 stride between the two half-tiles (shifts the banks)
+constexpr int HP = 17;     // float4 stride between the two half-tiles (16 pairs + 1: shifts the banks)
+constexpr float FAR_PAD = 1.0e4f;  // position of the padding source of an odd half-tile (zero strength)
+
+typedef unsigned long long f2;  // two FP32 values in one 64-bit register (low = first)
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void upk(f2 v, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v)); }
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
+// staged half-tile, per pair m of sources (2m, 2m + 1): A = (x0, x1, y0, y1),
+// Bz = (z0, z1, w0, w1) with w the Laplace weight, C = (m0, m1, dx0, dx1), D = (dy0, dy1, dz0, dz1)
+struct PairTile {
+  float4 A[2 * HP], Bz[2 * HP], C[2 * HP], D[2 * HP];
+};
 
 template <bool SELF>
-__device__ __forceinline__ void half_tile(const float x[3], const float4* __restrict__ P,
-                                          const float4* __restrict__ Sg, int lim, float kappa, float nk_log2e,
-                                          float& vl, float& kl, float& vy, float& ky) {
-  if (lim == 32) {
-#pragma unroll 8
-    for (int k = 0; k < 32; ++k) {
-      const float4 p = P[k], sg = Sg[k];
-      float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
-      float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      float rinv = rsqrt_approx(r2);
-      if (SELF) rinv = r2 > 0.f ? rinv : 0.f;
-      float r = r2 * rinv;
-      float e = exp2_approx(r * nk_log2e);
-      float mr = sg.x * rinv;
-      vl = fmaf(mr, p.w, vl);
-      vy = fmaf(mr, e, vy);
-      float t = fmaf(sg.y, dx, fmaf(sg.z, dy, sg.w * dz)) * (rinv * rinv) * rinv;
-      kl = fmaf(t, p.w, kl);
-      ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
-    }
+__device__ __forceinline__ void pair_x2(f2 X, f2 Y, f2 Z, const PairTile& T, int m, f2 K2, f2 NK2, f2 ONE2, f2* a) {
+  const float4 va = T.A[m], vb = T.Bz[m], vc = T.C[m], vd = T.D[m];
+  const f2 dx = sub2(X, pk(va.x, va.y)), dy = sub2(Y, pk(va.z, va.w)), dz = sub2(Z, pk(vb.x, vb.y));
+  const f2 pw = pk(vb.z, vb.w);
+  const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
+  float r2a, r2b;
+  upk(r2, r2a, r2b);
+  float ra = rsqrt_approx(r2a), rb = rsqrt_approx(r2b);
+  if (SELF) {
+    ra = r2a > 0.f ? ra : 0.f;
+    rb = r2b > 0.f ? rb : 0.f;
+  }
+  const f2 rinv = pk(ra, rb);
+  const f2 r = mul2(r2, rinv);
+  float ea, eb;
+  upk(mul2(r, NK2), ea, eb);
+  const f2 e = pk(exp2_approx(ea), exp2_approx(eb));
+  const f2 mr = mul2(pk(vc.x, vc.y), rinv);
+  a[0] = fma2(mr, pw, a[0]);
+  a[2] = fma2(mr, e, a[2]);
+  const f2 dR = fma2(pk(vc.z, vc.w), dx, fma2(pk(vd.x, vd.y), dy, mul2(pk(vd.z, vd.w), dz)));
+  const f2 t = mul2(mul2(dR, mul2(rinv, rinv)), rinv);
+  a[1] = fma2(t, pw, a[1]);
+  a[3] = fma2(mul2(t, fma2(K2, r, ONE2)), e, a[3]);
+}
+
+template <bool SELF>
+__device__ __forceinline__ void half_tile_x2(f2 X, f2 Y, f2 Z, const PairTile& T, int base, int npair, f2 K2,
+                                             f2 NK2, f2 ONE2, f2* a) {
+  if (npair == 16) {
+#pragma unroll 4
+    for (int m = 0; m < 16; ++m) pair_x2<SELF>(X, Y, Z, T, base + m, K2, NK2, ONE2, a);
   } else {
-    for (int k = 0; k < lim; ++k) {
-      const float4 p = P[k], sg = Sg[k];
-      float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
-      float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      float rinv = rsqrt_approx(r2);
-      if (SELF) rinv = r2 > 0.f ? rinv : 0.f;
-      float r = r2 * rinv;
-      float e = exp2_approx(r * nk_log2e);
-      float mr = sg.x * rinv;
-      vl = fmaf(mr, p.w, vl);
-      vy = fmaf(mr, e, vy);
-      float t = fmaf(sg.y, dx, fmaf(sg.z, dy, sg.w * dz)) * (rinv * rinv) * rinv;
-      kl = fmaf(t, p.w, kl);
-      ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
-    }
+    for (int m = 0; m < npair; ++m) pair_x2<SELF>(X, Y, Z, T, base + m, K2, NK2, ONE2, a);
   }
 }
 
@@ -518,8 +551,7 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
                                                     int n, const float4* __restrict__ src_rel,
                                                     const int* __restrict__ active, const int* __restrict__ leaf_sys,
                                                     double* __restrict__ out) {
-  __shared__ __align__(16) float4 sp[2 * HT];
-  __shared__ __align__(16) float4 ss[2 * HT];
+  __shared__ __align__(16) PairTile T;
   __shared__ int lb[NLC16];        // first source index of each leaf of the pass
   __shared__ int lc[NLC16 + 1];    // cumulative source counts
   __shared__ float lo3[NLC16][4];  // FP32 offset (source-leaf centre - target-leaf centre), Laplace weight
@@ -537,11 +569,15 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
     xr[1] = (float)(x.y - ct.y);
     xr[2] = (float)(x.z - ct.z);
   }
+  const f2 X = pk(xr[0], xr[0]), Y = pk(xr[1], xr[1]), Z = pk(xr[2], xr[2]);
+  const f2 K2 = pk(kappa, kappa), NK2 = pk(nk_log2e, nk_log2e), ONE2 = pk(1.f, 1.f);
   double acc[4] = {0, 0, 0, 0};
   const int base = near_ptr[leaf];
   const int nl = near_ptr[leaf + 1] - base;
   const int e0 = base + (int)(((long long)nl * blockIdx.y) / gridDim.y);
   const int e1 = base + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
+  // this lane stages stream-local source `lane` of both halves: pair lane / 2, slot lane & 1
+  const int pm = lane >> 1, slot = lane & 1;
   for (int eb = e0; eb < e1;) {
     const bool self = eb == base && near_list[base] == leaf;  // the leaf itself, alone in its pass
     const int cnt = self ? 1 : min(NLC16, e1 - eb);
@@ -564,7 +600,7 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
     }
     __syncwarp();
     const int total = lc[cnt];
-    float vl = 0.f, kl = 0.f, vy = 0.f, ky = 0.f;
+    f2 f[4] = {0ull, 0ull, 0ull, 0ull};  // per-lane FP32 sums (even, odd source)
     int ntile = 0;
     int lo0 = 0, lo1 = 0;  // leaf of this lane's two staged sources (indices only grow)
     for (int t0 = 0; t0 < total; t0 += 64) {
@@ -572,37 +608,55 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
       for (int u = 0; u < 2; ++u) {
         const int j = t0 + 32 * u + lane;
         int& lo = u ? lo1 : lo0;
-        float4 pz = make_float4(0.f, 0.f, 0.f, 0.f), sz = pz;
+        float px = FAR_PAD, py = FAR_PAD, pz = FAR_PAD, pw = 0.f;
+        float4 sz = make_float4(0.f, 0.f, 0.f, 0.f);
         if (j < total) {
           while (lc[lo + 1] <= j) ++lo;
           const int src = lb[lo] + (j - lc[lo]);
           const float4 r = src_rel[src];
-          pz = make_float4(r.x + lo3[lo][0], r.y + lo3[lo][1], r.z + lo3[lo][2], lo3[lo][3]);
+          px = r.x + lo3[lo][0];
+          py = r.y + lo3[lo][1];
+          pz = r.z + lo3[lo][2];
+          pw = lo3[lo][3];
           sz = str[src];
         }
-        sp[u * HT + lane] = pz;
-        ss[u * HT + lane] = sz;
+        float* a = reinterpret_cast<float*>(&T.A[u * HP + pm]);
+        float* bq = reinterpret_cast<float*>(&T.Bz[u * HP + pm]);
+        float* c = reinterpret_cast<float*>(&T.C[u * HP + pm]);
+        float* d = reinterpret_cast<float*>(&T.D[u * HP + pm]);
+        a[slot] = px;
+        a[2 + slot] = py;
+        bq[slot] = pz;
+        bq[2 + slot] = pw;
+        c[slot] = sz.x;
+        c[2 + slot] = sz.y;
+        d[slot] = sz.z;
+        d[2 + slot] = sz.w;
       }
       __syncwarp();
-      const int lim = min(32, max(0, total - t0 - 32 * h));
+      const int lim = min(32, max(0, total - t0 - 32 * h));  // sources of this half
       if (self)
-        half_tile<true>(xr, sp + h * HT, ss + h * HT, lim, kappa, nk_log2e, vl, kl, vy, ky);
+        half_tile_x2<true>(X, Y, Z, T, h * HP, (lim + 1) >> 1, K2, NK2, ONE2, f);
       else
-        half_tile<false>(xr, sp + h * HT, ss + h * HT, lim, kappa, nk_log2e, vl, kl, vy, ky);
-      if (++ntile == 4) {  // FP32 sums over at most 128 pairs per lane, then FP64
-        acc[0] += (double)vl;
-        acc[1] += (double)kl;
-        acc[2] += (double)vy;
-        acc[3] += (double)ky;
-        vl = kl = vy = ky = 0.f;
+        half_tile_x2<false>(X, Y, Z, T, h * HP, (lim + 1) >> 1, K2, NK2, ONE2, f);
+      if (++ntile == 4) {  // FP32 sums over at most 64 pairs per slot and lane, then FP64
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          float lo_, hi_;
+          upk(f[c], lo_, hi_);
+          acc[c] += (double)lo_ + (double)hi_;
+          f[c] = 0ull;
+        }
         ntile = 0;
       }
       __syncwarp();
     }
-    acc[0] += (double)vl;
-    acc[1] += (double)kl;
-    acc[2] += (double)vy;
-    acc[3] += (double)ky;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      float lo_, hi_;
+      upk(f[c], lo_, hi_);
+      acc[c] += (double)lo_ + (double)hi_;
+    }
     eb += cnt;
   }
 #pragma unroll
