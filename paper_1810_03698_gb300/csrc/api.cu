@@ -82,6 +82,18 @@ Ctx::~Ctx() {
   }
 }
 
+void check_device_error(Ctx& c, cudaStream_t s) {
+  if (!c.dev_err.p) return;
+  int v = 0;
+  BP_CUDA(cudaMemcpyAsync(&v, c.dev_err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+  if (v) {
+    c.dev_err.zero(s);
+    BP_CUDA(cudaStreamSynchronize(s));
+    fail(BEMPOL_ERR_TIMEOUT, "a device-side wait of the FP32 near-field kernel exceeded its limit; results invalid");
+  }
+}
+
 int num_sms(int device) {
   static int cache[64] = {0};
   if (device < 0 || device >= 64) device = 0;
@@ -437,6 +449,8 @@ bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out
     c->device = device;
     init_gauss_legendre();
     c->scal.alloc(16);
+    c->dev_err.alloc(1);
+    BP_CUDA(cudaMemset(c->dev_err.p, 0, sizeof(int)));
     BP_CUDA(cudaMallocHost(&c->h_pinned, 16 * sizeof(double)));
   } catch (const Error& e) {
     delete c;
@@ -660,6 +674,7 @@ bempol_status bempol_stats_read(bempol_ctx* c, bempol_stats* out, int reset) {
   return guard(c, [&] {
     if (!out) fail(BEMPOL_ERR_ARG, "out is NULL");
     BP_CUDA(cudaDeviceSynchronize());
+    check_device_error(*c, 0);
     c->collect_timers();
     out->kernel_launches = g_launches.load() - c->launches_at_reset;
     out->pair_launches = c->stat_launches[0];
@@ -971,6 +986,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     put(out->mu_diss, mu.p, 3 * (size_t)ns);
     put(out->mu_vac, mu_v.p, 3 * (size_t)ns);
     BP_CUDA(cudaStreamSynchronize(s));
+    check_device_error(*c, s);
     c->have_solution = true;
     out->t_total_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - wall0).count();
     for (int q = 0; q < S; ++q)
@@ -993,6 +1009,7 @@ bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, doubl
     if (!c->have_sites || !c->have_solution) fail(BEMPOL_ERR_STATE, "bempol_gradient needs a completed solve");
     EventTimer t(s);
     AdjointOut ao = gradient_internal(*c, grad_q, grad_d, grad_Q, grad_pos, s);
+    check_device_error(*c, s);
     const double ms = t.ms();
     if (info) {
       info->scf_iters_diss = ao.iters_diss;

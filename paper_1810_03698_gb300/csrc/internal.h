@@ -124,6 +124,14 @@ struct Tree {
   // FP32 Gauss-node positions relative to the centre of their own leaf (x, y, z, 0),
   // and the same for the collocation points
   DBuf<float4> src_rel32, cen_rel32;
+  // Gauss nodes of every leaf in pairs for the FP32 near field (a leaf with an odd count
+  // ends with a padding node): leaf l owns pairs [pair_ptr[l], pair_ptr[l+1]); pair_src[p]
+  // is the pair's first node (~node when the second is padding); positions relative to the
+  // leaf centre PA = (x0, x1, y0, y1), PB = (z0, z1, 0, 0) and strengths SA = (m0, m1,
+  // d0x, d1x), SB = (d0y, d1y, d0z, d1z) side by side
+  int npair = 0;
+  DBuf<int> pair_ptr, pair_src;
+  DBuf<float4> pairPA, pairPB, pairSA, pairSB;
   // charge moments of the transposed product (Laplace, Yukawa)
   DBuf<float> momT32[2];
   DBuf<double> momT64[2];
@@ -224,6 +232,9 @@ struct Ctx {
   cudaEvent_t gm_ev[2] = {nullptr, nullptr};  // residual copies of alternate GMRES iterations
   DBuf<double> vec_a, vec_b, vec_c, vec_d;   // [2n] scratch vectors
   DBuf<double> scal;         // device scalars
+  // set by a kernel whose bounded device-side wait ran out (read and cleared by the
+  // synchronising entry points, which then return BEMPOL_ERR_TIMEOUT)
+  DBuf<int> dev_err;
   double* h_pinned = nullptr;  // pinned host scalars
   int gm_m = 0;
 
@@ -296,6 +307,10 @@ bempol_status guard(Ctx* c, F&& f) {
     return BEMPOL_ERR_ARG;
   }
 }
+
+// BEMPOL_ERR_TIMEOUT if a kernel's bounded wait ran out since the last check (clears the
+// flag; synchronises s)
+void check_device_error(Ctx& c, cudaStream_t s);
 
 // ---------------------------------------------------------------- launch helpers
 inline int cdiv(long long a, long long b) { return (int)((a + b - 1) / b); }

@@ -455,24 +455,37 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
   }
 }
 
-// FP32 near field, sixteen targets per warp, with paired FP32 arithmetic.  Lane l
-// serves target (l & 15) of a block of <= 16 targets of one leaf, against one half
-// (l >> 4) of every 64-source tile: the two half-warps split the source stream and their
-// sums are added at the end, so a leaf's last, partly filled block leaves at most 15 of
-// 32 lanes idle (with 32 targets per warp the idle share at leaf size 256 is about twice
-// as large).  Each lane takes its sources two at a time: the staged tile holds sources
-// 2m and 2m + 1 of a half side by side in every component, so every FP32 operation of
-// the pair formula runs as one f32x2 instruction for both (sm_100 family), and only the
-// reciprocal square root and 2^x stay one per pair.  The leaf's own sources, the only
-// ones that can coincide with a target (the centroid node of its own panel), are summed
-// in a pass of their own with the r = 0 test; every other near leaf is summed without it
-// (a coincident pair of different panels is rejected when the near table is built).
-// The near list of every leaf holds the leaf itself first.  The leaf's near list is cut
-// into gridDim.y consecutive pieces; piece s writes its partial sums to out + s * 4n
-// (the combine kernel adds the pieces in order).
-constexpr int NLC16 = 64;  // near leaves per pass
-constexpr int HP = 17;     // float4 stride between the two half-tiles (16 pairs + 1: shifts the banks)
-constexpr float FAR_PAD = 1.0e4f;  // position of the padding source of an odd half-tile (zero strength)
+// ---------------------------------------------------------------- FP32 near field
+// Sixteen targets per warp, paired FP32 arithmetic, sources staged by 1-D bulk copies.
+//
+// Source records: the Gauss nodes of every leaf, taken two at a time (a leaf with an odd
+// count gets a padding node far away with zero strength), stored side by side in every
+// component: positions relative to the node's own leaf centre PA = (x0, x1, y0, y1),
+// PB = (z0, z1, 0, 0) (once per mesh), strengths SA = (m0, m1, d0x, d1x),
+// SB = (d0y, d1y, d0z, d1z) (once per product).  Leaf L owns the pairs
+// [pair_ptr[L], pair_ptr[L+1]).
+//
+// Lane l serves target (l & 15) of a block of <= 16 targets of one leaf; the two
+// half-warps take alternate pairs of every staged chunk and their sums are added at the
+// end, so a leaf's last, partly filled block leaves at most 15 of 32 lanes idle (with 32
+// targets per warp the idle share at leaf size 256 is about twice as large).  For each
+// near leaf the target is put in that leaf's frame once (x - c_L, formed in FP64), so the
+// loop over its sources is the pair formula alone: every FP32 operation runs as one
+// f32x2 instruction for the two nodes of a pair (sm_100 family), only the reciprocal
+// square root and 2^x stay one per node.  Chunks of CP pairs are copied into shared
+// memory by lane 0 with cp.async.bulk (completion on an mbarrier), double-buffered, so
+// the next chunk is in flight while the current one is summed.  Every wait on an
+// mbarrier is bounded: past MBAR_SPIN polls the kernel sets *err, waits (bounded) for
+// its other copy in flight and returns without writing.
+//
+// The leaf itself is the only near leaf whose nodes can coincide with a target (the
+// centroid node of the target's own panel), so only its sums carry the r = 0 test (a
+// coincident pair of different panels is rejected when the near table is built).  The
+// leaf's near list is cut into gridDim.y consecutive pieces; piece s writes its partial
+// sums to out + s * 4n (the combine kernel adds the pieces in order).
+constexpr int CP = 64;             // source pairs per staged chunk
+constexpr float FAR_PAD = 1.0e4f;  // leaf-relative position of a padding node (zero strength)
+constexpr int MBAR_SPIN = 1 << 20; // polls of an mbarrier before a wait is declared failed
 
 typedef unsigned long long f2;  // two FP32 values in one 64-bit register (low = first)
 
@@ -498,17 +511,43 @@ __device__ __forceinline__ f2 sub2(f2 a, f2 b) {
   return d;
 }
 
-// staged half-tile, per pair m of sources (2m, 2m + 1): A = (x0, x1, y0, y1),
-// Bz = (z0, z1, w0, w1) with w the Laplace weight, C = (m0, m1, dx0, dx1), D = (dy0, dy1, dz0, dz1)
-struct PairTile {
-  float4 A[2 * HP], Bz[2 * HP], C[2 * HP], D[2 * HP];
+// mbarrier and 1-D bulk copy (global -> this CTA's shared memory), sm_90 and later
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (int it = 0; it < MBAR_SPIN; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+struct NearChunk {
+  float4 PA[CP], PB[CP], SA[CP], SB[CP];
 };
 
 template <bool SELF>
-__device__ __forceinline__ void pair_x2(f2 X, f2 Y, f2 Z, const PairTile& T, int m, f2 K2, f2 NK2, f2 ONE2, f2* a) {
-  const float4 va = T.A[m], vb = T.Bz[m], vc = T.C[m], vd = T.D[m];
+__device__ __forceinline__ void pair_x2(f2 X, f2 Y, f2 Z, const NearChunk& T, int m, f2 PW, f2 K2, f2 NK2,
+                                        f2 ONE2, f2* a) {
+  const float4 va = T.PA[m], vb = T.PB[m], vc = T.SA[m], vd = T.SB[m];
   const f2 dx = sub2(X, pk(va.x, va.y)), dy = sub2(Y, pk(va.z, va.w)), dz = sub2(Z, pk(vb.x, vb.y));
-  const f2 pw = pk(vb.z, vb.w);
   const f2 r2 = fma2(dx, dx, fma2(dy, dy, mul2(dz, dz)));
   float r2a, r2b;
   upk(r2, r2a, r2b);
@@ -523,142 +562,142 @@ __device__ __forceinline__ void pair_x2(f2 X, f2 Y, f2 Z, const PairTile& T, int
   upk(mul2(r, NK2), ea, eb);
   const f2 e = pk(exp2_approx(ea), exp2_approx(eb));
   const f2 mr = mul2(pk(vc.x, vc.y), rinv);
-  a[0] = fma2(mr, pw, a[0]);
+  a[0] = fma2(mr, PW, a[0]);
   a[2] = fma2(mr, e, a[2]);
   const f2 dR = fma2(pk(vc.z, vc.w), dx, fma2(pk(vd.x, vd.y), dy, mul2(pk(vd.z, vd.w), dz)));
   const f2 t = mul2(mul2(dR, mul2(rinv, rinv)), rinv);
-  a[1] = fma2(t, pw, a[1]);
+  a[1] = fma2(t, PW, a[1]);
   a[3] = fma2(mul2(t, fma2(K2, r, ONE2)), e, a[3]);
 }
 
+// pairs h, h + 2, h + 4, ... of a staged chunk of `cnt` pairs
 template <bool SELF>
-__device__ __forceinline__ void half_tile_x2(f2 X, f2 Y, f2 Z, const PairTile& T, int base, int npair, f2 K2,
-                                             f2 NK2, f2 ONE2, f2* a) {
-  if (npair == 16) {
+__device__ __forceinline__ void chunk_x2(f2 X, f2 Y, f2 Z, const NearChunk& T, int h, int cnt, f2 PW, f2 K2, f2 NK2,
+                                         f2 ONE2, f2* a) {
+  if (cnt == CP) {
 #pragma unroll 4
-    for (int m = 0; m < 16; ++m) pair_x2<SELF>(X, Y, Z, T, base + m, K2, NK2, ONE2, a);
+    for (int m = h; m < CP; m += 2) pair_x2<SELF>(X, Y, Z, T, m, PW, K2, NK2, ONE2, a);
   } else {
-    for (int m = 0; m < npair; ++m) pair_x2<SELF>(X, Y, Z, T, base + m, K2, NK2, ONE2, a);
+    for (int m = h; m < cnt; m += 2) pair_x2<SELF>(X, Y, Z, T, m, PW, K2, NK2, ONE2, a);
   }
 }
 
 __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                     const int* __restrict__ leaf_cell,
-                                                    const double4* __restrict__ center, const int* __restrict__ begin,
-                                                    const int* __restrict__ end, const int* __restrict__ near_ptr,
-                                                    const int* __restrict__ near_list, int K,
-                                                    const float4* __restrict__ str, float kappa, float nk_log2e,
-                                                    int n, const float4* __restrict__ src_rel,
+                                                    const double4* __restrict__ center,
+                                                    const int* __restrict__ near_ptr,
+                                                    const int* __restrict__ near_list,
+                                                    const int* __restrict__ pair_ptr, const float4* __restrict__ PA,
+                                                    const float4* __restrict__ PB, const float4* __restrict__ SA,
+                                                    const float4* __restrict__ SB, float kappa, float nk_log2e, int n,
                                                     const int* __restrict__ active, const int* __restrict__ leaf_sys,
-                                                    double* __restrict__ out) {
-  __shared__ __align__(16) PairTile T;
-  __shared__ int lb[NLC16];        // first source index of each leaf of the pass
-  __shared__ int lc[NLC16 + 1];    // cumulative source counts
-  __shared__ float lo3[NLC16][4];  // FP32 offset (source-leaf centre - target-leaf centre), Laplace weight
+                                                    double* __restrict__ out, int* __restrict__ err) {
+  __shared__ __align__(128) NearChunk st[2];
+  __shared__ __align__(8) unsigned long long bar[2];
   const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
   if (active && !active[leaf_sys[leaf]]) return;
-  const double4 ct = center[leaf_cell[leaf]];
   const int i = B.y + tl;
   const bool act = tl < B.z;
-  float xr[3] = {0.f, 0.f, 0.f};
-  if (act) {
-    const double4 x = tgt64[i];
-    xr[0] = (float)(x.x - ct.x);
-    xr[1] = (float)(x.y - ct.y);
-    xr[2] = (float)(x.z - ct.z);
-  }
-  const f2 X = pk(xr[0], xr[0]), Y = pk(xr[1], xr[1]), Z = pk(xr[2], xr[2]);
+  const double4 x = tgt64[act ? i : B.y];
   const f2 K2 = pk(kappa, kappa), NK2 = pk(nk_log2e, nk_log2e), ONE2 = pk(1.f, 1.f);
-  double acc[4] = {0, 0, 0, 0};
+  const unsigned b0 = smem_addr(&bar[0]), b1 = smem_addr(&bar[1]);
+  if (lane == 0) {
+    mbar_init(b0, 1);
+    mbar_init(b1, 1);
+    mbar_init_fence();
+  }
+  __syncwarp();
   const int base = near_ptr[leaf];
   const int nl = near_ptr[leaf + 1] - base;
   const int e0 = base + (int)(((long long)nl * blockIdx.y) / gridDim.y);
   const int e1 = base + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
-  // this lane stages stream-local source `lane` of both halves: pair lane / 2, slot lane & 1
-  const int pm = lane >> 1, slot = lane & 1;
-  for (int eb = e0; eb < e1;) {
-    const bool self = eb == base && near_list[base] == leaf;  // the leaf itself, alone in its pass
-    const int cnt = self ? 1 : min(NLC16, e1 - eb);
-    __syncwarp();  // the previous pass is done with the leaf table
-    for (int q = lane; q < cnt; q += 32) {
-      const int ent = near_list[eb + q];
-      const int cl = leaf_cell[ent & ~NEAR_CROSS];
-      lb[q] = begin[cl] * K;
-      lc[q + 1] = (end[cl] - begin[cl]) * K;
-      const double4 cs = center[cl];
-      lo3[q][0] = (float)(cs.x - ct.x);
-      lo3[q][1] = (float)(cs.y - ct.y);
-      lo3[q][2] = (float)(cs.z - ct.z);
-      lo3[q][3] = (ent & NEAR_CROSS) ? 0.f : 1.f;
-    }
-    __syncwarp();
+  // lane 0 copies chunk (pairs [p, p + cnt)) into buffer b
+  auto issue = [&](int b, int p, int cnt) {
     if (lane == 0) {
-      lc[0] = 0;
-      for (int q = 1; q <= cnt; ++q) lc[q] += lc[q - 1];
+      const unsigned bb = b ? b1 : b0;
+      const unsigned bytes = (unsigned)cnt * 16u;
+      fence_proxy_async_smem();  // earlier generic reads of this buffer before the async writes
+      mbar_expect_tx(bb, 4u * bytes);
+      bulk_copy_g2s(smem_addr(st[b].PA), PA + p, bytes, bb);
+      bulk_copy_g2s(smem_addr(st[b].PB), PB + p, bytes, bb);
+      bulk_copy_g2s(smem_addr(st[b].SA), SA + p, bytes, bb);
+      bulk_copy_g2s(smem_addr(st[b].SB), SB + p, bytes, bb);
     }
-    __syncwarp();
-    const int total = lc[cnt];
-    f2 f[4] = {0ull, 0ull, 0ull, 0ull};  // per-lane FP32 sums (even, odd source)
-    int ntile = 0;
-    int lo0 = 0, lo1 = 0;  // leaf of this lane's two staged sources (indices only grow)
-    for (int t0 = 0; t0 < total; t0 += 64) {
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int j = t0 + 32 * u + lane;
-        int& lo = u ? lo1 : lo0;
-        float px = FAR_PAD, py = FAR_PAD, pz = FAR_PAD, pw = 0.f;
-        float4 sz = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (j < total) {
-          while (lc[lo + 1] <= j) ++lo;
-          const int src = lb[lo] + (j - lc[lo]);
-          const float4 r = src_rel[src];
-          px = r.x + lo3[lo][0];
-          py = r.y + lo3[lo][1];
-          pz = r.z + lo3[lo][2];
-          pw = lo3[lo][3];
-          sz = str[src];
-        }
-        float* a = reinterpret_cast<float*>(&T.A[u * HP + pm]);
-        float* bq = reinterpret_cast<float*>(&T.Bz[u * HP + pm]);
-        float* c = reinterpret_cast<float*>(&T.C[u * HP + pm]);
-        float* d = reinterpret_cast<float*>(&T.D[u * HP + pm]);
-        a[slot] = px;
-        a[2 + slot] = py;
-        bq[slot] = pz;
-        bq[2 + slot] = pw;
-        c[slot] = sz.x;
-        c[2 + slot] = sz.y;
-        d[slot] = sz.z;
-        d[2 + slot] = sz.w;
-      }
-      __syncwarp();
-      const int lim = min(32, max(0, total - t0 - 32 * h));  // sources of this half
-      if (self)
-        half_tile_x2<true>(X, Y, Z, T, h * HP, (lim + 1) >> 1, K2, NK2, ONE2, f);
-      else
-        half_tile_x2<false>(X, Y, Z, T, h * HP, (lim + 1) >> 1, K2, NK2, ONE2, f);
-      if (++ntile == 4) {  // FP32 sums over at most 64 pairs per slot and lane, then FP64
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          float lo_, hi_;
-          upk(f[c], lo_, hi_);
-          acc[c] += (double)lo_ + (double)hi_;
-          f[c] = 0ull;
-        }
-        ntile = 0;
-      }
-      __syncwarp();
-    }
+  };
+  // items: chunks (entry e, pairs [p, min(p + CP, pe))) of the near leaves of this piece
+  int ce = e0, cp_ = 0, cpe = 0;  // current entry, chunk start, end of its leaf's pairs
+  if (ce < e1) {
+    const int L = near_list[ce] & ~NEAR_CROSS;
+    cp_ = pair_ptr[L];
+    cpe = pair_ptr[L + 1];
+    issue(0, cp_, min(CP, cpe - cp_));
+  }
+  double acc[4] = {0, 0, 0, 0};
+  f2 f[4] = {0ull, 0ull, 0ull, 0ull};
+  unsigned ph0 = 0u, ph1 = 0u;  // parity of the next completion of each buffer's barrier
+  int b = 0, cur_e = -1, nsum = 0;
+  bool self = false;
+  f2 X = 0ull, Y = 0ull, Z = 0ull, PW = 0ull;
+  auto flush = [&]() {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       float lo_, hi_;
       upk(f[c], lo_, hi_);
       acc[c] += (double)lo_ + (double)hi_;
+      f[c] = 0ull;
     }
-    eb += cnt;
+    nsum = 0;
+  };
+  while (ce < e1) {
+    const int ccnt = min(CP, cpe - cp_);
+    // the next chunk: the rest of this leaf, else the next entry's leaf
+    int ne = ce, np = cp_ + CP, npe = cpe;
+    if (np >= cpe) {
+      ++ne;
+      if (ne < e1) {
+        const int L = near_list[ne] & ~NEAR_CROSS;
+        np = pair_ptr[L];
+        npe = pair_ptr[L + 1];
+      }
+    }
+    if (ne < e1) issue(b ^ 1, np, min(CP, npe - np));
+    if (ce != cur_e) {  // a new near leaf: the target in its frame, its Laplace weight
+      flush();
+      cur_e = ce;
+      const int ent = near_list[ce];
+      const int L = ent & ~NEAR_CROSS;
+      const double4 cs = center[leaf_cell[L]];
+      const float xl = (float)(x.x - cs.x), yl = (float)(x.y - cs.y), zl = (float)(x.z - cs.z);
+      X = pk(xl, xl);
+      Y = pk(yl, yl);
+      Z = pk(zl, zl);
+      const float w = (ent & NEAR_CROSS) ? 0.f : 1.f;
+      PW = pk(w, w);
+      self = L == leaf;
+    }
+    if (!mbar_wait(b ? b1 : b0, b ? ph1 : ph0)) {
+      atomicExch(err, 1);
+      if (ne < e1) mbar_wait(b ? b0 : b1, b ? ph0 : ph1);  // the other copy in flight
+      return;
+    }
+    if (b)
+      ph1 ^= 1u;
+    else
+      ph0 ^= 1u;
+    if (self)
+      chunk_x2<true>(X, Y, Z, st[b], h, ccnt, PW, K2, NK2, ONE2, f);
+    else
+      chunk_x2<false>(X, Y, Z, st[b], h, ccnt, PW, K2, NK2, ONE2, f);
+    if (++nsum == 2) flush();  // FP32 sums over at most 64 nodes per slot and lane, then FP64
+    __syncwarp();              // every lane is done with buffer b before it is refilled
+    ce = ne;
+    cp_ = np;
+    cpe = npe;
+    b ^= 1;
   }
+  flush();
 #pragma unroll
   for (int c = 0; c < 4; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
   if (h == 0 && act) {
@@ -668,6 +707,30 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
     o[2 * n + i] = acc[2];
     o[3 * n + i] = acc[3];
   }
+}
+
+// source-pair records of the FP32 near field: positions once per mesh, strengths per
+// product (pair_src[p] = first node of pair p, negative (~node) when the second is padding)
+__global__ void pair_pos_kernel(const int* __restrict__ pair_src, int npair, const float4* __restrict__ rel,
+                                float4* __restrict__ PA, float4* __restrict__ PB) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int q = pair_src[p];
+  const float4 a = rel[q < 0 ? ~q : q];
+  const float4 b = q < 0 ? make_float4(FAR_PAD, FAR_PAD, FAR_PAD, 0.f) : rel[q + 1];
+  PA[p] = make_float4(a.x, b.x, a.y, b.y);
+  PB[p] = make_float4(a.z, b.z, 0.f, 0.f);
+}
+
+__global__ void pair_str_kernel(const int* __restrict__ pair_src, int npair, const float4* __restrict__ str,
+                                float4* __restrict__ SA, float4* __restrict__ SB) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= npair) return;
+  const int q = pair_src[p];
+  const float4 a = str[q < 0 ? ~q : q];
+  const float4 b = q < 0 ? make_float4(0.f, 0.f, 0.f, 0.f) : str[q + 1];
+  SA[p] = make_float4(a.x, b.x, a.y, b.y);
+  SB[p] = make_float4(a.z, b.z, a.w, b.w);
 }
 
 }  // namespace
@@ -893,7 +956,7 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   c.time_begin(F64 ? 6 : 2, s, tp);
   BP_CUDA(cudaEventRecord(c.ev_fork, s));
   BP_CUDA(cudaStreamWaitEvent(sf, c.ev_fork, 0));
-  launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
+  launch(leaf_moments_kernel<P, Real>, T.nleaf, MomShape<P>::TPB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
          c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
   for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
@@ -928,10 +991,13 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
            T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
            c.mv_active, T.leaf_sys.p, c.part.p);
-  else
-    launch(near16_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.begin.p,
-           T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.str32.p, (float)kappa, (float)nk, c.n, T.src_rel32.p,
-           c.mv_active, T.leaf_sys.p, c.part.p);
+  else {
+    launch(pair_str_kernel, cdiv(T.npair, 256), 256, 0, s, T.pair_src.p, T.npair, c.str32.p, T.pairSA.p,
+           T.pairSB.p);
+    launch(near16_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+           T.near_ptr.p, T.near_list.p, T.pair_ptr.p, T.pairPA.p, T.pairPB.p, T.pairSA.p, T.pairSB.p,
+           (float)kappa, (float)nk, c.n, c.mv_active, T.leaf_sys.p, c.part.p, c.dev_err.p);
+  }
   if (!F64) c.time_end(s, tm);
   BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join
   BP_CUDA(cudaStreamWaitEvent(s, c.ev_join, 0));
@@ -1012,6 +1078,21 @@ void build_tree(Ctx& c, cudaStream_t s) {
   T.cen_rel32.alloc(c.n);
   launch(src_rel_kernel, T.nleaf, 128, 0, s, T.leaf_cell.p, T.nleaf, T.begin.p, T.end.p, T.center.p, 1, c.tgt64.p,
          T.cen_rel32.p);
+  {  // source pairs of every leaf for the FP32 near field
+    std::vector<int> pptr(T.nleaf + 1, 0), psrc;
+    for (int l = 0; l < T.nleaf; ++l) {
+      const int cl = T.h_leaf_cell[l];
+      const int a = T.h_begin[cl] * c.K, e = T.h_end[cl] * c.K;
+      for (int q = a; q < e; q += 2) psrc.push_back(q + 1 < e ? q : ~q);
+      pptr[l + 1] = (int)psrc.size();
+    }
+    T.npair = (int)psrc.size();
+    upload(T.pair_ptr, pptr, s);
+    upload(T.pair_src, psrc, s);
+    for (DBuf<float4>* d : {&T.pairPA, &T.pairPB, &T.pairSA, &T.pairSB}) d->alloc(std::max(1, T.npair));
+    launch(pair_pos_kernel, cdiv(T.npair, 256), 256, 0, s, T.pair_src.p, T.npair, T.src_rel32.p, T.pairPA.p,
+           T.pairPB.p);
+  }
   BP_CUDA(cudaStreamSynchronize(s));
   build_lists(c, s);
   BP_CUDA(cudaStreamSynchronize(s));

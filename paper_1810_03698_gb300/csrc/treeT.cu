@@ -377,7 +377,7 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   launch(centroid_charges_kernel<R4>, cdiv(c.n, 256), 256, 0, sf, u, c.n, sL.p, sY.p);
   for (int w = 0; w < 2; ++w) {
     DBuf<Real>& m = w ? mY : mL;
-    launch(leaf_moments_kernel<P, Real>, T.nleaf, LMG * TB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
+    launch(leaf_moments_kernel<P, Real>, T.nleaf, MomShape<P>::TPB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, 1,
            c.tgt64.p, (const R4*)(w ? sY.p : sL.p), c.mv_active, T.leaf_sys.p, m.p);
     for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {
       const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;

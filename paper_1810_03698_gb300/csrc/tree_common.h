@@ -173,104 +173,108 @@ __global__ void src_rel_kernel(const int* __restrict__ leaf_cell, int nleaf, con
 }
 
 // ---------------------------------------------------------------- moments
-// Leaf moments from the sources: one block of LMG groups x TB threads per leaf.  A tile
-// of TB sources is staged (powers of the offsets, strengths); group g sums sources
-// [g TB/LMG, (g+1) TB/LMG) of every tile for the moments o, o + TB, ... of its thread;
-// the groups' partial moments are then added in group order.
-constexpr int LMG = 4;
+// Leaf moments from the sources: one block per leaf, 2 * NCP threads with NCP = NC
+// rounded up to a warp: thread t < NCP sums the single-layer moment M_t, thread
+// NCP + t the double-layer moment D_t (so every warp takes one branch).  Tiles of
+// 2 * NCP sources are staged (powers of the offsets from the leaf centre, strengths);
+// each thread sums its moment over the tile with branch-free terms (a zero factor
+// stands for a missing lower index).
+template <int P>
+struct MomShape {
+  static constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
+  static constexpr int NCP = (NC + 31) / 32 * 32;
+  static constexpr int TPB = 2 * NCP;
+};
+
 template <int P, typename Real>
-__global__ void __launch_bounds__(LMG * TB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
-                                                                const int* __restrict__ begin,
-                                                                const int* __restrict__ end,
-                                                                const double4* __restrict__ center, int K,
-                                                                const double4* __restrict__ src64,
-                                                                const typename Vec4<Real>::T* __restrict__ str,
-                                                                const int* __restrict__ active,
-                                                                const int* __restrict__ leaf_sys,
-                                                                Real* __restrict__ mom) {
-  const MI<P>& mi = c_mi<P>;
-  constexpr int NC = MI<P>::NC;
-  constexpr int NU = (2 * NC + TB - 1) / TB;
-  __shared__ Real pw[TB][3][P + 1];
-  __shared__ Real sd[TB][4];
-  __shared__ Real red[LMG][2 * NC];
+__global__ void __launch_bounds__(MomShape<P>::TPB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
+                                                                      const int* __restrict__ begin,
+                                                                      const int* __restrict__ end,
+                                                                      const double4* __restrict__ center, int K,
+                                                                      const double4* __restrict__ src64,
+                                                                      const typename Vec4<Real>::T* __restrict__ str,
+                                                                      const int* __restrict__ active,
+                                                                      const int* __restrict__ leaf_sys,
+                                                                      Real* __restrict__ mom) {
+  constexpr int NC = MomShape<P>::NC, NCP = MomShape<P>::NCP, TPB = MomShape<P>::TPB;
+  __shared__ Real pw[TPB][3][P + 1];
+  __shared__ Real sd[TPB][4];
   if (active && !active[leaf_sys[blockIdx.x]]) return;  // system not being solved
   const int cidx = leaf_cell[blockIdx.x];
   const double4 c = center[cidx];
   const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
-  const int grp = threadIdx.x / TB, tl = threadIdx.x % TB;
-  Real acc[NU];
-  for (int u = 0; u < NU; ++u) acc[u] = 0;
-  for (int t0 = s0; t0 < s1; t0 += TB) {
-    if (threadIdx.x < TB) {
-      const int j = t0 + threadIdx.x;
-      if (j < s1) {
-        double4 y = src64[j];
-        Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
-        for (int d = 0; d < 3; ++d) {
-          Real p = 1;
-          for (int e = 0; e <= P; ++e) {
-            pw[threadIdx.x][d][e] = p;
-            p *= h[d];
-          }
+  const bool dbl = threadIdx.x >= NCP;
+  const int t = dbl ? threadIdx.x - NCP : threadIdx.x;
+  const bool on = t < NC;
+  int kx = 0, ky = 0, kz = 0;
+  if (on) {
+    kx = c_mi<P>.k[t][0];
+    ky = c_mi<P>.k[t][1];
+    kz = c_mi<P>.k[t][2];
+  }
+  // double layer: sum_j k_j d_j h^(k - e_j); a zero k_j gives a zero factor
+  const Real fx = (Real)kx, fy = (Real)ky, fz = (Real)kz;
+  const int mx = kx > 0 ? kx - 1 : 0, my = ky > 0 ? ky - 1 : 0, mz = kz > 0 ? kz - 1 : 0;
+  Real a = 0;
+  for (int t0 = s0; t0 < s1; t0 += TPB) {
+    const int j = t0 + threadIdx.x;
+    if (j < s1) {
+      const double4 y = src64[j];
+      const Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Real p = 1;
+#pragma unroll
+        for (int e = 0; e <= P; ++e) {
+          pw[threadIdx.x][d][e] = p;
+          p *= h[d];
         }
-        auto sv = str[j];
-        sd[threadIdx.x][0] = sv.x;
-        sd[threadIdx.x][1] = sv.y;
-        sd[threadIdx.x][2] = sv.z;
-        sd[threadIdx.x][3] = sv.w;
+      }
+      const auto sv = str[j];
+      sd[threadIdx.x][0] = sv.x;
+      sd[threadIdx.x][1] = sv.y;
+      sd[threadIdx.x][2] = sv.z;
+      sd[threadIdx.x][3] = sv.w;
+    }
+    __syncthreads();
+    const int lim = min(TPB, s1 - t0);
+    if (on) {
+      if (!dbl) {
+        for (int q = 0; q < lim; ++q) a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
+      } else {
+        for (int q = 0; q < lim; ++q) {
+          const Real X = pw[q][0][kx], Y = pw[q][1][ky], Z = pw[q][2][kz];
+          a += fx * sd[q][1] * pw[q][0][mx] * Y * Z + fy * sd[q][2] * X * pw[q][1][my] * Z +
+               fz * sd[q][3] * X * Y * pw[q][2][mz];
+        }
       }
     }
     __syncthreads();
-    const int lim = min(TB, s1 - t0);
-    const int q0 = grp * (TB / LMG), q1 = min(lim, q0 + TB / LMG);
-    for (int u = 0; u < NU; ++u) {
-      const int o = tl + u * TB;
-      if (o >= 2 * NC) break;
-      const bool dbl = o >= NC;
-      const int t = dbl ? o - NC : o;
-      const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
-      Real a = 0;
-      for (int q = q0; q < q1; ++q) {
-        if (!dbl) {
-          a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
-        } else {
-          Real v = 0;
-          if (kx) v += (Real)kx * sd[q][1] * pw[q][0][kx - 1] * pw[q][1][ky] * pw[q][2][kz];
-          if (ky) v += (Real)ky * sd[q][2] * pw[q][0][kx] * pw[q][1][ky - 1] * pw[q][2][kz];
-          if (kz) v += (Real)kz * sd[q][3] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz - 1];
-          a += v;
-        }
-      }
-      acc[u] += a;
-    }
-    __syncthreads();
   }
-  for (int u = 0; u < NU; ++u) {
-    const int o = tl + u * TB;
-    if (o < 2 * NC) red[grp][o] = acc[u];
-  }
-  __syncthreads();
-  for (int o = threadIdx.x; o < 2 * NC; o += LMG * TB) {
-    Real v = 0;
-    for (int g = 0; g < LMG; ++g) v += red[g][o];
-    mom[(size_t)cidx * 2 * NC + o] = v;
-  }
+  if (on) mom[(size_t)cidx * 2 * NC + (dbl ? NC : 0) + t] = a;
 }
 
 // Parent moments by shifting the children's: one block per parent cell of one depth,
 // one thread per (moment, child) shift; the children's shifted moments are then
-// added in child order.
+// added in child order.  The multi-index of a lower index l comes from its closed
+// form (orders below n, then a descending, then b descending) and the binomial
+// factors from a shared-memory copy, so threads of one warp may take different
+// moments without serialising on constant-memory reads.
 constexpr int M2M_TPB = 256;
+__device__ __forceinline__ int mi_index(int a, int b, int c) {
+  const int n = a + b + c;
+  return n * (n + 1) * (n + 2) / 6 + (n - a) * (n - a + 1) / 2 + (n - a - b);
+}
 template <int P, typename Real>
 __global__ void __launch_bounds__(M2M_TPB) m2m_kernel(int first_cell, const int* __restrict__ child0,
                                                       const int* __restrict__ nchild,
                                                       const double4* __restrict__ center, Real* __restrict__ mom) {
-  const MI<P>& mi = c_mi<P>;
   constexpr int NC = MI<P>::NC;
   __shared__ Real dp[8][3][P + 1];
   __shared__ Real cm[8][2 * NC];
   __shared__ Real red[8][2 * NC];
+  __shared__ int sk[NC][3];
+  __shared__ Real sb[P + 1][P + 1];
   const int pc = first_cell + blockIdx.x;
   const int nch = nchild[pc];
   if (nch == 0) return;  // leaf (uniform across the block)
@@ -287,23 +291,26 @@ __global__ void __launch_bounds__(M2M_TPB) m2m_kernel(int first_cell, const int*
       }
     }
   }
+  for (int q = threadIdx.x; q < NC * 3; q += M2M_TPB) sk[q / 3][q % 3] = c_mi<P>.k[q / 3][q % 3];
+  for (int q = threadIdx.x; q < (P + 1) * (P + 1); q += M2M_TPB)
+    sb[q / (P + 1)][q % (P + 1)] = (Real)c_binom.b[q / (P + 1)][q % (P + 1)];
   for (int q = threadIdx.x; q < nch * 2 * NC; q += M2M_TPB)
     cm[q / (2 * NC)][q % (2 * NC)] = mom[(size_t)(c0 + q / (2 * NC)) * 2 * NC + q % (2 * NC)];
   __syncthreads();
-  const auto& binom = c_binom.b;
   for (int w = threadIdx.x; w < nch * 2 * NC; w += M2M_TPB) {
     const int ch = w / (2 * NC), o = w - ch * 2 * NC;
     const int t = o < NC ? o : o - NC;
     const int off = o < NC ? 0 : NC;
-    const int kx = mi.k[t][0], ky = mi.k[t][1], kz = mi.k[t][2];
+    const int kx = sk[t][0], ky = sk[t][1], kz = sk[t][2];
     Real a = 0;
-    for (int lx = 0; lx <= kx; ++lx)
-      for (int ly = 0; ly <= ky; ++ly)
-        for (int lz = 0; lz <= kz; ++lz) {
-          const int l = mi.idx[lx][ly][lz];
-          a += (Real)(binom[kx][lx] * binom[ky][ly] * binom[kz][lz]) * dp[ch][0][kx - lx] * dp[ch][1][ky - ly] *
-               dp[ch][2][kz - lz] * cm[ch][off + l];
-        }
+    for (int lx = 0; lx <= kx; ++lx) {
+      const Real bx = sb[kx][lx] * dp[ch][0][kx - lx];
+      for (int ly = 0; ly <= ky; ++ly) {
+        const Real bxy = bx * sb[ky][ly] * dp[ch][1][ky - ly];
+        for (int lz = 0; lz <= kz; ++lz)
+          a += bxy * sb[kz][lz] * dp[ch][2][kz - lz] * cm[ch][off + mi_index(lx, ly, lz)];
+      }
+    }
     red[ch][o] = a;
   }
   __syncthreads();
