@@ -116,7 +116,14 @@ struct Tree {
   // 16-target near kernels
   int nblk = 0, nblk32 = 0, nblk16 = 0, nblk16f = 0, near_splits = 1, near_splits16 = 1;
   DBuf<int4> blk, blk32, blk16;
-  DBuf<int4> blk16f;  // the 16-target blocks in the order of the FP32 far field (most far work first)
+  DBuf<int4> blk16f;  // the 16-target blocks in the order of the forward far field (most far work first)
+  // interaction lists of the 16-target batches of the forward product (batch id = .w of
+  // blk16 / blk16f; acceptance against each batch's own bounding sphere): far cells of
+  // the Yukawa and Laplace kernels and near leaves, CSR by batch id
+  DBuf<int> bfar_ptr, bfar_list, bfarL_ptr, bfarL_list, bnear_ptr, bnear_list;
+  bool bfarL_same = true;
+  int bm2m_min_depth = 0;
+  long long bpairs_per_matvec = 0, bfar_per_matvec = 0;
   // multipole moments [ncell][2][NC]: single layer M_k, double layer D_k
   DBuf<float> mom32;
   DBuf<double> mom64;
@@ -138,6 +145,7 @@ struct Tree {
   DBuf<float4> chgT32[2];   // charges (u, 0, 0, 0) at the collocation points, Laplace / Yukawa
   DBuf<double4> chgT64[2];
   int m2m_min_depth = 0;  // shallowest depth whose cells appear in a far list
+
   double theta_built = -1.0;
   long long pairs_per_matvec = 0, far_per_matvec = 0, farL_per_matvec = 0;
 };

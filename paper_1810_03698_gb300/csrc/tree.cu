@@ -31,6 +31,7 @@
 // sums in FP32 and per-target sums in FP64.
 #include <algorithm>
 #include <cmath>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -136,86 +137,6 @@ __device__ __forceinline__ void far_eval_yukawa(const Real D[3], const Real* __r
 }
 
 
-// One block per target block (<= 128 targets of one leaf); loops over the leaf's far
-// cells.  YUK = 0 evaluates the Laplace kernel into rows (V_L, K_L), YUK = 1 the
-// Yukawa kernel into rows (V_Y, K_Y) of `out` ([4][n]).
-template <int P, typename Real, int YUK>
-__global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
-                                                 const int* __restrict__ leaf_cell, const double4* __restrict__ center,
-                                                 const int* __restrict__ far_ptr, const int* __restrict__ far_list,
-                                                 const Real* __restrict__ mom, Real kappa, int n,
-                                                 const int* __restrict__ active, const int* __restrict__ leaf_sys,
-                                                 double* __restrict__ out) {
-  constexpr int NC = MI<P>::NC;
-  // two buffers of staged cells: the next batch's moments are copied in (cp.async, 16-byte
-  // pieces, when a cell's moments are a whole number of them) while the current batch is
-  // evaluated; one barrier per batch.  FP64 batches are smaller to fit.
-  constexpr int FB = sizeof(Real) == 4 ? FCH : FCH / 4;
-  constexpr bool ASYNC = (2 * NC * sizeof(Real)) % 16 == 0;
-  __shared__ __align__(16) Real sm[2][FB][2 * NC];
-  __shared__ Real so[2][FB][3];
-  const int4 B = blk[blockIdx.x];
-  const int leaf = B.x;
-  if (active && !active[leaf_sys[leaf]]) return;
-  const double4 ct = center[leaf_cell[leaf]];
-  const int i = B.y + threadIdx.x;
-  const bool act = (int)threadIdx.x < B.z;
-  Real xr[3] = {0, 0, 0};
-  if (act) {
-    double4 x = tgt64[i];
-    xr[0] = (Real)(x.x - ct.x);
-    xr[1] = (Real)(x.y - ct.y);
-    xr[2] = (Real)(x.z - ct.z);
-  }
-  double aV = 0, aK = 0;
-  const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
-  auto stage = [&](int b, int fb) {
-    const int cnt = min(FB, f1 - fb);
-    if constexpr (ASYNC) {
-      constexpr int CH = (int)(2 * NC * sizeof(Real) / 16);  // 16-byte pieces per cell
-      for (int q = threadIdx.x; q < cnt * CH; q += TBT) {
-        const int cell = q / CH, piece = q - cell * CH;
-        const char* g = reinterpret_cast<const char*>(mom + (size_t)far_list[fb + cell] * 2 * NC) + 16 * piece;
-        cp_async16(reinterpret_cast<char*>(&sm[b][cell][0]) + 16 * piece, g);
-      }
-      cp_async_commit();
-    } else {
-      for (int q = threadIdx.x; q < cnt * 2 * NC; q += TBT)
-        sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
-    }
-    if ((int)threadIdx.x < cnt) {
-      double4 cc = center[far_list[fb + threadIdx.x]];
-      so[b][threadIdx.x][0] = (Real)(ct.x - cc.x);
-      so[b][threadIdx.x][1] = (Real)(ct.y - cc.y);
-      so[b][threadIdx.x][2] = (Real)(ct.z - cc.z);
-    }
-  };
-  if (f0 < f1) stage(0, f0);
-  int b = 0;
-  for (int fb = f0; fb < f1; fb += FB, b ^= 1) {
-    const int cnt = min(FB, f1 - fb);
-    if constexpr (ASYNC) cp_async_wait_all();  // this thread's pieces of batch b (the only copies in flight)
-    __syncthreads();  // batch b complete for every thread; every warp is done with the other buffer
-    if (fb + FB < f1) stage(b ^ 1, fb + FB);
-    Real v = 0, k = 0;
-    if ((int)(threadIdx.x & ~31u) < B.z) {  // warp holds at least one target
-      for (int q = 0; q < cnt; ++q) {
-        const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
-        if (YUK)
-          far_eval_yukawa<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
-        else
-          far_eval_laplace<P, Real>(D, sm[b][q], sm[b][q] + NC, v, k);
-      }
-    }
-    aV += (double)v;
-    aK += (double)k;
-  }
-  if (act) {
-    out[(2 * YUK) * (size_t)n + i] = aV;
-    out[(2 * YUK + 1) * (size_t)n + i] = aK;
-  }
-}
-
 // FP32 far field, one warp per block of <= 16 targets of one leaf.  Lane l serves target
 // (l & 15); the two half-warps take alternate cells of the leaf's far list (half h the
 // cells h, h + 2, ... of every batch) and their sums are added at the end.  Each warp
@@ -223,20 +144,20 @@ __global__ void __launch_bounds__(TBT) far_kernel(const int4* __restrict__ blk, 
 // only for its own copies (no block-wide barrier: a warp never waits for another).
 constexpr int FW = 8;  // cells per staged batch (four per half-warp)
 
-template <int P, int YUK>
+template <int P, typename Real, int YUK>
 __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                    const int* __restrict__ leaf_cell,
                                                    const double4* __restrict__ center,
                                                    const int* __restrict__ far_ptr, const int* __restrict__ far_list,
-                                                   const float* __restrict__ mom, float kappa, int n,
+                                                   const Real* __restrict__ mom, Real kappa, int n,
                                                    const int* __restrict__ active, const int* __restrict__ leaf_sys,
                                                    double* __restrict__ out) {
   constexpr int NC = MI<P>::NC;
-  // cp.async when a cell's moments are a whole number of 16-byte pieces (every order but 4)
-  constexpr bool ASYNC = (2 * NC * sizeof(float)) % 16 == 0;
-  constexpr int CH = (int)(2 * NC * sizeof(float) / 16);  // 16-byte pieces per cell
-  __shared__ __align__(16) float sm[2][FW][2 * NC];
-  __shared__ float so[2][FW][3];
+  // cp.async when a cell's moments are a whole number of 16-byte pieces (FP32: every order but 4)
+  constexpr bool ASYNC = (2 * NC * sizeof(Real)) % 16 == 0;
+  constexpr int CH = (int)(2 * NC * sizeof(Real) / 16);  // 16-byte pieces per cell
+  __shared__ __align__(16) Real sm[2][FW][2 * NC];
+  __shared__ Real so[2][FW][3];
   const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
@@ -244,15 +165,15 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
   const double4 ct = center[leaf_cell[leaf]];
   const int i = B.y + tl;
   const bool act = tl < B.z;
-  float xr[3] = {0.f, 0.f, 0.f};
+  Real xr[3] = {0, 0, 0};
   if (act) {
     const double4 x = tgt64[i];
-    xr[0] = (float)(x.x - ct.x);
-    xr[1] = (float)(x.y - ct.y);
-    xr[2] = (float)(x.z - ct.z);
+    xr[0] = (Real)(x.x - ct.x);
+    xr[1] = (Real)(x.y - ct.y);
+    xr[2] = (Real)(x.z - ct.z);
   }
   double aV = 0, aK = 0;
-  const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
+  const int f0 = far_ptr[B.w], f1 = far_ptr[B.w + 1];  // the batch's own far list
   auto stage = [&](int b, int fb) {
     const int cnt = min(FW, f1 - fb);
     if constexpr (ASYNC) {
@@ -268,9 +189,9 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
     }
     if (lane < cnt) {
       const double4 cc = center[far_list[fb + lane]];
-      so[b][lane][0] = (float)(ct.x - cc.x);
-      so[b][lane][1] = (float)(ct.y - cc.y);
-      so[b][lane][2] = (float)(ct.z - cc.z);
+      so[b][lane][0] = (Real)(ct.x - cc.x);
+      so[b][lane][1] = (Real)(ct.y - cc.y);
+      so[b][lane][2] = (Real)(ct.z - cc.z);
     }
   };
   if (f0 < f1) stage(0, f0);
@@ -280,13 +201,13 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
     if constexpr (ASYNC) cp_async_wait_all();  // this lane's pieces of batch b
     __syncwarp();  // every lane's pieces and offsets of batch b; all done with the other buffer
     if (fb + FW < f1) stage(b ^ 1, fb + FW);
-    float v = 0.f, k = 0.f;
+    Real v = 0, k = 0;
     for (int q = h; q < cnt; q += 2) {
-      const float D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
+      const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
       if (YUK)
-        far_eval_yukawa<P, float>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
+        far_eval_yukawa<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
       else
-        far_eval_laplace<P, float>(D, sm[b][q], sm[b][q] + NC, v, k);
+        far_eval_laplace<P, Real>(D, sm[b][q], sm[b][q] + NC, v, k);
     }
     aV += (double)v;
     aK += (double)k;
@@ -300,22 +221,6 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
 }
 
 // ---------------------------------------------------------------- near field
-__device__ __forceinline__ void pair_accum(const float x[3], float4 p, float4 s, float kappa, float nk_log2e,
-                                           float& vl, float& kl, float& vy, float& ky) {
-  float dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
-  float r2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-  float rinv = r2 > 0.f ? rsqrt_approx(r2) : 0.f;
-  float r = r2 * rinv;
-  float e = exp2_approx(r * nk_log2e);
-  float mr = s.x * rinv;
-  vl = fmaf(mr, p.w, vl);  // p.w: 1 for a source of the target's body, 0 for another body
-  vy = fmaf(mr, e, vy);
-  float dR = fmaf(s.y, dx, fmaf(s.z, dy, s.w * dz));
-  float t = dR * (rinv * rinv) * rinv;
-  kl = fmaf(t, p.w, kl);
-  ky = fmaf(t * fmaf(kappa, r, 1.f), e, ky);
-}
-
 __device__ __forceinline__ void pair_accum(const double x[3], double4 p, double4 s, double kappa, double,
                                            double& vl, double& kl, double& vy, double& ky) {
   double dx = x[0] - p.x, dy = x[1] - p.y, dz = x[2] - p.z;
@@ -330,129 +235,6 @@ __device__ __forceinline__ void pair_accum(const double x[3], double4 p, double4
   double t = (s.y * dx + s.z * dy + s.w * dz) * rinv * rinv * rinv;
   kl = fma(t, p.w, kl);
   ky += t * (1.0 + kappa * R) * e;
-}
-
-// One warp per target block of <= 32 targets of one leaf.  The leaf's near list is
-// cut into gridDim.y consecutive pieces; piece s writes its partial sums to
-// out + s * 4n (no atomics: the combine kernel adds the pieces in order).
-template <typename Real>
-__global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
-                                                  const int* __restrict__ leaf_cell,
-                                                  const double4* __restrict__ center, const int* __restrict__ begin,
-                                                  const int* __restrict__ end, const int* __restrict__ near_ptr,
-                                                  const int* __restrict__ near_list, int K,
-                                                  const double4* __restrict__ src64,
-                                                  const typename Vec4<Real>::T* __restrict__ str, Real kappa,
-                                                  Real nk_log2e, int n, const float4* __restrict__ src_rel,
-                                                  const int* __restrict__ active, const int* __restrict__ leaf_sys,
-                                                  double* __restrict__ out) {
-  typedef typename Vec4<Real>::T R4;
-  __shared__ R4 sp[NTB];
-  __shared__ R4 ss[NTB];
-  const int4 B = blk[blockIdx.x];
-  const int leaf = B.x;
-  if (active && !active[leaf_sys[leaf]]) return;
-  const double4 ct = center[leaf_cell[leaf]];
-  const int i = B.y + threadIdx.x;
-  const bool act = (int)threadIdx.x < B.z;
-  Real xr[3] = {0, 0, 0};
-  if (act) {
-    double4 x = tgt64[i];
-    xr[0] = (Real)(x.x - ct.x);
-    xr[1] = (Real)(x.y - ct.y);
-    xr[2] = (Real)(x.z - ct.z);
-  }
-  // The sources of up to NLC near leaves are streamed as one concatenated sequence,
-  // so every tile but the last of a pass is full and runs the unrolled loop.
-  constexpr int NLC = 64;
-  __shared__ int lb[NLC];       // first source index of each leaf of the pass
-  __shared__ int lc[NLC + 1];   // cumulative source counts
-  __shared__ float lo3[NLC][3]; // FP32 offset (source-leaf centre - target-leaf centre)
-  __shared__ float lw[NLC];     // Laplace weight of the leaf: 1 same body, 0 another body
-  double acc[4] = {0, 0, 0, 0};
-  const int nl = near_ptr[leaf + 1] - near_ptr[leaf];
-  const int e0 = near_ptr[leaf] + (int)(((long long)nl * blockIdx.y) / gridDim.y);
-  const int e1 = near_ptr[leaf] + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
-  for (int eb = e0; eb < e1; eb += NLC) {
-    const int cnt = min(NLC, e1 - eb);
-    __syncthreads();  // the previous pass is done with lb / lc
-    for (int q = threadIdx.x; q < cnt; q += NTB) {
-      const int ent = near_list[eb + q];
-      const int cl = leaf_cell[ent & ~NEAR_CROSS];
-      lw[q] = (ent & NEAR_CROSS) ? 0.f : 1.f;
-      lb[q] = begin[cl] * K;
-      lc[q + 1] = (end[cl] - begin[cl]) * K;
-      const double4 cs = center[cl];
-      lo3[q][0] = (float)(cs.x - ct.x);
-      lo3[q][1] = (float)(cs.y - ct.y);
-      lo3[q][2] = (float)(cs.z - ct.z);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      lc[0] = 0;
-      for (int q = 1; q <= cnt; ++q) lc[q] += lc[q - 1];
-    }
-    __syncthreads();
-    const int total = lc[cnt];
-    // per-pair sums in Real over up to four tiles (128 sources), then into FP64
-    Real vl = 0, kl = 0, vy = 0, ky = 0;
-    int ntile = 0;
-    int lo = 0;  // leaf of this lane's source: largest q with lc[q] <= j (j only grows)
-    for (int t0 = 0; t0 < total; t0 += NTB) {
-      const int j = t0 + threadIdx.x;
-      R4 pz, sz;
-      pz.x = pz.y = pz.z = pz.w = 0;
-      sz = pz;
-      if (j < total) {
-        while (lc[lo + 1] <= j) ++lo;
-        const int src = lb[lo] + (j - lc[lo]);
-        if constexpr (sizeof(Real) == 4) {
-          // leaf-relative FP32 position plus the leaf-pair offset: no FP64 work per source
-          const float4 r = src_rel[src];
-          pz.x = r.x + lo3[lo][0];
-          pz.y = r.y + lo3[lo][1];
-          pz.z = r.z + lo3[lo][2];
-        } else {
-          const double4 y = src64[src];
-          pz.x = (Real)(y.x - ct.x);
-          pz.y = (Real)(y.y - ct.y);
-          pz.z = (Real)(y.z - ct.z);
-        }
-        pz.w = (Real)lw[lo];
-        sz = str[src];
-      }
-      sp[threadIdx.x] = pz;
-      ss[threadIdx.x] = sz;
-      __syncthreads();
-      if (t0 + NTB <= total) {
-#pragma unroll 8
-        for (int k = 0; k < NTB; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
-      } else {
-        const int lim = total - t0;
-        for (int k = 0; k < lim; ++k) pair_accum(xr, sp[k], ss[k], kappa, nk_log2e, vl, kl, vy, ky);
-      }
-      if (++ntile == 4) {
-        acc[0] += (double)vl;
-        acc[1] += (double)kl;
-        acc[2] += (double)vy;
-        acc[3] += (double)ky;
-        vl = kl = vy = ky = 0;
-        ntile = 0;
-      }
-      __syncthreads();
-    }
-    acc[0] += (double)vl;
-    acc[1] += (double)kl;
-    acc[2] += (double)vy;
-    acc[3] += (double)ky;
-  }
-  if (act) {
-    double* o = out + (size_t)blockIdx.y * 4 * n;
-    o[i] = acc[0];
-    o[n + i] = acc[1];
-    o[2 * n + i] = acc[2];
-    o[3 * n + i] = acc[3];
-  }
 }
 
 // ---------------------------------------------------------------- FP32 near field
@@ -480,9 +262,10 @@ __global__ void __launch_bounds__(NTB) near_kernel(const int4* __restrict__ blk,
 //
 // The leaf itself is the only near leaf whose nodes can coincide with a target (the
 // centroid node of the target's own panel), so only its sums carry the r = 0 test (a
-// coincident pair of different panels is rejected when the near table is built).  The
-// leaf's near list is cut into gridDim.y consecutive pieces; piece s writes its partial
-// sums to out + s * 4n (the combine kernel adds the pieces in order).
+// coincident pair of different panels is rejected when the near table is built).  Block
+// (leaf, first, count, batch) takes the near list of its batch, cut into gridDim.y
+// consecutive pieces; piece s writes its partial sums to out + s * 4n (the combine
+// kernel adds the pieces in order).
 constexpr int CP = 64;             // source pairs per staged chunk
 constexpr float FAR_PAD = 1.0e4f;  // leaf-relative position of a padding node (zero strength)
 constexpr int MBAR_SPIN = 1 << 20; // polls of an mbarrier before a wait is declared failed
@@ -609,8 +392,8 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
     mbar_init_fence();
   }
   __syncwarp();
-  const int base = near_ptr[leaf];
-  const int nl = near_ptr[leaf + 1] - base;
+  const int base = near_ptr[B.w];  // the batch's own near list
+  const int nl = near_ptr[B.w + 1] - base;
   const int e0 = base + (int)(((long long)nl * blockIdx.y) / gridDim.y);
   const int e1 = base + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
   // lane 0 copies chunk (pairs [p, p + cnt)) into buffer b
@@ -698,6 +481,67 @@ __global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk
     b ^= 1;
   }
   flush();
+#pragma unroll
+  for (int c = 0; c < 4; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+  if (h == 0 && act) {
+    double* o = out + (size_t)blockIdx.y * 4 * n;
+    o[i] = acc[0];
+    o[n + i] = acc[1];
+    o[2 * n + i] = acc[2];
+    o[3 * n + i] = acc[3];
+  }
+}
+
+// FP64 near field of the forward product over the same 16-target batches and near
+// lists as the FP32 kernel: lane l serves target (l & 15), the two half-warps take
+// alternate nodes of every staged tile of 64 nodes of one near leaf, FP64 pair terms and
+// sums, the r = 0 test everywhere (FP64 throughput, not issue, bounds this kernel).
+__global__ void __launch_bounds__(32) near16d_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+                                                     const int* __restrict__ leaf_cell,
+                                                     const int* __restrict__ begin, const int* __restrict__ end,
+                                                     const int* __restrict__ near_ptr,
+                                                     const int* __restrict__ near_list, int K,
+                                                     const double4* __restrict__ src64,
+                                                     const double4* __restrict__ str, double kappa, int n,
+                                                     const int* __restrict__ active, const int* __restrict__ leaf_sys,
+                                                     double* __restrict__ out) {
+  __shared__ double4 sp[64];
+  __shared__ double4 ss[64];
+  const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
+  const int4 B = blk[blockIdx.x];
+  if (active && !active[leaf_sys[B.x]]) return;
+  const int i = B.y + tl;
+  const bool act = tl < B.z;
+  const double4 xt = tgt64[act ? i : B.y];
+  const double x[3] = {xt.x, xt.y, xt.z};
+  double acc[4] = {0, 0, 0, 0};
+  const int base = near_ptr[B.w];
+  const int nl = near_ptr[B.w + 1] - base;
+  const int e0 = base + (int)(((long long)nl * blockIdx.y) / gridDim.y);
+  const int e1 = base + (int)(((long long)nl * (blockIdx.y + 1)) / gridDim.y);
+  for (int e = e0; e < e1; ++e) {
+    const int ent = near_list[e];
+    const int cl = leaf_cell[ent & ~NEAR_CROSS];
+    const double w = (ent & NEAR_CROSS) ? 0.0 : 1.0;
+    const int s0 = begin[cl] * K, s1 = end[cl] * K;
+    for (int t0 = s0; t0 < s1; t0 += 64) {
+      __syncwarp();  // the previous tile is done
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int j = t0 + 32 * u + lane;
+        if (j < s1) {
+          double4 y = src64[j];
+          y.w = w;
+          sp[32 * u + lane] = y;
+          ss[32 * u + lane] = str[j];
+        }
+      }
+      __syncwarp();
+      const int lim = min(64, s1 - t0);
+      for (int k = h; k < lim; k += 2)
+        pair_accum(x, sp[k], ss[k], kappa, 0.0, acc[0], acc[1], acc[2], acc[3]);
+    }
+  }
 #pragma unroll
   for (int c = 0; c < 4; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
   if (h == 0 && act) {
@@ -801,6 +645,119 @@ void upload(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
   if (!h.empty()) BP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s));
 }
 
+// Interaction lists of the forward product's target batches (the 16-target blocks of
+// the FP32 and FP64 near and far kernels): batch b holds the targets [first, first +
+// count) of one leaf, and a cell C is accepted for it when R_C < theta (|c_b - c_C| - R_b)
+// with (c_b, R_b) the bounding sphere of the batch's own collocation points, so every
+// target satisfies the paper's criterion theta > R_C / r and a small batch accepts
+// cells closer to its targets than its whole leaf could (fewer near pairs and far
+// terms).  Cells of another system are skipped, cells of another body of the same
+// system enter the Yukawa lists only, the multi-group root and any cell holding the
+// batch are opened; the leaf of the batch comes first in its near list.  Built on
+// several host threads, each over a contiguous range of batches.
+struct BatchLists {
+  std::vector<int> fptr, fl, lptr, ll, nptr, nl;
+  long long pairs = 0, fars = 0, farsL = 0;
+};
+
+static void batch_lists(const Ctx& c, const std::vector<int4>& batches, const std::vector<double4>& h_tgt,
+                        const std::vector<int>& leaf_of, BatchLists& out) {
+  const Tree& T = c.tree;
+  const double theta = c.par.theta;
+  const int nb = (int)batches.size();
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  nth = std::min<unsigned>(nth, (unsigned)std::max(1, nb / 64));
+  std::vector<BatchLists> part(nth);
+  auto work = [&](unsigned w) {
+    BatchLists& o = part[w];
+    const int b0 = (int)((long long)nb * w / nth), b1 = (int)((long long)nb * (w + 1) / nth);
+    std::vector<int> stack;
+    o.fptr.push_back(0);
+    o.lptr.push_back(0);
+    o.nptr.push_back(0);
+    for (int bi = b0; bi < b1; ++bi) {
+      const int4 B = batches[bi];
+      const int leaf = B.x, first = B.y, cnt = B.z;
+      const int ct = T.h_leaf_cell[leaf];
+      const int g = T.h_cell_grp[ct];
+      const int sy = c.h_grp_sys[g];
+      double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+      for (int i = first; i < first + cnt; ++i) {
+        const double v[3] = {h_tgt[i].x, h_tgt[i].y, h_tgt[i].z};
+        for (int d = 0; d < 3; ++d) {
+          lo[d] = std::min(lo[d], v[d]);
+          hi[d] = std::max(hi[d], v[d]);
+        }
+      }
+      const double ax = 0.5 * (lo[0] + hi[0]), ay = 0.5 * (lo[1] + hi[1]), az = 0.5 * (lo[2] + hi[2]);
+      double rb = 0.0;
+      for (int i = first; i < first + cnt; ++i) {
+        const double dx = h_tgt[i].x - ax, dy = h_tgt[i].y - ay, dz = h_tgt[i].z - az;
+        rb = std::max(rb, std::sqrt(dx * dx + dy * dy + dz * dz));
+      }
+      const size_t nl0 = o.nl.size();
+      stack.assign(1, 0);
+      while (!stack.empty()) {
+        const int q = stack.back();
+        stack.pop_back();
+        const int cg = T.h_cell_grp[q];
+        if (cg < 0) {
+          for (int k = T.h_nchild[q] - 1; k >= 0; --k) stack.push_back(T.h_child0[q] + k);
+          continue;
+        }
+        if (c.h_grp_sys[cg] != sy) continue;
+        const double4 cc = T.h_center[q];
+        const double dx = ax - cc.x, dy = ay - cc.y, dz = az - cc.z;
+        const double gap = std::sqrt(dx * dx + dy * dy + dz * dz) - rb;
+        const bool holds = T.h_begin[q] <= first && first + cnt <= T.h_end[q];
+        if (!holds && gap > 0.0 && cc.w < theta * gap) {
+          o.fl.push_back(q);
+          o.fars += cnt;
+          if (cg == g) {
+            o.ll.push_back(q);
+            o.farsL += cnt;
+          }
+        } else if (T.h_nchild[q] == 0) {
+          o.nl.push_back(leaf_of[q] | (cg == g ? 0 : NEAR_CROSS));
+          o.pairs += (long long)cnt * (T.h_end[q] - T.h_begin[q]) * c.K;
+        } else {
+          for (int k = T.h_nchild[q] - 1; k >= 0; --k) stack.push_back(T.h_child0[q] + k);
+        }
+      }
+      for (size_t e = nl0; e < o.nl.size(); ++e)
+        if (o.nl[e] == leaf) {
+          std::rotate(o.nl.begin() + nl0, o.nl.begin() + e, o.nl.begin() + e + 1);
+          break;
+        }
+      o.fptr.push_back((int)o.fl.size());
+      o.lptr.push_back((int)o.ll.size());
+      o.nptr.push_back((int)o.nl.size());
+    }
+  };
+  std::vector<std::thread> th;
+  for (unsigned w = 1; w < nth; ++w) th.emplace_back(work, w);
+  work(0);
+  for (auto& t : th) t.join();
+  out = BatchLists();
+  out.fptr.assign(1, 0);
+  out.lptr.assign(1, 0);
+  out.nptr.assign(1, 0);
+  for (const BatchLists& o : part) {
+    const int f0 = (int)out.fl.size(), l0 = (int)out.ll.size(), n0 = (int)out.nl.size();
+    for (size_t k = 1; k < o.fptr.size(); ++k) {
+      out.fptr.push_back(f0 + o.fptr[k]);
+      out.lptr.push_back(l0 + o.lptr[k]);
+      out.nptr.push_back(n0 + o.nptr[k]);
+    }
+    out.fl.insert(out.fl.end(), o.fl.begin(), o.fl.end());
+    out.ll.insert(out.ll.end(), o.ll.begin(), o.ll.end());
+    out.nl.insert(out.nl.end(), o.nl.begin(), o.nl.end());
+    out.pairs += o.pairs;
+    out.fars += o.fars;
+    out.farsL += o.farsL;
+  }
+}
+
 // Interaction lists of every leaf under the batch acceptance criterion.  Cells of
 // another system are skipped, cells of another body of the same system enter the
 // Yukawa lists only (Laplace layers act within a body), and the multi-group root
@@ -865,6 +822,51 @@ void build_lists(Ctx& c, cudaStream_t s) {
     for (int off = 0; off < ntgt; off += 16)
       blk16.push_back(make_int4(l, T.h_begin[ct] + off, std::min(16, ntgt - off), 0));
   }
+  // lists of the 16-target batches of the forward product (batch id = blk16[.].w)
+  {
+    std::vector<double4> h_tgt(c.n);
+    BP_CUDA(cudaMemcpyAsync(h_tgt.data(), c.tgt64.p, sizeof(double4) * c.n, cudaMemcpyDeviceToHost, s));
+    BP_CUDA(cudaStreamSynchronize(s));
+    for (size_t b = 0; b < blk16.size(); ++b) blk16[b].w = (int)b;
+    BatchLists BL;
+    batch_lists(c, blk16, h_tgt, leaf_of, BL);
+    std::vector<long long> bnear(blk16.size(), 0), bfar(blk16.size(), 0);
+    for (size_t b = 0; b < blk16.size(); ++b) {
+      bfar[b] = BL.fptr[b + 1] - BL.fptr[b];
+      for (int e = BL.nptr[b]; e < BL.nptr[b + 1]; ++e) {
+        const int q = T.h_leaf_cell[BL.nl[e] & ~NEAR_CROSS];
+        bnear[b] += T.h_end[q] - T.h_begin[q];
+      }
+    }
+    std::vector<int4> bf = blk16;
+    // largest blocks first: the grids are a few waves deep, so launching the long blocks
+    // early shortens the tail (a block's result does not depend on the order)
+    std::stable_sort(blk16.begin(), blk16.end(), [&](const int4& u, const int4& v) { return bnear[u.w] > bnear[v.w]; });
+    std::stable_sort(bf.begin(), bf.end(), [&](const int4& u, const int4& v) { return bfar[u.w] > bfar[v.w]; });
+    T.nblk16 = (int)blk16.size();
+    T.nblk16f = (int)bf.size();
+    T.near_splits16 = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk16))));
+    upload(T.blk16, blk16, s);
+    upload(T.blk16f, bf, s);
+    upload(T.bfar_ptr, BL.fptr, s);
+    upload(T.bfar_list, BL.fl, s);
+    T.bfarL_same = BL.ll.size() == BL.fl.size();
+    if (!T.bfarL_same) {
+      upload(T.bfarL_ptr, BL.lptr, s);
+      upload(T.bfarL_list, BL.ll, s);
+    }
+    upload(T.bnear_ptr, BL.nptr, s);
+    upload(T.bnear_list, BL.nl, s);
+    T.bpairs_per_matvec = BL.pairs;
+    T.bfar_per_matvec = BL.fars;
+    // shallowest tree depth that holds a cell of a batch far list
+    T.bm2m_min_depth = T.ndepth;
+    for (int q : BL.fl) {
+      int d = 0;
+      while (d + 1 < T.ndepth && T.h_depth_begin[d + 1] <= q) ++d;
+      T.bm2m_min_depth = std::min(T.bm2m_min_depth, d);
+    }
+  }
   // largest blocks first: the grids are only one or two waves deep, so launching the
   // long blocks early shortens the tail (each block's result does not depend on order)
   std::vector<long long> far_work(T.nleaf), near_work(T.nleaf, 0);
@@ -881,13 +883,6 @@ void build_lists(Ctx& c, cudaStream_t s) {
   std::stable_sort(blk32.begin(), blk32.end(), [&](const int4& u, const int4& v) {
     return near_work[u.x] * u.z > near_work[v.x] * v.z;
   });
-  std::vector<int4> blk16f = blk16;
-  std::stable_sort(blk16.begin(), blk16.end(), [&](const int4& u, const int4& v) {
-    return near_work[u.x] > near_work[v.x];  // a block's time does not depend on its fill
-  });
-  std::stable_sort(blk16f.begin(), blk16f.end(), [&](const int4& u, const int4& v) {
-    return far_work[u.x] > far_work[v.x];
-  });
   // shallowest tree depth that holds an accepted cell: moments above it are never read
   T.m2m_min_depth = T.ndepth;
   for (int q : flist) {
@@ -899,12 +894,7 @@ void build_lists(Ctx& c, cudaStream_t s) {
   T.nblk32 = (int)blk32.size();
   // split each near-field block's source stream so the grid holds ~56 warps per SM
   T.near_splits = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk32))));
-  T.nblk16 = (int)blk16.size();
-  T.near_splits16 = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk16))));
   upload(T.blk32, blk32, s);
-  upload(T.blk16, blk16, s);
-  T.nblk16f = (int)blk16f.size();
-  upload(T.blk16f, blk16f, s);
   T.pairs_per_matvec = pairs;
   T.far_per_matvec = fars;
   T.farL_per_matvec = farsL;
@@ -939,15 +929,16 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str32.p);
   else
     str = reinterpret_cast<const R4*>(c.str64.p);
-  const int S = F64 ? T.near_splits : T.near_splits16;
+  const int S = T.near_splits16;
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
-  const Real nk = (Real)(-c.par.kappa * 1.4426950408889634);
+  const float nk = (float)(-c.par.kappa * 1.4426950408889634);
   // Fork: the far-field chain (moments, M2M shifts, far kernels) on the context's
   // high-priority side stream, the near field on `s`; the near kernel needs no moments,
   // so its blocks fill the SMs that the small M2M grids and the far kernels' last wave
-  // leave idle.  The two write disjoint pieces of c.part.
+  // leave idle.  The two write disjoint pieces of c.part.  Both precisions use the
+  // interaction lists of the 16-target batches.
   c.ensure_aux();
   const cudaStream_t sf = c.aux;
   // accounting: FP32 products per kernel (pair, far) and whole; FP64 products (the
@@ -956,47 +947,40 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   c.time_begin(F64 ? 6 : 2, s, tp);
   BP_CUDA(cudaEventRecord(c.ev_fork, s));
   BP_CUDA(cudaStreamWaitEvent(sf, c.ev_fork, 0));
-  launch(leaf_moments_kernel<P, Real>, T.nleaf, MomShape<P>::TPB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p, T.center.p, c.K,
-         c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
-  for (int d = T.ndepth - 2; d >= T.m2m_min_depth; --d) {  // depths above are in no far list
+  launch(leaf_moments_kernel<P, Real>, T.nleaf, MomShape<P>::TPB, 0, sf, T.leaf_cell.p, T.begin.p, T.end.p,
+         T.center.p, c.K, c.src64.p, str, c.mv_active, T.leaf_sys.p, mom.p);
+  for (int d = T.ndepth - 2; d >= T.bm2m_min_depth; --d) {  // depths above are in no far list
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
     launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
   Ctx::Timed tf;
   if (!F64) {
     c.time_begin(1, sf, tf);
-    c.stat_far += T.far_per_matvec;
+    c.stat_far += T.bfar_per_matvec;
   }
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
-  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
-  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
-  if constexpr (F64) {
-    launch(far_kernel<P, Real, 0>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
-           kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-    launch(far_kernel<P, Real, 1>, T.nblk, TBT, 0, sf, T.blk.p, c.tgt64.p, T.leaf_cell.p, T.center.p, T.far_ptr.p,
-           T.far_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  } else {
-    launch(far16_kernel<P, 0>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll,
-           mom.p, (float)kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-    launch(far16_kernel<P, 1>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-           T.far_ptr.p, T.far_list.p, mom.p, (float)kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  }
+  const int* lp = T.bfarL_same ? T.bfar_ptr.p : T.bfarL_ptr.p;
+  const int* ll = T.bfarL_same ? T.bfar_list.p : T.bfarL_list.p;
+  launch(far16_kernel<P, Real, 0>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll,
+         mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(far16_kernel<P, Real, 1>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+         T.bfar_ptr.p, T.bfar_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
   if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
   if (!F64) {
     c.time_begin(0, s, tm);
-    c.stat_pairs += T.pairs_per_matvec;
+    c.stat_pairs += T.bpairs_per_matvec;
   }
-  if constexpr (F64)
-    launch(near_kernel<Real>, dim3(T.nblk32, S), NTB, 0, s, T.blk32.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-           T.begin.p, T.end.p, T.near_ptr.p, T.near_list.p, c.K, c.src64.p, str, kappa, nk, c.n, T.src_rel32.p,
-           c.mv_active, T.leaf_sys.p, c.part.p);
-  else {
+  if constexpr (F64) {
+    launch(near16d_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.begin.p, T.end.p,
+           T.bnear_ptr.p, T.bnear_list.p, c.K, c.src64.p, str, (double)kappa, c.n, c.mv_active, T.leaf_sys.p,
+           c.part.p);
+  } else {
     launch(pair_str_kernel, cdiv(T.npair, 256), 256, 0, s, T.pair_src.p, T.npair, c.str32.p, T.pairSA.p,
            T.pairSB.p);
     launch(near16_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-           T.near_ptr.p, T.near_list.p, T.pair_ptr.p, T.pairPA.p, T.pairPB.p, T.pairSA.p, T.pairSB.p,
-           (float)kappa, (float)nk, c.n, c.mv_active, T.leaf_sys.p, c.part.p, c.dev_err.p);
+           T.bnear_ptr.p, T.bnear_list.p, T.pair_ptr.p, T.pairPA.p, T.pairPB.p, T.pairSA.p, T.pairSB.p,
+           (float)kappa, nk, c.n, c.mv_active, T.leaf_sys.p, c.part.p, c.dev_err.p);
   }
   if (!F64) c.time_end(s, tm);
   BP_CUDA(cudaEventRecord(c.ev_join, sf));  // join

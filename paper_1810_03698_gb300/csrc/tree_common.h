@@ -73,9 +73,10 @@ struct MI {
 
 __host__ __device__ constexpr int ncoef(int P) { return (P + 1) * (P + 2) * (P + 3) / 6; }
 
-// constant-memory copies for kernels that index the tables at run time
+// constant-memory copy of the tables for set-up code that indexes them at run time
 template <int P>
 __constant__ MI<P> c_mi{};
+
 
 struct Binom {
   int b[MAXP + 1][MAXP + 1];
@@ -173,85 +174,90 @@ __global__ void src_rel_kernel(const int* __restrict__ leaf_cell, int nleaf, con
 }
 
 // ---------------------------------------------------------------- moments
-// Leaf moments from the sources: one block per leaf, 2 * NCP threads with NCP = NC
-// rounded up to a warp: thread t < NCP sums the single-layer moment M_t, thread
-// NCP + t the double-layer moment D_t (so every warp takes one branch).  Tiles of
-// 2 * NCP sources are staged (powers of the offsets from the leaf centre, strengths);
-// each thread sums its moment over the tile with branch-free terms (a zero factor
-// stands for a missing lower index).
+// Leaf moments from the sources: one block of 2 * MT threads per leaf, tiles of MT
+// sources.  Thread j < MT forms, for source j of the tile, the single-layer terms
+// m h^k of every k (the monomials h^k built in registers, each from h^(k - e_j) times
+// one coordinate, in the order of the multi-index table); thread MT + j forms the
+// double-layer terms sum_i k_i d_i h^(k - e_i).  The terms go to a shared [source][moment]
+// table, and thread o then adds column o over the tile's sources (one conflict-free
+// shared load per source and moment).
+constexpr int MT = 64;  // sources per tile
 template <int P>
 struct MomShape {
   static constexpr int NC = (P + 1) * (P + 2) * (P + 3) / 6;
-  static constexpr int NCP = (NC + 31) / 32 * 32;
-  static constexpr int TPB = 2 * NCP;
+  static constexpr int TPB = 2 * MT;
 };
 
 template <int P, typename Real>
-__global__ void __launch_bounds__(MomShape<P>::TPB) leaf_moments_kernel(const int* __restrict__ leaf_cell,
-                                                                      const int* __restrict__ begin,
-                                                                      const int* __restrict__ end,
-                                                                      const double4* __restrict__ center, int K,
-                                                                      const double4* __restrict__ src64,
-                                                                      const typename Vec4<Real>::T* __restrict__ str,
-                                                                      const int* __restrict__ active,
-                                                                      const int* __restrict__ leaf_sys,
-                                                                      Real* __restrict__ mom) {
-  constexpr int NC = MomShape<P>::NC, NCP = MomShape<P>::NCP, TPB = MomShape<P>::TPB;
-  __shared__ Real pw[TPB][3][P + 1];
-  __shared__ Real sd[TPB][4];
+__global__ void __launch_bounds__(2 * MT) leaf_moments_kernel(const int* __restrict__ leaf_cell,
+                                                              const int* __restrict__ begin,
+                                                              const int* __restrict__ end,
+                                                              const double4* __restrict__ center, int K,
+                                                              const double4* __restrict__ src64,
+                                                              const typename Vec4<Real>::T* __restrict__ str,
+                                                              const int* __restrict__ active,
+                                                              const int* __restrict__ leaf_sys,
+                                                              Real* __restrict__ mom) {
+  constexpr MI<P> mi{};
+  constexpr int NC = MI<P>::NC;
+  constexpr int NO = (2 * NC + 2 * MT - 1) / (2 * MT);  // moments per thread in the column sums
+  __shared__ Real term[MT][2 * NC + 1];
   if (active && !active[leaf_sys[blockIdx.x]]) return;  // system not being solved
   const int cidx = leaf_cell[blockIdx.x];
   const double4 c = center[cidx];
   const int s0 = begin[cidx] * K, s1 = end[cidx] * K;
-  const bool dbl = threadIdx.x >= NCP;
-  const int t = dbl ? threadIdx.x - NCP : threadIdx.x;
-  const bool on = t < NC;
-  int kx = 0, ky = 0, kz = 0;
-  if (on) {
-    kx = c_mi<P>.k[t][0];
-    ky = c_mi<P>.k[t][1];
-    kz = c_mi<P>.k[t][2];
-  }
-  // double layer: sum_j k_j d_j h^(k - e_j); a zero k_j gives a zero factor
-  const Real fx = (Real)kx, fy = (Real)ky, fz = (Real)kz;
-  const int mx = kx > 0 ? kx - 1 : 0, my = ky > 0 ? ky - 1 : 0, mz = kz > 0 ? kz - 1 : 0;
-  Real a = 0;
-  for (int t0 = s0; t0 < s1; t0 += TPB) {
-    const int j = t0 + threadIdx.x;
-    if (j < s1) {
-      const double4 y = src64[j];
+  const int j = threadIdx.x % MT;
+  const bool dbl = threadIdx.x >= MT;
+  Real acc[NO];
+#pragma unroll
+  for (int u = 0; u < NO; ++u) acc[u] = 0;
+  for (int t0 = s0; t0 < s1; t0 += MT) {
+    const int q = t0 + j;
+    Real mono[NC];
+    Real w[4] = {0, 0, 0, 0};
+    mono[0] = 1;
+    if (q < s1) {
+      const double4 y = src64[q];
       const Real h[3] = {(Real)(y.x - c.x), (Real)(y.y - c.y), (Real)(y.z - c.z)};
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        Real p = 1;
-#pragma unroll
-        for (int e = 0; e <= P; ++e) {
-          pw[threadIdx.x][d][e] = p;
-          p *= h[d];
-        }
+      for (int t = 1; t < NC; ++t) {
+        const int jj = mi.m1[t][0] >= 0 ? 0 : (mi.m1[t][1] >= 0 ? 1 : 2);
+        mono[t] = mono[mi.m1[t][jj]] * h[jj];
       }
-      const auto sv = str[j];
-      sd[threadIdx.x][0] = sv.x;
-      sd[threadIdx.x][1] = sv.y;
-      sd[threadIdx.x][2] = sv.z;
-      sd[threadIdx.x][3] = sv.w;
+      const auto sv = str[q];
+      w[0] = sv.x;
+      w[1] = sv.y;
+      w[2] = sv.z;
+      w[3] = sv.w;
+    }
+    if (!dbl) {
+#pragma unroll
+      for (int t = 0; t < NC; ++t) term[j][t] = w[0] * mono[t];
+    } else {
+#pragma unroll
+      for (int t = 0; t < NC; ++t) {
+        Real v = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+          if (mi.m1[t][i] >= 0) v += (Real)mi.k[t][i] * w[1 + i] * mono[mi.m1[t][i]];
+        term[j][NC + t] = v;
+      }
     }
     __syncthreads();
-    const int lim = min(TPB, s1 - t0);
-    if (on) {
-      if (!dbl) {
-        for (int q = 0; q < lim; ++q) a += sd[q][0] * pw[q][0][kx] * pw[q][1][ky] * pw[q][2][kz];
-      } else {
-        for (int q = 0; q < lim; ++q) {
-          const Real X = pw[q][0][kx], Y = pw[q][1][ky], Z = pw[q][2][kz];
-          a += fx * sd[q][1] * pw[q][0][mx] * Y * Z + fy * sd[q][2] * X * pw[q][1][my] * Z +
-               fz * sd[q][3] * X * Y * pw[q][2][mz];
-        }
-      }
+    const int lim = min(MT, s1 - t0);
+#pragma unroll
+    for (int u = 0; u < NO; ++u) {
+      const int o = threadIdx.x + u * 2 * MT;
+      if (o < 2 * NC)
+        for (int r = 0; r < lim; ++r) acc[u] += term[r][o];
     }
     __syncthreads();
   }
-  if (on) mom[(size_t)cidx * 2 * NC + (dbl ? NC : 0) + t] = a;
+#pragma unroll
+  for (int u = 0; u < NO; ++u) {
+    const int o = threadIdx.x + u * 2 * MT;
+    if (o < 2 * NC) mom[(size_t)cidx * 2 * NC + o] = acc[u];
+  }
 }
 
 // Parent moments by shifting the children's: one block per parent cell of one depth,
