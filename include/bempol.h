@@ -436,6 +436,47 @@ typedef struct {
 
 bempol_status bempol_measure_peaks(int device, int iters, int reps, bempol_peaks* out);
 
+/* Target sharding over several GPUs (Sec. "The treecode algorithm": the source-target
+ * and box-target interactions of different targets are independent).  Each GPU holds
+ * the whole mesh, sites and sources in its own context and computes only the rows of
+ * its rank: a contiguous range of the library's internal (Morton) panel order, cut at
+ * target-batch boundaries so that the treecode work (near pairs plus weighted far
+ * terms) is balanced.  After every treecode product the rows are exchanged through a
+ * caller-supplied all-gather, and everything else (GMRES with its Arnoldi process,
+ * induced dipoles, energies) runs redundantly on every rank with identical results.
+ *
+ * bempol_shard_rows: host only (no device work).  Split n_units consecutive units
+ * with costs cost[n_units] (NULL = 1 each, every cost >= 0) into `world` contiguous
+ * ranges of nearly equal cost: bounds[world+1] (host int64) with bounds[0] = 0,
+ * bounds[world] = n_units, nondecreasing; range r = [bounds[r], bounds[r+1]).  Cut r
+ * is the unit boundary whose cost prefix is nearest to r/world of the total (ties to
+ * the earlier one; a zero total gives equal unit counts).  BEMPOL_ERR_ARG on NULL
+ * bounds, n_units < 0, world < 1 or a negative cost. */
+bempol_status bempol_shard_rows(int64_t n_units, const double* cost, int world, int64_t* bounds);
+
+/* Exchange callback: called by the library on its host thread after this rank's rows
+ * of a product are in the exchange buffer; it must fill every other rank's rows (of
+ * both halves, phi rows [0, N) and psi rows [N, 2N), internal order) with theirs, with
+ * the copies ordered on `stream` (e.g. an NCCL all-gather), and return.  bounds
+ * [world+1] (host, valid during the call) are the row bounds of every rank.  The
+ * callback must not call into the same context. */
+typedef void (*bempol_exchange_fn)(void* user, const int64_t* bounds, int world, void* stream);
+
+/* Make this context rank `rank` of `world` for every treecode product (forward,
+ * BEMPOL_OP_FP32_TREE and BEMPOL_OP_FP64_TREE; direct forms and the transposed
+ * product compute every row).  exchange_buf: caller-owned device float64 [2N], kept
+ * until the sharding is replaced or the context destroyed; each product copies its
+ * result there (internal order), calls fn(user, stream) and copies it back.
+ * world = 1 (fn and exchange_buf may be NULL) turns sharding off.  Rebuilt with the
+ * tree (bempol_set_mesh, theta or leaf changes).  Requires a mesh (BEMPOL_ERR_STATE);
+ * BEMPOL_ERR_ARG on a bad rank/world or NULL fn/buffer with world > 1. */
+bempol_status bempol_set_shard(bempol_ctx* c, int rank, int world, double* exchange_buf, bempol_exchange_fn fn,
+                               void* user);
+
+/* Row bounds of the current sharding in internal panel order (host int64 [world+1];
+ * bounds[world] = N).  Builds the tree if needed.  BEMPOL_ERR_STATE without a mesh. */
+bempol_status bempol_shard_bounds(bempol_ctx* c, int64_t* bounds);
+
 /* Turn event timing on (1) or off (0).  Counting is always on. */
 bempol_status bempol_stats_enable(bempol_ctx* c, int enable);
 

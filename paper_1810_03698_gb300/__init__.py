@@ -91,6 +91,10 @@ class Peaks(C.Structure):
                 ("clock_mhz_attr", C.c_double)]
 
 
+# exchange callback of a sharded context: (user, stream) -> None
+ExchangeFn = C.CFUNCTYPE(None, C.c_void_p, C.POINTER(C.c_int64), C.c_int, C.c_void_p)
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1810_03698_gb300.build`")
@@ -123,6 +127,9 @@ def _load():
         "bempol_stats_enable": (i32, [vp, i32]),
         "bempol_stats_read": (i32, [vp, C.POINTER(Stats), i32]),
         "bempol_measure_peaks": (i32, [i32, i32, i32, C.POINTER(Peaks)]),
+        "bempol_shard_rows": (i32, [i64, vp, i32, vp]),
+        "bempol_set_shard": (i32, [vp, i32, i32, vp, ExchangeFn, vp]),
+        "bempol_shard_bounds": (i32, [vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -338,6 +345,34 @@ class Solver:
     def multipole_field(self, out, mu=None, mode=0, stream=None):
         self._chk(_lib.bempol_multipole_field(self._h, _ptr(mu)[0], mode, _ptr(out)[0], _stream(stream)))
 
+    def set_shard(self, rank: int, world: int, exchange=None):
+        """Compute only this rank's treecode rows (bempol_set_shard).  ``exchange(buf,
+        bounds)`` receives the library's product in ``buf`` (a device float64 tensor
+        [2N], internal panel order, this rank's rows valid) and the row bounds, and must
+        fill the other ranks' rows, e.g. ``lambda b, bd: allgather_rows(b, bd, rank,
+        world)``.  world = 1 turns sharding off."""
+        if world <= 1:
+            self._chk(_lib.bempol_set_shard(self._h, 0, 1, None, ExchangeFn(), None))
+            self._shard = None
+            return
+        import torch
+        n = self.sizes()["n_panels"]
+        buf = torch.zeros(2 * n, dtype=torch.float64, device=f"cuda:{self.device}")
+
+        def cb(user, bounds, nw, stream):
+            exchange(buf, [int(bounds[k]) for k in range(nw + 1)])
+
+        fn = ExchangeFn(cb)
+        self._shard = (buf, fn, None, world)   # the library holds raw pointers to buf and fn
+        self._chk(_lib.bempol_set_shard(self._h, rank, world, _ptr(buf)[0], fn, None))
+
+    def shard_bounds(self):
+        """Row bounds [world + 1] of the current sharding (internal panel order)."""
+        world = 1 if getattr(self, "_shard", None) is None else self._shard[3]
+        b = np.zeros(world + 1, dtype=np.int64)
+        self._chk(_lib.bempol_shard_bounds(self._h, b.ctypes.data))
+        return [int(v) for v in b]
+
     def autotune(self, target_err=1e-5, stream=None):
         """Pick leaf, theta and order for the current mesh (bempol_autotune); returns the
         choice and updates this Solver's parameters."""
@@ -376,6 +411,39 @@ def measure_peaks(device: int = 0, iters: int = 65536, reps: int = 3) -> dict:
     if st != 0:
         raise BempolError(st, "bempol_measure_peaks failed")
     return {k: getattr(r, k) for k, _ in Peaks._fields_}
+
+
+def shard_rows(n_units: int, world: int, cost=None):
+    """Contiguous ranges of nearly equal cost (bempol_shard_rows, host only)."""
+    b = np.zeros(world + 1, dtype=np.int64)
+    c = None if cost is None else np.ascontiguousarray(cost, dtype=np.float64)
+    st = _lib.bempol_shard_rows(int(n_units), None if c is None else c.ctypes.data, int(world), b.ctypes.data)
+    if st != 0:
+        raise BempolError(st, "bempol_shard_rows: bad arguments")
+    return [int(v) for v in b]
+
+
+def allgather_rows(buf, bounds, rank: int, world: int, group=None):
+    """The exchange of a sharded product: rank r holds rows [bounds[r], bounds[r+1]) of
+    both halves of ``buf`` ([2N]: phi rows, then psi rows); after the call every rank
+    holds every row.  One torch.distributed all-gather of the ranks' row blocks (padded
+    to the longest), on any backend (NCCL for device tensors, gloo for host tensors)."""
+    import torch
+    import torch.distributed as dist
+    n = bounds[-1]
+    lens = [bounds[k + 1] - bounds[k] for k in range(world)]
+    m = max(lens)
+    lo, hi = bounds[rank], bounds[rank + 1]
+    mine = torch.zeros(2 * m, dtype=buf.dtype, device=buf.device)
+    mine[:hi - lo] = buf[lo:hi]
+    mine[m:m + hi - lo] = buf[n + lo:n + hi]
+    parts = [torch.empty_like(mine) for _ in range(world)]
+    dist.all_gather(parts, mine, group=group)
+    for k in range(world):
+        a, e = bounds[k], bounds[k + 1]
+        buf[a:e] = parts[k][:e - a]
+        buf[n + a:n + e] = parts[k][m:m + e - a]
+    return buf
 
 
 KCAL_PER_UNIT = 4.0 * 3.141592653589793 * 332.0637132991921  # kcal/mol per e^2/A (vacuum permittivity 1)

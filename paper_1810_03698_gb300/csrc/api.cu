@@ -396,6 +396,7 @@ void set_sites_impl(Ctx* c, int64_t ns, const double* pos, const double* q, cons
   to_device(c->sys_site, c->h_sys_site.data(), c->h_sys_site.size(), BEMPOL_HOST, s);
   c->nsblk = (int)sblk.size();
   to_device(c->sblk, sblk.data(), sblk.size(), BEMPOL_HOST, s);
+  c->stree.ready = false;
   site_validation(*c, s);
   BP_CUDA(cudaStreamSynchronize(s));
   c->have_sites = true;
@@ -664,6 +665,50 @@ bempol_status bempol_sizes(const bempol_ctx* cc, int64_t* n_panels, int32_t* gau
   if (n_cells) *n_cells = cc->tree_ready ? cc->tree.ncell : 0;
   if (n_leaves) *n_leaves = cc->tree_ready ? cc->tree.nleaf : 0;
   return BEMPOL_OK;
+}
+
+bempol_status bempol_shard_rows(int64_t n_units, const double* cost, int world, int64_t* bounds) {
+  if (!bounds || n_units < 0 || world < 1) return BEMPOL_ERR_ARG;
+  try {
+    std::vector<double> v((size_t)n_units, 1.0);
+    if (cost)
+      for (int64_t i = 0; i < n_units; ++i) {
+        if (!(cost[i] >= 0.0)) return BEMPOL_ERR_ARG;
+        v[(size_t)i] = cost[i];
+      }
+    const std::vector<int64_t> b = shard_cuts(v, world);
+    for (int r = 0; r <= world; ++r) bounds[r] = b[r];
+    return BEMPOL_OK;
+  } catch (...) {
+    return BEMPOL_ERR_ARG;
+  }
+}
+
+bempol_status bempol_set_shard(bempol_ctx* c, int rank, int world, double* exchange_buf, bempol_exchange_fn fn,
+                               void* user) {
+  return guard(c, [&] {
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "bempol_set_shard needs a mesh");
+    if (world < 1 || rank < 0 || rank >= world) fail(BEMPOL_ERR_ARG, "rank must be in [0, world)");
+    if (world > 1 && (!fn || !exchange_buf)) fail(BEMPOL_ERR_ARG, "sharding needs an exchange buffer and callback");
+    c->sh_rank = world > 1 ? rank : 0;
+    c->sh_world = world;
+    c->sh_buf = world > 1 ? exchange_buf : nullptr;
+    c->sh_fn = world > 1 ? fn : nullptr;
+    c->sh_user = world > 1 ? user : nullptr;
+    c->sh_ready = false;
+  });
+}
+
+bempol_status bempol_shard_bounds(bempol_ctx* c, int64_t* bounds) {
+  return guard(c, [&] {
+    if (!c->have_mesh) fail(BEMPOL_ERR_STATE, "no mesh");
+    if (!bounds) fail(BEMPOL_ERR_ARG, "bounds is NULL");
+    cudaStream_t s = 0;
+    ensure_tree(*c, BEMPOL_OP_FP32_TREE, s);
+    if (!c->sh_ready) build_shard(*c, s);
+    for (int r = 0; r <= std::max(1, c->sh_world); ++r)
+      bounds[r] = c->sh_world > 1 ? c->sh_bounds[r] : (r == 0 ? 0 : c->n);
+  });
 }
 
 bempol_status bempol_stats_enable(bempol_ctx* c, int enable) {

@@ -121,6 +121,11 @@ struct Tree {
   // blk16 / blk16f; acceptance against each batch's own bounding sphere): far cells of
   // the Yukawa and Laplace kernels and near leaves, CSR by batch id
   DBuf<int> bfar_ptr, bfar_list, bfarL_ptr, bfarL_list, bnear_ptr, bnear_list;
+  // host copies: the batches (leaf, first, count, id) in id order with their cost (near
+  // pairs + far terms weighted by their flops), and the two launch orders
+  std::vector<int4> h_batch, h_blk16, h_blk16f;
+  std::vector<double> h_batch_cost;
+  std::vector<long long> h_batch_pairs, h_batch_far;
   bool bfarL_same = true;
   int bm2m_min_depth = 0;
   long long bpairs_per_matvec = 0, bfar_per_matvec = 0;
@@ -151,6 +156,21 @@ struct Tree {
 };
 
 constexpr int NEAR_CROSS = 1 << 30;  // near-list flag: source leaf of another body
+
+// Treecode evaluation of the reaction field at the sites: batches of <= 16 sites of one
+// body in Morton order (bat: first position in perm, count, group, 0; bcen: centre and
+// radius), their accepted cells and near leaves (CSR by batch), and the combined
+// moments W = M - D of the cells.  Rebuilt after set_sites or a new tree.
+struct SiteTree {
+  bool ready = false;
+  int nbat = 0, min_depth = 0;
+  long long far_evals = 0, pairs = 0;  // (site, cell) terms and (site, node) pairs per evaluation
+  DBuf<int4> bat;
+  DBuf<double4> bcen;
+  DBuf<int> perm, far_ptr, far_list, near_ptr, near_list;
+  DBuf<float> w32;
+  DBuf<double> w64;
+};
 
 // ---------------------------------------------------------------- context
 struct Ctx {
@@ -190,6 +210,7 @@ struct Ctx {
   std::vector<unsigned> h_morton;  // 30-bit Morton code of each internal panel (sorted)
   Tree tree;
   bool tree_ready = false;
+  SiteTree stree;
 
   // groups (bodies) and systems
   int ngroup = 1, nsys = 1;
@@ -246,6 +267,18 @@ struct Ctx {
   double* h_pinned = nullptr;  // pinned host scalars
   int gm_m = 0;
 
+  // target sharding: this rank computes the treecode rows [sh_bounds[rank],
+  // sh_bounds[rank+1]) (internal order) with the block tables below, then sh_fn
+  // exchanges the rest through the caller's buffer sh_buf [2n]
+  int sh_rank = 0, sh_world = 1;
+  std::vector<int64_t> sh_bounds;
+  double* sh_buf = nullptr;
+  bempol_exchange_fn sh_fn = nullptr;
+  void* sh_user = nullptr;
+  int sh_nblk16 = 0, sh_nblk16f = 0;
+  DBuf<int4> sh_blk16, sh_blk16f;
+  long long sh_pairs = 0, sh_far = 0;  // this rank's near pairs and far terms per product
+  bool sh_ready = false;  // tables match the current tree
   // side stream (highest priority) of a treecode product: the moments, M2M shifts and
   // far-field kernels run on it while the near-field kernel runs on the caller's
   // stream; fork and join events order the two.  Created with the tree.
@@ -271,6 +304,7 @@ struct Ctx {
   double stat_ms[NKIND] = {};
   long long stat_launches[NKIND] = {};
   long long stat_pairs = 0, stat_far = 0;
+  long long stat_site_pairs = 0, stat_site_far = 0;  // treecode reaction-field terms at the sites
   long long launches_at_reset = 0;
   void time_begin(int kind, cudaStream_t s, Timed& t);
   void time_end(cudaStream_t s, Timed& t);
@@ -340,6 +374,10 @@ void combine(Ctx& c, const double* x, double* y, cudaStream_t s);
 void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s);
 // tree.cu
 void build_tree(Ctx& c, cudaStream_t s);
+// contiguous ranges of nearly equal cost (bempol_shard_rows)
+std::vector<int64_t> shard_cuts(const std::vector<double>& cost, int world);
+// this rank's block tables and row bounds for the current tree (no-op without sharding)
+void build_shard(Ctx& c, cudaStream_t s);
 void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s);
 void tree_matvec_T_sums(Ctx& c, const double* u, cudaStream_t s);
 void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vector<int>& cells);
@@ -365,6 +403,9 @@ std::vector<double> energy_internal(Ctx& c, const double* react10, const double*
 std::vector<double> sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
                                const int* d_active, cudaStream_t s);
 void site_validation(Ctx& c, cudaStream_t s);
+// sitetree.cu: reaction potential, field and Hessian at the sites by the treecode, FP32
+// terms with FP64 sums or FP64 (out [ns*10] as site_reaction_internal)
+void site_reaction_tree(Ctx& c, const double* x, double* out, bool fp32, cudaStream_t s);
 bool site_reaction_scratch(Ctx& c, const double* x, double* out, bool fp32, bool hessian, double* scratch,
                            size_t cap, cudaStream_t s);
 // gmres.cu

@@ -335,11 +335,19 @@ void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s)
     return;
   }
   strengths(c, x, fp32, s);
-  if (op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE)
+  const bool tree = op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE;
+  if (tree)
     tree_matvec_sums(c, fp32, s);
   else
     p2p_direct(c, fp32, s);
   combine(c, x, y, s);
+  if (tree && c.sh_world > 1) {
+    // this rank's treecode rows are valid; the caller's all-gather supplies the rest
+    const size_t bytes = sizeof(double) * 2 * (size_t)c.n;
+    BP_CUDA(cudaMemcpyAsync(c.sh_buf, y, bytes, cudaMemcpyDeviceToDevice, s));
+    c.sh_fn(c.sh_user, c.sh_bounds.data(), c.sh_world, (void*)s);
+    BP_CUDA(cudaMemcpyAsync(y, c.sh_buf, bytes, cudaMemcpyDeviceToDevice, s));
+  }
 }
 
 }  // namespace bp

@@ -838,11 +838,23 @@ void build_lists(Ctx& c, cudaStream_t s) {
         bnear[b] += T.h_end[q] - T.h_begin[q];
       }
     }
+    T.h_batch = blk16;
+    T.h_batch_cost.assign(blk16.size(), 0.0);
+    T.h_batch_pairs.assign(blk16.size(), 0);
+    T.h_batch_far.assign(blk16.size(), 0);
+    for (size_t b = 0; b < blk16.size(); ++b) {
+      T.h_batch_pairs[b] = bnear[b] * c.K * blk16[b].z;
+      T.h_batch_far[b] = bfar[b] * blk16[b].z;
+      // a far term costs about 68 pair terms (2,040 against 30 flops at order 5)
+      T.h_batch_cost[b] = (double)T.h_batch_pairs[b] + 68.0 * (double)T.h_batch_far[b];
+    }
     std::vector<int4> bf = blk16;
     // largest blocks first: the grids are a few waves deep, so launching the long blocks
     // early shortens the tail (a block's result does not depend on the order)
     std::stable_sort(blk16.begin(), blk16.end(), [&](const int4& u, const int4& v) { return bnear[u.w] > bnear[v.w]; });
     std::stable_sort(bf.begin(), bf.end(), [&](const int4& u, const int4& v) { return bfar[u.w] > bfar[v.w]; });
+    T.h_blk16 = blk16;
+    T.h_blk16f = bf;
     T.nblk16 = (int)blk16.size();
     T.nblk16f = (int)bf.size();
     T.near_splits16 = std::max(1, std::min(4, cdiv((long long)num_sms(c.device) * 56, std::max(1, T.nblk16))));
@@ -929,6 +941,12 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     str = reinterpret_cast<const R4*>(c.str32.p);
   else
     str = reinterpret_cast<const R4*>(c.str64.p);
+  // this rank's blocks when the rows are sharded over several GPUs
+  const bool sh = c.sh_world > 1;
+  if (sh && !c.sh_ready) build_shard(c, s);
+  const int4* b16 = sh ? c.sh_blk16.p : T.blk16.p;
+  const int4* b16f = sh ? c.sh_blk16f.p : T.blk16f.p;
+  const int nb16 = sh ? c.sh_nblk16 : T.nblk16, nb16f = sh ? c.sh_nblk16f : T.nblk16f;
   const int S = T.near_splits16;
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
@@ -956,29 +974,29 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   Ctx::Timed tf;
   if (!F64) {
     c.time_begin(1, sf, tf);
-    c.stat_far += T.bfar_per_matvec;
+    c.stat_far += sh ? c.sh_far : T.bfar_per_matvec;
   }
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
   const int* lp = T.bfarL_same ? T.bfar_ptr.p : T.bfarL_ptr.p;
   const int* ll = T.bfarL_same ? T.bfar_list.p : T.bfarL_list.p;
-  launch(far16_kernel<P, Real, 0>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll,
-         mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(far16_kernel<P, Real, 1>, T.nblk16f, 32, 0, sf, T.blk16f.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
-         T.bfar_ptr.p, T.bfar_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(far16_kernel<P, Real, 0>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
+         kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(far16_kernel<P, Real, 1>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, T.bfar_ptr.p,
+         T.bfar_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
   if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
   if (!F64) {
     c.time_begin(0, s, tm);
-    c.stat_pairs += T.bpairs_per_matvec;
+    c.stat_pairs += sh ? c.sh_pairs : T.bpairs_per_matvec;
   }
   if constexpr (F64) {
-    launch(near16d_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.begin.p, T.end.p,
+    launch(near16d_kernel, dim3(nb16, S), 32, 0, s, b16, c.tgt64.p, T.leaf_cell.p, T.begin.p, T.end.p,
            T.bnear_ptr.p, T.bnear_list.p, c.K, c.src64.p, str, (double)kappa, c.n, c.mv_active, T.leaf_sys.p,
            c.part.p);
   } else {
     launch(pair_str_kernel, cdiv(T.npair, 256), 256, 0, s, T.pair_src.p, T.npair, c.str32.p, T.pairSA.p,
            T.pairSB.p);
-    launch(near16_kernel, dim3(T.nblk16, S), 32, 0, s, T.blk16.p, c.tgt64.p, T.leaf_cell.p, T.center.p,
+    launch(near16_kernel, dim3(nb16, S), 32, 0, s, b16, c.tgt64.p, T.leaf_cell.p, T.center.p,
            T.bnear_ptr.p, T.bnear_list.p, T.pair_ptr.p, T.pairPA.p, T.pairPB.p, T.pairSA.p, T.pairSB.p,
            (float)kappa, nk, c.n, c.mv_active, T.leaf_sys.p, c.part.p, c.dev_err.p);
   }
@@ -1043,6 +1061,68 @@ void tree_near_candidates(Ctx& c, double rmax, std::vector<int>& ptr, std::vecto
   }
 }
 
+std::vector<int64_t> shard_cuts(const std::vector<double>& cost, int world) {
+  const int64_t n = (int64_t)cost.size();
+  std::vector<int64_t> b(world + 1, 0);
+  double total = 0.0;
+  for (double v : cost) total += v;
+  b[world] = n;
+  if (!(total > 0.0)) {  // no cost anywhere: equal unit counts
+    for (int r = 1; r < world; ++r) b[r] = n * r / world;
+    return b;
+  }
+  // cut r at the unit boundary whose cost prefix is nearest to r/world of the total
+  // (ties to the earlier boundary); cuts never move backwards
+  double prefix = 0.0;
+  int64_t i = 0;
+  for (int r = 1; r < world; ++r) {
+    const double want = total * r / world;
+    while (i < n && prefix + cost[i] <= want) prefix += cost[i++];
+    if (i < n && prefix + cost[i] - want < want - prefix) prefix += cost[i++];
+    b[r] = i;
+  }
+  return b;
+}
+
+void build_shard(Ctx& c, cudaStream_t s) {
+  Tree& T = c.tree;
+  c.sh_ready = true;
+  c.sh_bounds.assign(2, 0);
+  c.sh_bounds[1] = c.n;
+  if (c.sh_world <= 1) return;
+  // batches in panel order; cuts at batch boundaries
+  std::vector<int> ord(T.h_batch.size());
+  for (size_t k = 0; k < ord.size(); ++k) ord[k] = (int)k;
+  std::sort(ord.begin(), ord.end(), [&](int a, int b) { return T.h_batch[a].y < T.h_batch[b].y; });
+  std::vector<double> cost(ord.size());
+  for (size_t k = 0; k < ord.size(); ++k) cost[k] = T.h_batch_cost[ord[k]];
+  const std::vector<int64_t> cut = shard_cuts(cost, c.sh_world);
+  c.sh_bounds.assign(c.sh_world + 1, 0);
+  for (int r = 0; r <= c.sh_world; ++r)
+    c.sh_bounds[r] = cut[r] < (int64_t)ord.size() ? T.h_batch[ord[cut[r]]].y : c.n;
+  std::vector<char> own(T.h_batch.size(), 0);
+  c.sh_pairs = c.sh_far = 0;
+  for (int64_t k = cut[c.sh_rank]; k < cut[c.sh_rank + 1]; ++k) {
+    own[ord[k]] = 1;
+    c.sh_pairs += T.h_batch_pairs[ord[k]];
+    c.sh_far += T.h_batch_far[ord[k]];
+  }
+  std::vector<int4> b16, b16f;
+  for (const int4& q : T.h_blk16)
+    if (own[q.w]) b16.push_back(q);
+  for (const int4& q : T.h_blk16f)
+    if (own[q.w]) b16f.push_back(q);
+  c.sh_nblk16 = (int)b16.size();
+  c.sh_nblk16f = (int)b16f.size();
+  c.sh_blk16.alloc(std::max<size_t>(1, b16.size()));
+  c.sh_blk16f.alloc(std::max<size_t>(1, b16f.size()));
+  if (!b16.empty())
+    BP_CUDA(cudaMemcpyAsync(c.sh_blk16.p, b16.data(), sizeof(int4) * b16.size(), cudaMemcpyHostToDevice, s));
+  if (!b16f.empty())
+    BP_CUDA(cudaMemcpyAsync(c.sh_blk16f.p, b16f.data(), sizeof(int4) * b16f.size(), cudaMemcpyHostToDevice, s));
+  BP_CUDA(cudaStreamSynchronize(s));
+}
+
 void build_tree(Ctx& c, cudaStream_t s) {
   Tree& T = c.tree;
   c.ensure_aux();  // the products' side stream, created here rather than inside a product
@@ -1082,6 +1162,8 @@ void build_tree(Ctx& c, cudaStream_t s) {
   BP_CUDA(cudaStreamSynchronize(s));
   T.mom_order = -1;
   c.tree_ready = true;
+  c.sh_ready = false;  // the shard tables follow the tree
+  c.stree.ready = false;  // so do the sites' lists
 }
 
 
