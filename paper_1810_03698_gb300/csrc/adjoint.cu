@@ -817,7 +817,7 @@ AdjointOut gradient_internal(Ctx& c, double* g_q, double* g_d, double* g_Q, doub
   zero3.alloc(3 * (size_t)ns);
   zero3.zero(s);
   // forward quantities at the solution: reaction fields (FP64) and energy-form multipole potentials
-  site_reaction_internal(c, c.sol_x.p, F_s.p, f32, true, s);
+  site_reaction_form(c, c.sol_x.p, F_s.p, P.residual_op, true, s);  // as the forward energy's
   multipole_internal(c, c.sol_mu.p, 1, P_mu.p, s, f32);
   multipole_internal(c, zero3.p, 1, P_0.p, s, f32);
   multipole_internal(c, c.sol_mu_v.p, 3, Pv_mu.p, s, f32);

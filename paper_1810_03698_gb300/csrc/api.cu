@@ -561,7 +561,7 @@ bempol_status bempol_site_reaction(bempol_ctx* c, const double* x, double* out, 
     if (!c->have_sites) fail(BEMPOL_ERR_STATE, "no sites");
     if (!x || !out) fail(BEMPOL_ERR_ARG, "NULL array");
     permute_to_internal(*c, x, c->vec_a.p, 2, s);
-    site_reaction_internal(*c, c->vec_a.p, out, op_fp32(op), true, s);
+    site_reaction_form(*c, c->vec_a.p, out, op, true, s);
   });
 }
 
@@ -837,6 +837,9 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     const bool final_only = refining && P.refine_scope == BEMPOL_REFINE_FINAL;
     const bool f32_final = op_fp32(P.residual_op);
     const bool f32 = final_only ? op_fp32(P.op) : f32_final;
+    // operator form of the reaction field inside the induced-dipole iterations (tree or
+    // direct, FP32 or FP64): that of the solves' precision, as for the other site sums
+    const int scf_form = final_only ? P.op : P.residual_op;
     DBuf<double>& mu = c->sol_mu;
     DBuf<double>& mu_v = c->sol_mu_v;
     DBuf<double>& x = c->sol_x;
@@ -946,7 +949,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
         bem(want, false);
         Ctx::Timed tx, tm;
         c->time_begin(4, s, tx);
-        site_reaction_internal(*c, x.p, react.p, f32, false, s);
+        site_reaction_form(*c, x.p, react.p, scf_form, false, s);
         c->time_end(s, tx);
         c->time_begin(5, s, tm);
         multipole_internal(*c, mu.p, 0, emult.p, s, f32);
@@ -972,7 +975,7 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
     }
     std::fill(want.begin(), want.end(), 1);
     bem(want, true);
-    site_reaction_internal(*c, x.p, react.p, f32_final, true, s);
+    site_reaction_form(*c, x.p, react.p, P.residual_op, true, s);
     multipole_internal(*c, mu.p, 1, mult10.p, s, f32_final);
     std::vector<double> Gd = energy_internal(*c, react.p, mult10.p, s);
     multipole_internal(*c, mu_v.p, 3, mult10.p, s, f32_final);

@@ -395,6 +395,10 @@ void site_field_of_charges(Ctx& c, const double4* src, const double4* str, const
                            int K, bool fp32, double* out10, cudaStream_t s);
 void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s);
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s);
+// the reaction field in the form of operator `op`: by the treecode for the tree forms
+// (always with the Hessian), by direct K-node sums otherwise; FP32 pair terms for the
+// FP32 forms
+void site_reaction_form(Ctx& c, const double* x, double* out, int op, bool hessian, cudaStream_t s);
 void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStream_t s, bool fp32 = false);
 // per-system energies (host vector of nsys)
 std::vector<double> energy_internal(Ctx& c, const double* react10, const double* mult10, cudaStream_t s);

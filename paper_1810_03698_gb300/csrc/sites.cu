@@ -458,6 +458,14 @@ void rhs_internal(Ctx& c, const double* p, double* b, bool fp32, cudaStream_t s)
   BP_CHECK_LAUNCH();
 }
 
+void site_reaction_form(Ctx& c, const double* x, double* out, int op, bool hessian, cudaStream_t s) {
+  const bool fp32 = op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE;
+  if (op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE)
+    site_reaction_tree(c, x, out, fp32, s);
+  else
+    site_reaction_internal(c, x, out, fp32, hessian, s);
+}
+
 void site_reaction_internal(Ctx& c, const double* x, double* out, bool fp32, bool hessian, cudaStream_t s) {
   strengths(c, x, fp32, s);
   const int S = site_splits(c, max_group_sources(c));

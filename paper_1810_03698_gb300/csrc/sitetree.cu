@@ -17,12 +17,15 @@
 // Gauss nodes are summed directly (sites are validated to lie outside every panel's
 // near-singular radius, so the K-node rule holds for all of them).
 //
-// Sites are grouped per body into batches of <= 16 in Morton order; a cell C is
-// accepted for a batch when R_C < theta (|c_b - c_C| - R_b) with (c_b, R_b) the batch's
-// bounding sphere, so every site satisfies the paper's criterion.  Only cells of the
-// site's own body are visited (Laplace layers act within a body).  One warp per batch
-// in both kernels: lane l serves site (l & 15), the half-warps split the cells (far) or
-// the nodes of every staged tile (near), FP32 (or FP64) terms with FP64 per-site sums.
+// Sites are grouped per body into batches of <= 8 in Morton order; a cell C is accepted
+// for a batch when R_C < theta_s (|c_b - c_C| - R_b) with (c_b, R_b) the batch's bounding
+// sphere and theta_s = theta / 2 (below), so every site satisfies the paper's criterion.
+// Only cells of the site's own body are visited (Laplace layers act within a body).
+// Each batch's lists are cut into pieces over the grid's y dimension; one warp per
+// (batch, piece) in both kernels: lane l serves site (l & 7) of the batch, the four
+// groups of eight lanes split the cells (far) or the nodes of every staged tile (near),
+// FP32 (or FP64) terms with FP64 per-site sums; the pieces' partial sums are added in
+// order.
 #include <algorithm>
 #include <cmath>
 #include <thread>
@@ -122,9 +125,9 @@ __global__ void wmom_kernel(const Real* __restrict__ mom, int ncell, Real* __res
   w[q] = mom[(size_t)cell * 2 * NC + t] - mom[(size_t)cell * 2 * NC + NC + t];
 }
 
-constexpr int SFW = 8;  // cells per staged batch of the site far kernel
+constexpr int SFW = 8;  // cells per staged batch of the site far kernel (two per lane group)
 
-// batch b = (first position in site_perm, count <= 16, group, 0); batch centre bcen[b]
+// batch b = (first position in site_perm, count <= 8, group, 0); batch centre bcen[b]
 template <int P, typename Real>
 __global__ void __launch_bounds__(32) site_far_kernel(const int4* __restrict__ bat, const int* __restrict__ perm,
                                                       const double4* __restrict__ site_pos,
@@ -132,13 +135,13 @@ __global__ void __launch_bounds__(32) site_far_kernel(const int4* __restrict__ b
                                                       const double4* __restrict__ center,
                                                       const int* __restrict__ far_ptr,
                                                       const int* __restrict__ far_list, const Real* __restrict__ wm,
-                                                      double* __restrict__ out) {
+                                                      int nsites, double* __restrict__ out) {
   constexpr int NC = MI<P>::NC;
   constexpr bool ASYNC = (NC * sizeof(Real)) % 16 == 0;
   constexpr int CH = (int)(NC * sizeof(Real) / 16);
   __shared__ __align__(16) Real sm[2][SFW][NC];
   __shared__ Real so[2][SFW][3];
-  const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
+  const int lane = threadIdx.x, h = lane >> 3, tl = lane & 7;  // site tl, stream h of 4
   const int4 B = bat[blockIdx.x];
   const double4 cb = bcen[blockIdx.x];
   const bool act = tl < B.y;
@@ -148,7 +151,10 @@ __global__ void __launch_bounds__(32) site_far_kernel(const int4* __restrict__ b
   double acc[10];
 #pragma unroll
   for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-  const int f0 = far_ptr[blockIdx.x], f1 = far_ptr[blockIdx.x + 1];
+  // this block's piece of the batch's far list (the list is cut into gridDim.y pieces)
+  const int fa = far_ptr[blockIdx.x], fz = far_ptr[blockIdx.x + 1];
+  const int f0 = fa + (int)(((long long)(fz - fa) * blockIdx.y) / gridDim.y);
+  const int f1 = fa + (int)(((long long)(fz - fa) * (blockIdx.y + 1)) / gridDim.y);
   auto stage = [&](int b, int fb) {
     const int cnt = min(SFW, f1 - fb);
     if constexpr (ASYNC) {
@@ -179,7 +185,7 @@ __global__ void __launch_bounds__(32) site_far_kernel(const int4* __restrict__ b
     Real f[10];
 #pragma unroll
     for (int c = 0; c < 10; ++c) f[c] = 0;
-    for (int q = h; q < cnt; q += 2) {
+    for (int q = h; q < cnt; q += 4) {
       const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
       site_far_eval<P, Real>(D, sm[b][q], f);
     }
@@ -187,10 +193,13 @@ __global__ void __launch_bounds__(32) site_far_kernel(const int4* __restrict__ b
     for (int c = 0; c < 10; ++c) acc[c] += (double)f[c];
   }
 #pragma unroll
-  for (int c = 0; c < 10; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+  for (int c = 0; c < 10; ++c) {
+    acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+    acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 8);
+  }
   if (h == 0 && act) {
 #pragma unroll
-    for (int c = 0; c < 10; ++c) out[(size_t)site * 10 + c] = acc[c];
+    for (int c = 0; c < 10; ++c) out[((size_t)blockIdx.y * nsites + site) * 10 + c] = acc[c];
   }
 }
 
@@ -205,11 +214,11 @@ __global__ void __launch_bounds__(32) site_near_kernel(const int4* __restrict__ 
                                                        const int* __restrict__ near_ptr,
                                                        const int* __restrict__ near_list, int K,
                                                        const R4* __restrict__ pos, const R4* __restrict__ str,
-                                                       double* __restrict__ out) {
+                                                       int nsites, double* __restrict__ out) {
   constexpr bool REL = sizeof(Real) == 4;  // FP32: positions relative to the node's leaf centre
   __shared__ R4 sp[64];
   __shared__ R4 ss[64];
-  const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
+  const int lane = threadIdx.x, h = lane >> 3, tl = lane & 7;  // site tl, stream h of 4
   const int4 B = bat[blockIdx.x];
   const bool act = tl < B.y;
   const int site = perm[B.x + (act ? tl : 0)];
@@ -217,7 +226,11 @@ __global__ void __launch_bounds__(32) site_near_kernel(const int4* __restrict__ 
   double acc[10];
 #pragma unroll
   for (int c = 0; c < 10; ++c) acc[c] = 0.0;
-  for (int e = near_ptr[blockIdx.x]; e < near_ptr[blockIdx.x + 1]; ++e) {
+  // this block's piece of the batch's near list (cut into gridDim.y pieces)
+  const int ea = near_ptr[blockIdx.x], ez = near_ptr[blockIdx.x + 1];
+  const int e0 = ea + (int)(((long long)(ez - ea) * blockIdx.y) / gridDim.y);
+  const int e1 = ea + (int)(((long long)(ez - ea) * (blockIdx.y + 1)) / gridDim.y);
+  for (int e = e0; e < e1; ++e) {
     const int cl = leaf_cell[near_list[e]];
     const double4 cc = center[cl];
     const Real X = REL ? (Real)(x.x - cc.x) : (Real)x.x;
@@ -239,7 +252,7 @@ __global__ void __launch_bounds__(32) site_near_kernel(const int4* __restrict__ 
       }
       __syncwarp();
       const int lim = min(64, s1 - t0);
-      for (int k = h; k < lim; k += 2) {
+      for (int k = h; k < lim; k += 4) {
         const R4 p = sp[k], sg = ss[k];
         const Real Rx = X - p.x, Ry = Y - p.y, Rz = Z - p.z;
         const Real r2 = Rx * Rx + Ry * Ry + Rz * Rz;
@@ -269,17 +282,23 @@ __global__ void __launch_bounds__(32) site_near_kernel(const int4* __restrict__ 
     for (int c = 0; c < 10; ++c) acc[c] += (double)a[c];
   }
 #pragma unroll
-  for (int c = 0; c < 10; ++c) acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+  for (int c = 0; c < 10; ++c) {
+    acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 16);
+    acc[c] += __shfl_down_sync(0xffffffffu, acc[c], 8);
+  }
   if (h == 0 && act) {
 #pragma unroll
-    for (int c = 0; c < 10; ++c) out[(size_t)site * 10 + c] = acc[c];
+    for (int c = 0; c < 10; ++c) out[((size_t)blockIdx.y * nsites + site) * 10 + c] = acc[c];
   }
 }
 
-__global__ void site_tree_reduce_kernel(const double* __restrict__ far, const double* __restrict__ near, int n10,
-                                        double* __restrict__ out) {
+// out = (sum of the np partial layers [np][n10]) / (4 pi), layers added in order
+__global__ void site_tree_reduce_kernel(const double* __restrict__ part, int np, int n10, double* __restrict__ out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n10) out[t] = (far[t] + near[t]) * (0.25 / M_PI);
+  if (t >= n10) return;
+  double v = 0.0;
+  for (int q = 0; q < np; ++q) v += part[(size_t)q * n10 + t];
+  out[t] = v * (0.25 / M_PI);
 }
 
 template <typename V>
@@ -287,6 +306,13 @@ void upload_vec(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
   d.alloc(std::max<size_t>(1, h.size()));
   if (!h.empty()) BP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s));
 }
+
+// Sites per batch, and the acceptance parameter of the site fields relative to the
+// product's theta: the field and Hessian are derivatives of the truncated expansion and
+// converge more slowly than the potential, so the sites accept a cell only at half the
+// product's theta (errors about 2^-(P+1) smaller at the same order).
+constexpr int SB = 8;
+constexpr double SITE_THETA_SCALE = 0.5;
 
 // Site batches of every body (Morton order of the sites within the body's bounding box)
 // and their interaction lists with the panel octree, built on several host threads.
@@ -328,8 +354,8 @@ void build_site_tree(Ctx& c, cudaStream_t s) {
     }
     std::sort(key.begin(), key.end());
     for (int k = 0; k < e - a; ++k) perm[a + k] = key[k].second;
-    for (int k = a; k < e; k += 16) {
-      const int cnt = std::min(16, e - k);
+    for (int k = a; k < e; k += SB) {
+      const int cnt = std::min(SB, e - k);
       double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
       for (int q = k; q < k + cnt; ++q) {
         const double4 p = hp[perm[q]];
@@ -352,7 +378,7 @@ void build_site_tree(Ctx& c, cudaStream_t s) {
   const int nb = (int)bat.size();
   std::vector<int> leaf_of(T.ncell, -1);
   for (int l = 0; l < T.nleaf; ++l) leaf_of[T.h_leaf_cell[l]] = l;
-  const double theta = c.par.theta;
+  const double theta = SITE_THETA_SCALE * c.par.theta;
   unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
   nth = std::min<unsigned>(nth, (unsigned)std::max(1, nb / 16));
   struct Part {
@@ -469,15 +495,20 @@ void site_tree_eval(Ctx& c, double* out, cudaStream_t s) {
     launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, s, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
   launch(wmom_kernel<P, Real>, cdiv((long long)T.ncell * NC, 256), 256, 0, s, mom.p, T.ncell, wm.p);
-  const size_t need = 2 * (size_t)c.ns * 10;
+  // each batch's far and near lists cut into Y pieces (grid y), so the grids hold about
+  // 24 warps per SM whatever the number of sites; partial sums per piece
+  const int Y = std::max(1, std::min(64, cdiv((long long)num_sms(c.device) * 24, std::max(1, ST.nbat))));
+  const size_t need = 2 * (size_t)Y * c.ns * 10;
   if (c.site_part.n < need) c.site_part.alloc(need);
   double* far = c.site_part.p;
-  double* near = c.site_part.p + (size_t)c.ns * 10;
-  launch(site_far_kernel<P, Real>, ST.nbat, 32, 0, s, ST.bat.p, ST.perm.p, c.site_pos.p, ST.bcen.p, T.center.p,
-         ST.far_ptr.p, ST.far_list.p, wm.p, far);
-  launch(site_near_kernel<Real, R4>, ST.nbat, 32, 0, s, ST.bat.p, ST.perm.p, c.site_pos.p, T.leaf_cell.p,
-         T.center.p, T.begin.p, T.end.p, ST.near_ptr.p, ST.near_list.p, c.K, pos, str, near);
-  launch(site_tree_reduce_kernel, cdiv((long long)c.ns * 10, 256), 256, 0, s, far, near, c.ns * 10, out);
+  double* near = c.site_part.p + (size_t)Y * c.ns * 10;
+  launch(site_far_kernel<P, Real>, dim3(ST.nbat, Y), 32, 0, s, ST.bat.p, ST.perm.p, c.site_pos.p, ST.bcen.p,
+         T.center.p, ST.far_ptr.p, ST.far_list.p, wm.p, c.ns, far);
+  launch(site_near_kernel<Real, R4>, dim3(ST.nbat, Y), 32, 0, s, ST.bat.p, ST.perm.p, c.site_pos.p,
+         T.leaf_cell.p, T.center.p, T.begin.p, T.end.p, ST.near_ptr.p, ST.near_list.p, c.K, pos, str, c.ns,
+         near);
+  launch(site_tree_reduce_kernel, cdiv((long long)c.ns * 10, 256), 256, 0, s, c.site_part.p, 2 * Y, c.ns * 10,
+         out);
   BP_CHECK_LAUNCH();
 }
 
