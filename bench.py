@@ -19,7 +19,10 @@ right-hand sides, reaction fields, site multipole fields and the rest.
 
 Launch: python bench.py [--gpus N --steps K --warmup W] ; for N > 1 under
 torch.distributed.run each rank solves its own replica (independent problems, no
-collective in the data path: weak scaling).  --impl reference times the oracle.
+collective in the data path: weak scaling).  With --shard the ranks instead solve the
+same problem together: each computes its Morton range of target rows of every treecode
+product and one NCCL all-gather per product exchanges them (strong scaling).
+--impl reference times the oracle.
 
 --workload gradient times the adjoint gradient dDelta G_solv/d(positions, q, d, Q)
 after a forward solve on the 327,680-panel surface with 10,000 sites (--grad-panels 81920
@@ -63,7 +66,7 @@ FLOPS_PER_PAIR = 30
 # induced-dipole iterations and the final solve's inner GMRES, plus its FP64 residuals).
 # The CPU baseline prices one Delta G as this many FP64 matrix-vector products of the
 # oracle in both arms; the native arm also reports its own count beside it.
-PRODUCTS_PER_DG = 763
+PRODUCTS_PER_DG = 747
 # DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
 # its kernels from one ncu capture; None until the kernels as built have been captured.
 TRAFFIC_PER_PRODUCT_BYTES = None
@@ -101,6 +104,9 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2,
                     help="untimed-in-value steps of the plain form (residual_op = op) reported beside the headline")
     ap.add_argument("--no-peaks", action="store_true", help="skip the FP32/FP64/MUFU peak measurement")
+    ap.add_argument("--shard", action="store_true",
+                    help="with N > 1: every rank solves the same Delta G with its share of each treecode product "
+                         "and an all-gather of the product (strong scaling) instead of an independent replica")
     ap.add_argument("--matvec-reps", type=int, default=10)
     ap.add_argument("--fp64-reps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
@@ -524,6 +530,11 @@ def main():
     stream = torch.cuda.current_stream()
     peaks = measure_peaks(bp, local, not args.no_peaks)
 
+    sharded = args.shard and world > 1
+    if sharded:   # each rank computes its rows of every treecode product; NCCL all-gathers the rest
+        s.set_mesh(d_verts, d_tris)
+        s.set_shard(rank, world, exchange=lambda buf, bounds: bp.allgather_rows(buf, bounds, rank, world))
+
     def step():
         s.set_mesh(d_verts, d_tris)
         s.set_sites(*d_site, group=d_group)
@@ -568,7 +579,7 @@ def main():
     clocks = sampler.stop()
     stats = s.stats(reset=True)
     total_ms = job_time_ms(float(np.sum(step_ms)), dist, dev)
-    value = seconds_per_unit(total_ms, args.steps, world)
+    value = seconds_per_unit(total_ms, args.steps, 1 if sharded else world)
     out = outs[-1]
 
     # ---- one more step split into its phases (not part of the timed value)
@@ -711,7 +722,8 @@ def main():
             d2h = sum(o[k2].nbytes for k2 in ("phi", "dphidn", "site_reaction", "mu_diss", "mu_vac")) + 8 * 3
             if k > 0:
                 e2e_ms.append((t1 - t0) * 1e3)
-        e2e = {"value": float(np.mean(e2e_ms)) / 1e3 / world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": float(np.mean(e2e_ms)) / 1e3 / (1 if sharded else world), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h)}
 
     if rank != 0:
@@ -732,9 +744,11 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": float(np.mean(step_ms)), "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if "fp32" in args.op else "f64",
-        "data": "synthetic",
+        "scaling": "strong" if sharded else "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if "fp32" in args.op else "f64", "data": "synthetic",
         "config": {"workload": pr.name, "panels": n, "gauss_k": K, "sites": st.n, "op": args.op,
+                   "parallelism": (f"target rows sharded over {world} GPUs" if sharded
+                                   else f"{world} independent replica(s)"),
                    "residual_op": res_op, "refine_scope": args.refine_scope if refining else None,
                    "theta": pr.params.theta, "order": pr.params.order, "leaf": pr.params.leaf,
                    "gmres_tol": pr.params.gmres_tol, "scf_tol": pr.params.scf_tol,

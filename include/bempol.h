@@ -273,8 +273,9 @@ bempol_status bempol_solve_systems(bempol_ctx* c, void* stream, bempol_result* o
  *                 dDelta G = sum_l G_l : dQ_l for symmetric traceless dQ_l,
  *   grad_pos [ns*3] dDelta G_solv/dr_l with the mesh held fixed (the surface does
  *                 not follow the sites).
- * Units: paper units (e^2/A per e, per e*A, per e*A^2, per A); multiply by
- * 4 pi 332.0637 for kcal/mol.  With several systems each site's gradient is that
+ * Units: `units` = BEMPOL_UNITS_PAPER gives paper units (e^2/A per e, per e*A, per
+ * e*A^2, per A); BEMPOL_UNITS_KCAL gives kcal/mol per the same (the paper units times
+ * 4 pi 332.0637133, as dG_solv_kcal).  With several systems each site's gradient is that
  * of its own system's Delta G_solv.  info (host, may be NULL) receives iteration
  * counts and the event time.  BEMPOL_ERR_NOT_CONVERGED if a limit was hit (outputs
  * written).  Synchronises `stream`. */
@@ -286,8 +287,10 @@ typedef struct {
   double t_ms;
 } bempol_gradient_info;
 
+enum { BEMPOL_UNITS_PAPER = 0, BEMPOL_UNITS_KCAL = 1 };
+
 bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, double* grad_d, double* grad_Q,
-                              double* grad_pos, bempol_gradient_info* info);
+                              double* grad_pos, bempol_gradient_info* info, int units);
 
 /* y = A x for the operator form `op` (BEMPOL_OP_*), one matrix-vector product of
  * Eq. integral_eq.  x, y: device float64 [2N] = [phi; psi] in the caller's panel

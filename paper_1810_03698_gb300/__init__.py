@@ -116,7 +116,7 @@ def _load():
         "bempol_matvec": (i32, [vp, vp, vp, i32, vp]),
         "bempol_matvec_transposed": (i32, [vp, vp, vp, i32, vp]),
         "bempol_autotune": (i32, [vp, dp, C.POINTER(TuneResult), vp]),
-        "bempol_gradient": (i32, [vp, vp, vp, vp, vp, vp, C.POINTER(GradientInfo)]),
+        "bempol_gradient": (i32, [vp, vp, vp, vp, vp, vp, C.POINTER(GradientInfo), i32]),
         "bempol_rhs": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction": (i32, [vp, vp, vp, i32, vp]),
         "bempol_site_reaction_noalloc": (i32, [vp, vp, vp, i32, vp]),
@@ -310,10 +310,11 @@ class Solver:
         self._chk(_lib.bempol_matvec_transposed(self._h, _ptr(x)[0], _ptr(y)[0], OP_NAMES.get(op, op),
                                                 _stream(stream)))
 
-    def gradient(self, stream=None, allow_unconverged=False):
-        """Adjoint gradient of the last solve's Delta G_solv (paper units) with respect to
-        every site's q, d, Q and position: dict of numpy arrays ``q`` [ns], ``d`` [ns, 3],
-        ``Q`` [ns, 3, 3], ``pos`` [ns, 3] and ``info``."""
+    def gradient(self, stream=None, allow_unconverged=False, units="paper", as_tensors=False):
+        """Adjoint gradient of the last solve's Delta G_solv with respect to every site's
+        q, d, Q and position (``units`` "paper" or "kcal"): dict of arrays ``q`` [ns],
+        ``d`` [ns, 3], ``Q`` [ns, 3, 3], ``pos`` [ns, 3] (numpy, or device tensors with
+        ``as_tensors``) and ``info``."""
         import torch
         ns = self.sizes()["n_sites"]
         dev = f"cuda:{self.device}"
@@ -323,9 +324,12 @@ class Solver:
         gp = torch.zeros(ns * 3, dtype=torch.float64, device=dev)
         info = GradientInfo()
         st = _lib.bempol_gradient(self._h, _stream(stream), _ptr(gq)[0], _ptr(gd)[0], _ptr(gQ)[0], _ptr(gp)[0],
-                                  C.byref(info))
+                                  C.byref(info), {"paper": 0, "kcal": 1}[units])
         if st != 0 and not (allow_unconverged and st == 4):
             self._chk(st)
+        if as_tensors:
+            return {"q": gq, "d": gd.reshape(-1, 3), "Q": gQ.reshape(-1, 3, 3), "pos": gp.reshape(-1, 3),
+                    "info": {k: getattr(info, k) for k, _ in GradientInfo._fields_}, "status": st}
         return {"q": gq.cpu().numpy(), "d": gd.cpu().numpy().reshape(-1, 3), "Q": gQ.cpu().numpy().reshape(-1, 3, 3),
                 "pos": gp.cpu().numpy().reshape(-1, 3),
                 "info": {k: getattr(info, k) for k, _ in GradientInfo._fields_}, "status": st}
@@ -472,9 +476,9 @@ def _torch_function():
 
         @staticmethod
         def backward(ctx, g):
-            gr = ctx.solver.gradient()
-            k = g.to(torch.float64) * KCAL_PER_UNIT
-            t = lambda a: torch.as_tensor(a, dtype=torch.float64, device=ctx.dev) * k
+            gr = ctx.solver.gradient(units="kcal", as_tensors=True)   # kcal/mol per unit, from the library
+            k = g.to(torch.float64)
+            t = lambda a: a.to(ctx.dev) * k
             return None, t(gr["pos"]), t(gr["q"]), t(gr["d"]), t(gr["Q"]), None, None
 
     return SolvationEnergy

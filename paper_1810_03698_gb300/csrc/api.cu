@@ -225,6 +225,11 @@ __global__ void add_vec_scaled(const double* __restrict__ a, const double* __res
   if (i < n) o[i] = a[i] + sb * b[i];
 }
 
+__global__ void scale_kernel(double* __restrict__ a, double f, int n) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] *= f;
+}
+
 __global__ void add_vec(const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ o, int n) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) o[i] = a[i] + (b ? b[i] : 0.0);
@@ -1051,12 +1056,21 @@ bempol_status bempol_solve(bempol_ctx* c, void* stream, bempol_result* out) {
 }
 
 bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, double* grad_d, double* grad_Q,
-                              double* grad_pos, bempol_gradient_info* info) {
+                              double* grad_pos, bempol_gradient_info* info, int units) {
   return guard(c, [&] {
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->have_sites || !c->have_solution) fail(BEMPOL_ERR_STATE, "bempol_gradient needs a completed solve");
+    if (units != BEMPOL_UNITS_PAPER && units != BEMPOL_UNITS_KCAL) fail(BEMPOL_ERR_ARG, "bad units");
     EventTimer t(s);
     AdjointOut ao = gradient_internal(*c, grad_q, grad_d, grad_Q, grad_pos, s);
+    if (units == BEMPOL_UNITS_KCAL) {
+      const size_t ns = (size_t)c->ns;
+      const std::pair<double*, size_t> outs[4] = {{grad_q, ns}, {grad_d, 3 * ns}, {grad_Q, 9 * ns}, {grad_pos, 3 * ns}};
+      for (const auto& o : outs)
+        if (o.first) launch(scale_kernel, cdiv((long long)o.second, 256), 256, 0, s, o.first, KCAL_PER_UNIT, (int)o.second);
+      BP_CHECK_LAUNCH();
+      BP_CUDA(cudaStreamSynchronize(s));
+    }
     check_device_error(*c, s);
     const double ms = t.ms();
     if (info) {

@@ -212,3 +212,15 @@ def test_adjoint_identity_fullsize(bp, op, bar):
     rhs = float(torch.dot(aty, x))
     scale = float(torch.linalg.norm(y) * torch.linalg.norm(ax))
     assert abs(lhs - rhs) <= bar * scale
+
+
+def test_gradient_units_kcal(bp):
+    """units="kcal" is the paper-unit gradient times 4 pi 332.0637 (the library scales)."""
+    pr = gen.sphere_r4_1280()
+    s = bp.problem_solver(pr, op="fp64_direct", residual_op="fp64_direct")
+    s.solve()
+    a = s.gradient()
+    b = s.gradient(units="kcal")
+    for k in ("q", "d", "Q", "pos"):
+        assert np.allclose(b[k], a[k] * bp.KCAL_PER_UNIT, rtol=1e-12, atol=0.0), k
+    s.close()
