@@ -68,9 +68,11 @@ FLOPS_PER_PAIR = 30
 # oracle in both arms; the native arm also reports its own count beside it.
 PRODUCTS_PER_DG = 747
 # DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
-# its kernels from one ncu capture; None until the kernels as built have been captured.
-TRAFFIC_PER_PRODUCT_BYTES = None
-TRAFFIC_BASIS = None
+# its kernels from one ncu capture of the kernels as committed (set to None when they change).
+TRAFFIC_PER_PRODUCT_BYTES = 47.63e6
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels of one FP32 treecode "
+                 "product (leaf moments, 3 M2M levels, far Laplace and Yukawa, pair strengths, near field), "
+                 "cache flushed before each kernel; profiles/tree_product_dram_bumpy81920.md")
 
 
 def far_flops(P):
