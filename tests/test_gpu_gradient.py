@@ -158,41 +158,6 @@ def test_gradient_needs_a_solve(bp):
     assert e.value.status == 8
 
 
-@pytest.mark.slow
-def test_gradient_at_scale_copy(bp):
-    """Workload 5's surface (R = 24 A bumpy) at subdivision 4, 300 sites: the FP32-treecode
-    adjoint agrees with the FP64-direct adjoint (treecode accuracy, 1e-4 of the largest
-    entry), and the FP64-direct position gradient with central differences of the
-    GPU's own Delta G_solv (h = 1e-4 A, tolerances 1e-12) for one coordinate."""
-    pr = gen.with_params(gen.bumpy_problem(24.0, 4, 300, 5, alpha_range=gen.configs.DENSE_ALPHA),
-                         gmres_tol=1e-12, scf_tol=1e-12, scf_maxit=400)
-    s64 = bp.problem_solver(pr)
-    r = s64.solve()
-    g64 = s64.gradient()
-    # the FP32 treecode at the workload's tolerances (1e-6; the FP32 operator cannot reach 1e-8)
-    s32 = bp.problem_solver(gen.with_params(pr, gmres_tol=1e-6, scf_tol=1e-6), op="fp32_tree",
-                            residual_op="fp32_tree", theta=0.5, order=5)
-    s32.solve()
-    g32 = s32.gradient()
-    for k in ("q", "d", "Q", "pos"):
-        assert _relmax(g32[k], g64[k]) < 1e-4, k
-    st = pr.sites
-    h = 1e-4
-    for l in (0,):
-        for a in (0,):
-            vals = []
-            for sgn in (1.0, -1.0):
-                pos = st.pos.copy()
-                pos[l, a] += sgn * h
-                s64.set_sites(np.ascontiguousarray(pos), np.ascontiguousarray(st.q), np.ascontiguousarray(st.d),
-                              np.ascontiguousarray(st.Q.reshape(-1, 9)), np.ascontiguousarray(st.alpha),
-                              np.ascontiguousarray(st.group, dtype=np.int32))
-                rr = s64.solve()
-                vals.append(rr["G_diss"] - rr["G_vac"])
-            fd = (vals[0] - vals[1]) / (2.0 * h)
-            assert fd == pytest.approx(g64["pos"][l, a], rel=1e-5, abs=1e-7 * np.max(np.abs(g64["pos"]))), (l, a)
-
-
 @pytest.mark.parametrize("op,bar", [("fp64_direct", 1e-12), ("fp32_tree", 2e-4)])
 def test_adjoint_identity_fullsize(bp, op, bar):
     """<y, A x> = <A^T y, x> on the 20,480-panel sphere with 100 sites: to rounding for
