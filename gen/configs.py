@@ -43,6 +43,7 @@ class Params:
     sor_omega: float = 0.7
     scf_maxit: int = 200
     thole_a: float = 0.39
+    damp_permanent: bool = False  # Thole-damp the permanent moments' polarising field (AMOEBA; not the paper's rule)
 
 
 @dataclass

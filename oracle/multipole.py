@@ -187,7 +187,7 @@ def _pairs(pos, body):
 
 
 def mult_potentials(pos, q, d, Q, mu, alpha, group, body, eps_in, thole_a,
-                    masked: bool, same_body_only: bool):
+                    masked: bool, same_body_only: bool, damp_permanent: bool = False):
     """Potential, gradient and Hessian at every site from all OTHER sites.
 
     Permanent moments (q, d, Q) are undamped; when ``masked`` the permanent
@@ -196,8 +196,15 @@ def mult_potentials(pos, q, d, Q, mu, alpha, group, body, eps_in, thole_a,
     energy they are unmasked.  Induced dipoles mu are Thole-damped.  With
     ``same_body_only`` sites of other bodies are ignored (dissolved state of a
     multi-body system: bodies talk only through the solvent).
+    ``damp_permanent`` (the AMOEBA rule, not the paper's): the gradient of the
+    permanent moments is taken with the Thole-damped tensors too (the charge's
+    1/r^3 term with lambda3, the dipole's with lambda3 and lambda5, the
+    quadrupole's with lambda5 and lambda7); it applies to the polarising field
+    only, so it requires ``masked``, and the potential and Hessian stay undamped.
     Returns (phi [Ns], grad [Ns, 3], hess [Ns, 3, 3]).
     """
+    if damp_permanent and not masked:
+        raise ValueError("damp_permanent applies to the polarising (masked) field only")
     ns = pos.shape[0]
     li, mi = _pairs(pos, body)
     if same_body_only:
@@ -216,6 +223,9 @@ def mult_potentials(pos, q, d, Q, mu, alpha, group, body, eps_in, thole_a,
                                   + np.einsum("pij,pijkl->pkl", Qm, T4) / 6.0)
     l3, l5, l7 = thole_lambdas(R, alpha[li], alpha[mi], thole_a)
     D1, D2, D3 = damped_tensors(R, l3, l5, l7)
+    if damp_permanent:
+        grad = perm[:, None] * (qm[:, None] * D1 - np.einsum("pi,pik->pk", dm, D2)
+                                + np.einsum("pij,pijk->pk", Qm, D3) / 6.0)
     mm = mu[mi]
     pot = pot - np.sum(mm * D1, axis=1)
     grad = grad - np.einsum("pi,pik->pk", mm, D2)
@@ -271,6 +281,12 @@ class SolvationResult:
     rhs: np.ndarray
 
 
+def _damp_perm(par) -> bool:
+    """Whether the permanent moments' polarising field is Thole-damped (an AMOEBA rule the
+    paper does not state; off unless the parameters ask for it)."""
+    return bool(getattr(par, "damp_permanent", False))
+
+
 def _rms(x):
     return float(np.sqrt(np.sum(x * x) / max(1, x.shape[0])))
 
@@ -281,7 +297,7 @@ def vacuum_scf(sites, par, direct: bool = False):
     four_pi_alpha = FOUR_PI * sites.alpha
     _, gperm, _ = mult_potentials(sites.pos, sites.q, sites.d, sites.Q, np.zeros((ns, 3)), sites.alpha,
                                   sites.group, sites.body, par.eps_in, par.thole_a, masked=True,
-                                  same_body_only=False)
+                                  same_body_only=False, damp_permanent=_damp_perm(par))
     Eperm = -gperm
     if direct:
         T = thole_matrix(sites.pos, sites.alpha, sites.body, par.eps_in, par.thole_a, False)
@@ -336,7 +352,7 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
 
     _, gperm, _ = mult_potentials(sites.pos, sites.q, sites.d, sites.Q, np.zeros((ns, 3)), sites.alpha,
                                   sites.group, sites.body, par.eps_in, par.thole_a, masked=True,
-                                  same_body_only=True)
+                                  same_body_only=True, damp_permanent=_damp_perm(par))
     Eperm = -gperm
 
     def E_induced(mu):
