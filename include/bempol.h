@@ -103,6 +103,11 @@ typedef struct {
   double thole_a;              /* Thole damping parameter (AMOEBA: 0.39) */
   int refine_scope;            /* which BEM solves of bempol_solve* are refined when residual_op != op:
                                   BEMPOL_REFINE_EVERY or BEMPOL_REFINE_FINAL (see below) */
+  int thole_perm;              /* 1: Thole-damp the permanent moments' polarising field too (AMOEBA's
+                                  rule; the paper damps only the induced dipoles): the 1/r^3 terms
+                                  take lambda3, the 1/r^5 lambda5, the 1/r^7 lambda7.  The energy's
+                                  permanent terms stay undamped.  bempol_gradient does not support
+                                  it (BEMPOL_ERR_ARG).  0 (default): the paper's rule. */
 } bempol_params;
 
 /* Scope of the FP64 iterative refinement inside bempol_solve* (residual_op != op).
@@ -151,7 +156,8 @@ typedef struct {
 
 /* Fill `p` with the defaults: eps 1/80, kappa 0.125, K=4, near 2.0, theta 0.5,
  * P=5, leaf 256, GMRES 1e-8/100/500, SCF 1e-8/omega 0.7/200, op FP64 direct,
- * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39, refine_scope EVERY. */
+ * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39, refine_scope EVERY,
+ * thole_perm 0. */
 void bempol_default_params(bempol_params* p);
 
 /* Create a context on CUDA device `device`.  Validates `p` (ranges above);

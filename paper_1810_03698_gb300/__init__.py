@@ -35,7 +35,7 @@ class Params(C.Structure):
         ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
         ("scf_tol", C.c_double), ("sor_omega", C.c_double), ("scf_maxit", C.c_int),
         ("op", C.c_int), ("residual_op", C.c_int), ("inner_tol", C.c_double), ("refine_maxit", C.c_int),
-        ("thole_a", C.c_double), ("refine_scope", C.c_int),
+        ("thole_a", C.c_double), ("refine_scope", C.c_int), ("thole_perm", C.c_int),
     ]
 
 
@@ -493,7 +493,8 @@ def _param_kw(par, overrides):
     kw = dict(eps_in=par.eps_in, eps_out=par.eps_out, kappa=par.kappa, gauss_k=par.gauss_k,
               near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,
               gmres_tol=par.gmres_tol, gmres_restart=par.gmres_restart, gmres_maxit=par.gmres_maxit,
-              scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a)
+              scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a,
+              thole_perm=int(bool(getattr(par, "damp_permanent", False))))
     kw.update(overrides)
     return kw
 
@@ -539,13 +540,7 @@ def problem_solver(problem, device: int = 0, stream=None, **overrides) -> Solver
     problem with several bodies (``panel_body``) is loaded as one system of bodies."""
     if getattr(problem, "panel_body", None) is not None:
         return batch_solver([problem], device=device, stream=stream, **overrides)
-    par = problem.params
-    kw = dict(eps_in=par.eps_in, eps_out=par.eps_out, kappa=par.kappa, gauss_k=par.gauss_k,
-              near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,
-              gmres_tol=par.gmres_tol, gmres_restart=par.gmres_restart, gmres_maxit=par.gmres_maxit,
-              scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a)
-    kw.update(overrides)
-    s = Solver(device=device, **kw)
+    s = Solver(device=device, **_param_kw(problem.params, overrides))
     s.set_mesh(np.ascontiguousarray(problem.verts, dtype=np.float64),
                np.ascontiguousarray(problem.tris, dtype=np.int32), stream=stream)
     st = problem.sites

@@ -133,6 +133,7 @@ void check_params(const bempol_params* p) {
   if (!(p->thole_a >= 0)) bad("thole_a must be >= 0");
   if (p->refine_scope != BEMPOL_REFINE_EVERY && p->refine_scope != BEMPOL_REFINE_FINAL)
     bad("refine_scope must be BEMPOL_REFINE_EVERY or BEMPOL_REFINE_FINAL");
+  if (p->thole_perm != 0 && p->thole_perm != 1) bad("thole_perm must be 0 or 1");
 }
 
 bool op_fp32(int op) { return op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE; }
@@ -436,6 +437,7 @@ void bempol_default_params(bempol_params* p) {
   p->refine_maxit = 20;
   p->thole_a = 0.39;
   p->refine_scope = BEMPOL_REFINE_EVERY;
+  p->thole_perm = 0;
 }
 
 bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out) {
@@ -1061,6 +1063,8 @@ bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, doubl
     cudaStream_t s = (cudaStream_t)stream;
     if (!c->have_sites || !c->have_solution) fail(BEMPOL_ERR_STATE, "bempol_gradient needs a completed solve");
     if (units != BEMPOL_UNITS_PAPER && units != BEMPOL_UNITS_KCAL) fail(BEMPOL_ERR_ARG, "bad units");
+    if (c->par.thole_perm)
+      fail(BEMPOL_ERR_ARG, "the adjoint gradient does not differentiate damped permanent fields (thole_perm = 1)");
     EventTimer t(s);
     AdjointOut ao = gradient_internal(*c, grad_q, grad_d, grad_Q, grad_pos, s);
     if (units == BEMPOL_UNITS_KCAL) {

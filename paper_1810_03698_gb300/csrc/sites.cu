@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
                                                         const int* __restrict__ stag, const int* __restrict__ gsite,
                                                         const int* __restrict__ grp_sys,
                                                         const int* __restrict__ sys_site, int ns, int mode,
-                                                        double thole_a, double scale, double* __restrict__ out) {
+                                                        double thole_a, int damp_perm, double scale,
+                                                        double* __restrict__ out) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int l = blockIdx.x * 8 + warp;
   if (l >= ns) return;
@@ -217,6 +218,17 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
     const Real i2 = rinv * rinv, i3 = i2 * rinv, i5 = i3 * i2, i7 = i5 * i2, i9 = i7 * i2;
     const Real R[3] = {Rx, Ry, Rz};
     Real g[3] = {0, 0, 0}, H[6] = {0, 0, 0, 0, 0, 0}, P = 0;
+    // Thole factors of the pair (the induced dipoles' damping, and the permanent moments'
+    // polarising field when damp_perm is set)
+    const double aa = pl.w * pm.w;
+    Real l3 = 1, l5 = 1, l7 = 1;
+    if (aa > 0.0) {
+      const Real au3 = ta * r2 * sqrt(r2) / (Real)sqrt(aa);
+      const Real e = exp(-au3);
+      l3 = (Real)1 - e;
+      l5 = (Real)1 - ((Real)1 + au3) * e;
+      l7 = (Real)1 - ((Real)1 + au3 + (Real)0.6 * au3 * au3) * e;
+    }
     bool perm = !ind_only && ((mode == 1) || (group[m] != gl));
     if (perm) {
       const Real qm = (Real)q[m];
@@ -230,8 +242,13 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
       const Real RQR = QR[0] * Rx + QR[1] * Ry + QR[2] * Rz;
       const Real pR = pv[0] * Rx + pv[1] * Ry + pv[2] * Rz;
       P = qm * rinv + pR * i3 + (Real)0.5 * RQR * i5;
+      // the polarising field (mode 0) optionally with the damped tensors: the 1/r^3 terms
+      // take lambda3, the 1/r^5 terms lambda5, the 1/r^7 term lambda7
+      const bool dp = damp_perm && mode == 0;
+      const Real d3 = dp ? l3 : (Real)1, d5 = dp ? l5 : (Real)1, d7 = dp ? l7 : (Real)1;
       for (int a = 0; a < 3; ++a)
-        g[a] = -qm * R[a] * i3 + pv[a] * i3 - (Real)3 * pR * R[a] * i5 + QR[a] * i5 - (Real)2.5 * RQR * R[a] * i7;
+        g[a] = d3 * (-qm * R[a] * i3 + pv[a] * i3) + d5 * (-(Real)3 * pR * R[a] * i5 + QR[a] * i5) -
+               d7 * (Real)2.5 * RQR * R[a] * i7;
       if (mode == 1) {
         int k = 0;
         for (int a = 0; a < 3; ++a)
@@ -245,15 +262,6 @@ __global__ void __launch_bounds__(256) multipole_kernel(const double4* __restric
     }
     // induced dipole, Thole damped
     const Real mv[3] = {(Real)mu[3 * m], (Real)mu[3 * m + 1], (Real)mu[3 * m + 2]};
-    const double aa = pl.w * pm.w;
-    Real l3 = 1, l5 = 1, l7 = 1;
-    if (aa > 0.0) {
-      const Real au3 = ta * r2 * sqrt(r2) / (Real)sqrt(aa);
-      const Real e = exp(-au3);
-      l3 = (Real)1 - e;
-      l5 = (Real)1 - ((Real)1 + au3) * e;
-      l7 = (Real)1 - ((Real)1 + au3 + (Real)0.6 * au3 * au3) * e;
-    }
     const Real mR = mv[0] * Rx + mv[1] * Ry + mv[2] * Rz;
     P += l3 * mR * i3;
     for (int a = 0; a < 3; ++a) g[a] += l3 * mv[a] * i3 - (Real)3 * l5 * mR * R[a] * i5;
@@ -481,11 +489,11 @@ void multipole_internal(Ctx& c, const double* mu, int mode, double* out, cudaStr
   if (fp32)
     launch(multipole_kernel<float>, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
            c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
-           INV4PI / c.par.eps_in, out);
+           c.par.thole_perm, INV4PI / c.par.eps_in, out);
   else
     launch(multipole_kernel<double>, cdiv(c.ns, 8), 256, 0, s, c.site_pos.p, c.site_q.p, c.site_d.p, c.site_Q.p, mu,
            c.site_group.p, c.stag.p, c.gsite.p, c.grp_sys.p, c.sys_site.p, c.ns, mode, c.par.thole_a,
-           INV4PI / c.par.eps_in, out);
+           c.par.thole_perm, INV4PI / c.par.eps_in, out);
   BP_CHECK_LAUNCH();
 }
 
