@@ -60,14 +60,16 @@ def gauss_rule(k: int):
 
 
 def _rule19():
-    """A fully symmetric 19-node rule of degree 8 with positive weights and interior nodes,
-    for the paper's nearly-singular pairs ("finer quadrature rules with 19 Gauss nodes",
-    Sec. "Comparison with Tinker-APBS"; the paper gives no table).  Orbits: the centroid,
-    four (a, a, 1-2a) orbits of 3 nodes and one (b, c, 1-b-c) orbit of 6 nodes; their 12
-    parameters solve the 10 moment equations of the S3-invariant polynomials of degree
-    <= 8, int l1^i l2^j l3^k dA / A = 2 i! j! k! / (i+j+k+2)!, by least squares from seeded
-    starting points (the first solution with positive weights and interior nodes is kept;
-    the system is underdetermined, so this is one member of the degree-8 family).  Cached."""
+    """The fully symmetric 19-node rule of degree 9 for the paper's nearly-singular pairs
+    ("finer quadrature rules with 19 Gauss nodes", Sec. "Comparison with Tinker-APBS"; the
+    paper gives no table).  Orbits: the centroid, four (a, a, 1-2a) orbits of 3 nodes and one
+    (b, c, 1-b-c) orbit of 6 nodes, 12 parameters in all; the S3-invariant polynomials of
+    degree <= 9 give exactly 12 independent moment equations,
+    int l1^i l2^j l3^k dA / A = 2 i! j! k! / (i+j+k+2)!,
+    so the degree-9 rule with positive weights and interior nodes is an isolated solution
+    (Dunavant, Int. J. Numer. Meth. Eng. 21 (1985) 1129, 19 points, degree 9).  It is solved
+    here by least squares on the monomial moments from that table's values rounded to 3
+    digits; the solve, not the rounded start, fixes every digit.  Cached."""
     global _RULE19
     if _RULE19 is not None:
         return _RULE19
@@ -85,23 +87,23 @@ def _rule19():
         w += [w5 / 6] * 6
         return np.array(lam), np.array(w)
 
-    mons = [(i, j, k) for i in range(9) for j in range(9) for k in range(9) if i + j + k <= 8 and i >= j >= k]
+    mons = [(i, j, k) for i in range(10) for j in range(10) for k in range(10) if i + j + k <= 9 and i >= j >= k]
     exact = np.array([2.0 * factorial(i) * factorial(j) * factorial(k) / factorial(i + j + k + 2) for i, j, k in mons])
 
     def resid(p):
         lam, w = nodes(p)
-        return np.array([np.sum(w * lam[:, 0] ** i * lam[:, 1] ** j * lam[:, 2] ** k) for i, j, k in mons]) - exact
+        got = np.array([np.sum(w * lam[:, 0] ** i * lam[:, 1] ** j * lam[:, 2] ** k) for i, j, k in mons])
+        return got / exact - 1.0  # relative: the high moments are ~1e-7 and must count as much
 
-    rng = np.random.default_rng(0)
-    for _ in range(1000):
-        p0 = np.array([0.1, *rng.uniform(0.02, 0.49, 4), 0.15, 0.15, 0.15, 0.15, rng.uniform(0.01, 0.3),
-                       rng.uniform(0.2, 0.5), 0.2])
-        r = least_squares(resid, p0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=20000)
-        lam, w = nodes(r.x)
-        if np.abs(resid(r.x)).max() < 1e-14 and w.min() > 0 and lam.min() > 0:
-            _RULE19 = (lam, w)
-            return _RULE19
-    raise RuntimeError("no 19-node degree-8 rule found")
+    # start: the table's centroid weight, orbit parameters and orbit weights (sum of the
+    # orbit's node weights), to 3 digits
+    p0 = np.array([0.0971, 0.490, 0.437, 0.188, 0.0447, 0.094, 0.233, 0.239, 0.0767, 0.0368, 0.222, 0.260])
+    r = least_squares(resid, p0, xtol=1e-15, ftol=1e-15, gtol=1e-15, max_nfev=2000)
+    lam, w = nodes(r.x)
+    if not (np.abs(resid(r.x)).max() < 1e-13 and w.min() > 0 and lam.min() > 0):
+        raise RuntimeError("the 19-node degree-9 rule did not converge")
+    _RULE19 = (lam, w)
+    return _RULE19
 
 
 _RULE19 = None

@@ -124,12 +124,12 @@ def test_double_layer_jump_across_panel():
 
 
 def test_gauss_rules_exactness():
-    """The K=1, 3, 4, 19 rules integrate polynomials of degree 1, 2, 3, 8 exactly over a triangle."""
+    """The K=1, 3, 4, 19 rules integrate polynomials of degree 1, 2, 3, 9 exactly over a triangle."""
     # exact: int over the unit right triangle of x^i y^j = i! j! / (i + j + 2)!
     from math import factorial
     v = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
     f = np.array([[0, 1, 2]], dtype=np.int32)
-    for k, deg in ((1, 1), (3, 2), (4, 3), (19, 8)):
+    for k, deg in ((1, 1), (3, 2), (4, 3), (19, 9)):
         y, w = geometry.gauss_points(v, f, k)
         for i in range(deg + 1):
             for j in range(deg + 1 - i):
@@ -143,6 +143,25 @@ def test_gauss_rules_exactness():
     lam, wb = geometry.gauss_rule(19)
     assert lam.shape == (19, 3) and np.all(wb > 0) and np.all(lam > 0)
     assert np.allclose(lam.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+
+
+def test_rule19_is_the_published_degree9_rule():
+    """The moment equations of degree 9 fix the 19-node rule's 12 orbit parameters; the
+    solution equals the published table (tests/golden/dunavant19_degree9.json, 15 digits)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "dunavant19_degree9.json")))
+    lam, w = geometry.gauss_rule(19)
+    assert abs(w[0] - gold["centroid_weight"]) < 1e-13
+    assert np.allclose(lam[0], 1.0 / 3.0, rtol=0, atol=1e-16)
+    for k, orb in enumerate(gold["orbits_aa"]):
+        rows = lam[1 + 3 * k:4 + 3 * k]
+        assert np.allclose(np.sort(rows, axis=1), [np.sort([orb["a"], orb["a"], 1 - 2 * orb["a"]])] * 3, rtol=0, atol=1e-13)
+        assert np.allclose(w[1 + 3 * k:4 + 3 * k], orb["weight_per_node"], rtol=0, atol=1e-13)
+    o = gold["orbit_abc"]
+    want = np.sort([o["b"], o["c"], 1 - o["b"] - o["c"]])
+    assert np.allclose(np.sort(lam[13:], axis=1), [want] * 6, rtol=0, atol=1e-13)
+    assert np.allclose(w[13:], o["weight_per_node"], rtol=0, atol=1e-13)
 
 
 def test_rule19_on_nearly_singular_pairs():
