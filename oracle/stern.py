@@ -43,7 +43,8 @@ from . import bem, panel
 def cross_layers(tgt: bem.Mesh, src: bem.Mesh, kappa: float, near_factor: float, row_chunk: int = 256):
     """Dense [Nt, Ns] VL, KL, VY, KY for targets at the centroids of ``tgt`` and the panels
     of ``src`` (two different surfaces): the K-node rule, replaced by the accurate panel
-    integrals where |x_i - c_j|^2 < near_factor^2 A_j (the source panel's area)."""
+    integrals where |x_i - c_j|^2 < near_factor^2 A_i, A_i the area of the element holding
+    the collocation point (Sec. "The boundary element method"), as on one surface."""
     from scipy.spatial import cKDTree
 
     nt, ns = tgt.n, src.n
@@ -57,13 +58,13 @@ def cross_layers(tgt: bem.Mesh, src: bem.Mesh, kappa: float, near_factor: float,
         nr = np.tile(src.normal, (m, 1))
         for o, v in zip(out, panel.kpoint_sums(x, yg, wg, nr, kappa)):
             o[s:e] = v.reshape(m, ns)
-    thr = near_factor * near_factor * src.area
+    thr = (near_factor * near_factor) * tgt.area
     radius = float(np.sqrt(thr.max())) * (1.0 + 1e-6) + 1e-12
     cand = cKDTree(src.cen).query_ball_point(tgt.cen, radius)
     ci = np.repeat(np.arange(nt), [len(c) for c in cand])
     cj = np.concatenate([np.asarray(c, dtype=np.int64) for c in cand]) if nt else np.zeros(0, np.int64)
     d = tgt.cen[ci] - src.cen[cj]
-    keep = np.sum(d * d, axis=1) < thr[cj]
+    keep = (d[:, 0] * d[:, 0] + d[:, 1] * d[:, 1]) + d[:, 2] * d[:, 2] < thr[ci]
     ci, cj = ci[keep], cj[keep]
     if ci.size:
         t = src.tris[cj]
