@@ -44,6 +44,7 @@ class Params:
     scf_maxit: int = 200
     thole_a: float = 0.39
     damp_permanent: bool = False  # Thole-damp the permanent moments' polarising field (AMOEBA; not the paper's rule)
+    near_rule: str = "exact"      # near pairs off the self panel: "exact" (semi-analytical) or "gauss19"
 
 
 @dataclass

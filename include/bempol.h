@@ -108,7 +108,15 @@ typedef struct {
                                   take lambda3, the 1/r^5 lambda5, the 1/r^7 lambda7.  The energy's
                                   permanent terms stay undamped.  bempol_gradient does not support
                                   it (BEMPOL_ERR_ARG).  0 (default): the paper's rule. */
+  int near_rule;               /* accurate value of a near pair other than the self panel:
+                                  BEMPOL_NEAR_SEMI_ANALYTICAL (default) or BEMPOL_NEAR_GAUSS19, the
+                                  fully symmetric 19-node rule of degree 9 (Dunavant 1985), which
+                                  the paper's production runs apply within 1.25 sqrt(A) (Sec.
+                                  "Comparison with Tinker-APBS").  The self panel stays
+                                  semi-analytical.  Fixed once a mesh is set. */
 } bempol_params;
+
+enum { BEMPOL_NEAR_SEMI_ANALYTICAL = 0, BEMPOL_NEAR_GAUSS19 = 19 };
 
 /* Scope of the FP64 iterative refinement inside bempol_solve* (residual_op != op).
  *  BEMPOL_REFINE_EVERY: every BEM solve of both induced-dipole iterations is refined, and the
@@ -157,7 +165,7 @@ typedef struct {
 /* Fill `p` with the defaults: eps 1/80, kappa 0.125, K=4, near 2.0, theta 0.5,
  * P=5, leaf 256, GMRES 1e-8/100/500, SCF 1e-8/omega 0.7/200, op FP64 direct,
  * residual FP64 direct, inner_tol 1e-3, refine 20, Thole 0.39, refine_scope EVERY,
- * thole_perm 0. */
+ * thole_perm 0, near_rule semi-analytical. */
 void bempol_default_params(bempol_params* p);
 
 /* Create a context on CUDA device `device`.  Validates `p` (ranges above);
@@ -199,7 +207,8 @@ bempol_status bempol_set_mesh(bempol_ctx* c, int64_t nv, const double* verts, in
  * All host or device per `where`.  Validation: every site strictly inside the
  * surface and farther than near_factor*sqrt(A_j) from every panel centroid j
  * (BEMPOL_ERR_SITES).  Requires bempol_set_mesh first, and a single-body mesh
- * (BEMPOL_ERR_STATE; see bempol_set_sites_systems). */
+ * (BEMPOL_ERR_STATE; see bempol_set_sites_systems) or a Stern-layer mesh
+ * (bempol_set_mesh_stern; the sites then lie inside both surfaces). */
 bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, const double* q,
                                const double* d, const double* Q, const double* alpha,
                                const int32_t* group, int where, void* stream);
@@ -218,6 +227,26 @@ bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, con
 bempol_status bempol_set_mesh_systems(bempol_ctx* c, int64_t nv, const double* verts, int64_t nt,
                                       const int32_t* tris, const int32_t* panel_system,
                                       const int32_t* panel_body, int where, void* stream);
+
+/* Stern (ion-exclusion) layer, Sec. "Spherical cavity": the dielectric boundary Gamma_1
+ * (verts1 [nv1*3], tris1 [nt1*3]) strictly inside the surface Gamma_2 (verts2, tris2) where
+ * the ions begin; three regions: Laplace with eps_in inside Gamma_1, Laplace with eps_out
+ * and no ions between, Yukawa (kappa) with eps_out outside Gamma_2.  Unknowns phi and
+ * psi = dphi/dn on both surfaces (psi on Gamma_1 as seen from the solute), laid out as for
+ * one surface over the panels of both: caller order is Gamma_1's triangles, then Gamma_2's.
+ * Rows, with r = eps_in/eps_out and Kij, Vij the Laplace layers at Gamma_i from Gamma_j:
+ *   Gamma_1: phi1/2 + K11 phi1 - V11 psi1 = RHS;
+ *            phi1/2 - K11 phi1 + r V11 psi1 + K12 phi2 - V12 psi2 = 0;
+ *   Gamma_2: phi2/2 + K22 phi2 - V22 psi2 - K21 phi1 + r V21 psi1 = 0;
+ *            phi2/2 - KY22 phi2 + VY22 psi2 = 0.
+ * The reaction field at the sites is Gamma_1's.  Host arrays only (`where` must be
+ * BEMPOL_HOST).  Each surface must be closed and Gamma_1 must lie inside Gamma_2
+ * (BEMPOL_ERR_MESH).  Such a context takes the direct operator forms only (a treecode
+ * form is BEMPOL_ERR_ARG), its sites are set with bempol_set_sites (all inside Gamma_1),
+ * and bempol_gradient does not cover it (BEMPOL_ERR_ARG). */
+bempol_status bempol_set_mesh_stern(bempol_ctx* c, int64_t nv1, const double* verts1, int64_t nt1,
+                                    const int32_t* tris1, int64_t nv2, const double* verts2, int64_t nt2,
+                                    const int32_t* tris2, int where, void* stream);
 
 /* Sites of a context set with bempol_set_mesh_systems.  As bempol_set_sites, plus
  *   site_system, site_body [ns] int32 (NULL = all 0), host or device per `where`.
@@ -444,6 +473,14 @@ typedef struct {
 } bempol_peaks;
 
 bempol_status bempol_measure_peaks(int device, int iters, int reps, bempol_peaks* out);
+
+/* The 19-node triangle rule used by near_rule = BEMPOL_NEAR_GAUSS19 (Sec. "Comparison with
+ * Tinker-APBS": 19 Gauss nodes for near pairs): the fully symmetric rule of degree 9, solved
+ * on the host from its moment equations.  Writes 19 x 4 doubles to host memory `nodes`
+ * (caller-owned): barycentric coordinates l1, l2, l3 and the weight (weights sum to 1;
+ * node 0 is the centroid).  Host only: needs no device or context.
+ * BEMPOL_ERR_ARG (NULL) / BEMPOL_ERR_NOT_CONVERGED (the solve failed). */
+bempol_status bempol_near_rule19(double* nodes);
 
 /* Target sharding over several GPUs (Sec. "The treecode algorithm": the source-target
  * and box-target interactions of different targets are independent).  Each GPU holds

@@ -38,6 +38,7 @@ from . import multipole as mp
 def _dense_solver(problem):
     par = problem.params
     mesh = bem.build_mesh(problem.verts, problem.tris, par.gauss_k, par.near_factor,
+                          near_rule=getattr(par, "near_rule", "exact"),
                           body=getattr(problem, "panel_body", None))
     solver = bem.DenseSolver(mesh, par.eps_in, par.eps_out, par.kappa)
     solver.mesh = mesh

@@ -337,6 +337,7 @@ def solvation(problem, solver=None, direct_polarization: bool = False) -> Solvat
     ns = sites.n
     if solver is None:
         mesh = bem.build_mesh(problem.verts, problem.tris, par.gauss_k, par.near_factor,
+                              near_rule=getattr(par, "near_rule", "exact"),
                               body=getattr(problem, "panel_body", None))
         solver = bem.DenseSolver(mesh, par.eps_in, par.eps_out, par.kappa)
         solver.mesh = mesh

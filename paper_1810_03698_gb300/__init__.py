@@ -22,6 +22,7 @@ OP_FP64_DIRECT, OP_FP32_DIRECT, OP_FP32_TREE, OP_FP64_TREE = 0, 1, 2, 3
 OP_NAMES = {"fp64_direct": 0, "fp32_direct": 1, "fp32_tree": 2, "fp64_tree": 3}
 REFINE_EVERY, REFINE_FINAL = 0, 1
 REFINE_NAMES = {"every": 0, "final": 1}
+NEAR_RULES = {"semi_analytical": 0, "exact": 0, "gauss19": 19}
 
 STATUS = {0: "OK", 1: "ERR_ARG", 2: "ERR_MESH", 3: "ERR_SITES", 4: "ERR_NOT_CONVERGED", 5: "ERR_CUDA",
           6: "ERR_TIMEOUT", 7: "ERR_OOM", 8: "ERR_STATE"}
@@ -35,7 +36,7 @@ class Params(C.Structure):
         ("gmres_tol", C.c_double), ("gmres_restart", C.c_int), ("gmres_maxit", C.c_int),
         ("scf_tol", C.c_double), ("sor_omega", C.c_double), ("scf_maxit", C.c_int),
         ("op", C.c_int), ("residual_op", C.c_int), ("inner_tol", C.c_double), ("refine_maxit", C.c_int),
-        ("thole_a", C.c_double), ("refine_scope", C.c_int), ("thole_perm", C.c_int),
+        ("thole_a", C.c_double), ("refine_scope", C.c_int), ("thole_perm", C.c_int), ("near_rule", C.c_int),
     ]
 
 
@@ -109,6 +110,7 @@ def _load():
         "bempol_set_mesh": (i32, [vp, i64, vp, i64, vp, i32, vp]),
         "bempol_set_sites": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, i32, vp]),
         "bempol_set_mesh_systems": (i32, [vp, i64, vp, i64, vp, vp, vp, i32, vp]),
+        "bempol_set_mesh_stern": (i32, [vp, i64, vp, i64, vp, i64, vp, i64, vp, i32, vp]),
         "bempol_set_sites_systems": (i32, [vp, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, vp]),
         "bempol_systems": (i32, [vp, C.POINTER(i64), C.POINTER(i64)]),
         "bempol_solve": (i32, [vp, vp, C.POINTER(Result)]),
@@ -127,6 +129,7 @@ def _load():
         "bempol_stats_enable": (i32, [vp, i32]),
         "bempol_stats_read": (i32, [vp, C.POINTER(Stats), i32]),
         "bempol_measure_peaks": (i32, [i32, i32, i32, C.POINTER(Peaks)]),
+        "bempol_near_rule19": (i32, [vp]),
         "bempol_shard_rows": (i32, [i64, vp, i32, vp]),
         "bempol_set_shard": (i32, [vp, i32, i32, vp, ExchangeFn, vp]),
         "bempol_shard_bounds": (i32, [vp, vp]),
@@ -156,6 +159,8 @@ def default_params(**kw) -> Params:
             v = OP_NAMES[v]
         if k == "refine_scope" and isinstance(v, str):
             v = REFINE_NAMES[v]
+        if k == "near_rule" and isinstance(v, str):
+            v = NEAR_RULES[v]
         setattr(p, k, v)
     return p
 
@@ -218,6 +223,8 @@ class Solver:
                 v = OP_NAMES[v]
             if k == "refine_scope" and isinstance(v, str):
                 v = REFINE_NAMES[v]
+            if k == "near_rule" and isinstance(v, str):
+                v = NEAR_RULES[v]
             setattr(self.params, k, v)
         self._chk(_lib.bempol_set_params(self._h, C.byref(self.params)))
 
@@ -238,6 +245,18 @@ class Solver:
                 raise ValueError("system/body arrays must live where the mesh arrays live")
         self._chk(_lib.bempol_set_mesh_systems(self._h, verts.shape[0], pv, tris.shape[0], pt, ps, pb, wv,
                                                _stream(stream)))
+
+    def set_mesh_stern(self, verts1, tris1, verts2, tris2, stream=None):
+        """Dielectric boundary (verts1, tris1) inside the ion-exclusion surface (verts2,
+        tris2), host arrays (bempol_set_mesh_stern); panels in caller order are the first
+        surface's, then the second's."""
+        v1 = np.ascontiguousarray(verts1, dtype=np.float64)
+        t1 = np.ascontiguousarray(tris1, dtype=np.int32)
+        v2 = np.ascontiguousarray(verts2, dtype=np.float64)
+        t2 = np.ascontiguousarray(tris2, dtype=np.int32)
+        self._chk(_lib.bempol_set_mesh_stern(self._h, v1.shape[0], v1.ctypes.data, t1.shape[0], t1.ctypes.data,
+                                             v2.shape[0], v2.ctypes.data, t2.shape[0], t2.ctypes.data, HOST,
+                                             _stream(stream)))
 
     def set_sites(self, pos, q, d, Q, alpha, group=None, system=None, body=None, stream=None):
         """Point multipoles; with several bodies/systems pass ``system`` / ``body`` per
@@ -417,6 +436,16 @@ def measure_peaks(device: int = 0, iters: int = 65536, reps: int = 3) -> dict:
     return {k: getattr(r, k) for k, _ in Peaks._fields_}
 
 
+def near_rule19() -> np.ndarray:
+    """The library's 19-node triangle rule [19, 4]: l1, l2, l3, weight (bempol_near_rule19,
+    host only)."""
+    out = np.zeros((19, 4), dtype=np.float64)
+    st = _lib.bempol_near_rule19(out.ctypes.data)
+    if st != 0:
+        raise BempolError(st, "bempol_near_rule19 failed")
+    return out
+
+
 def shard_rows(n_units: int, world: int, cost=None):
     """Contiguous ranges of nearly equal cost (bempol_shard_rows, host only)."""
     b = np.zeros(world + 1, dtype=np.int64)
@@ -494,7 +523,8 @@ def _param_kw(par, overrides):
               near_factor=par.near_factor, theta=par.theta, order=par.order, leaf=par.leaf,
               gmres_tol=par.gmres_tol, gmres_restart=par.gmres_restart, gmres_maxit=par.gmres_maxit,
               scf_tol=par.scf_tol, sor_omega=par.sor_omega, scf_maxit=par.scf_maxit, thole_a=par.thole_a,
-              thole_perm=int(bool(getattr(par, "damp_permanent", False))))
+              thole_perm=int(bool(getattr(par, "damp_permanent", False))),
+              near_rule=NEAR_RULES[getattr(par, "near_rule", "exact")])
     kw.update(overrides)
     return kw
 

@@ -134,6 +134,8 @@ void check_params(const bempol_params* p) {
   if (p->refine_scope != BEMPOL_REFINE_EVERY && p->refine_scope != BEMPOL_REFINE_FINAL)
     bad("refine_scope must be BEMPOL_REFINE_EVERY or BEMPOL_REFINE_FINAL");
   if (p->thole_perm != 0 && p->thole_perm != 1) bad("thole_perm must be 0 or 1");
+  if (p->near_rule != BEMPOL_NEAR_SEMI_ANALYTICAL && p->near_rule != BEMPOL_NEAR_GAUSS19)
+    bad("near_rule must be BEMPOL_NEAR_SEMI_ANALYTICAL or BEMPOL_NEAR_GAUSS19");
 }
 
 bool op_fp32(int op) { return op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE; }
@@ -217,6 +219,7 @@ std::vector<int> make_groups(Ctx& c, int64_t nt, const std::vector<int32_t>& sy,
 }
 
 void ensure_tree(Ctx& c, int op, cudaStream_t s) {
+  if (op_tree(op) && c.stern) fail(BEMPOL_ERR_ARG, "a Stern-layer mesh takes the direct operator forms only");
   if (op_tree(op) && !c.tree_ready) build_tree(c, s);
 }
 
@@ -277,7 +280,8 @@ struct EventTimer {
 };
 
 void set_mesh_impl(Ctx* c, int64_t nv, const double* verts, int64_t nt, const int32_t* tris,
-                   const int32_t* panel_system, const int32_t* panel_body, int where, cudaStream_t s) {
+                   const int32_t* panel_system, const int32_t* panel_body, int where, cudaStream_t s,
+                   bool stern = false) {
   if (nv < 4 || nt < 4 || !verts || !tris) fail(BEMPOL_ERR_ARG, "need nv >= 4, nt >= 4 and non-NULL arrays");
   if (nt >= (int64_t)1 << 24) fail(BEMPOL_ERR_ARG, "at most 16,777,215 triangles");
   if (nv >= (int64_t)1 << 31) fail(BEMPOL_ERR_ARG, "too many vertices");
@@ -286,6 +290,7 @@ void set_mesh_impl(Ctx* c, int64_t nv, const double* verts, int64_t nt, const in
   c->have_sites = false;
   c->have_solution = false;
   c->tree_ready = false;
+  c->stern = stern;
   c->n = (int)nt;
   c->nv = (int)nv;
   c->K = c->par.gauss_k;
@@ -309,6 +314,10 @@ void set_mesh_impl(Ctx* c, int64_t nv, const double* verts, int64_t nt, const in
   build_geometry(*c, dv.p, ht.data(), grp, s);
   lap(1);
   build_blocks(*c, s);
+  if (stern) {
+    build_stern_blocks(*c, s);
+    stern_check_nested(*c, s);
+  }
   lap(2);
   build_tree(*c, s);  // the octree also narrows the near-pair search
   lap(3);
@@ -346,6 +355,8 @@ void set_sites_impl(Ctx* c, int64_t ns, const double* pos, const double* q, cons
       fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": its (system, body) has no surface");
     if (l > 0 && g < tag[l - 1])
       fail(BEMPOL_ERR_SITES, "sites must be ordered by system, then body (site " + std::to_string(l) + ")");
+    if (c->stern && g != 0)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + ": with a Stern layer every site lies inside body 0");
     tag[l] = g;
     ++c->h_gsite[g + 1];
   }
@@ -438,6 +449,7 @@ void bempol_default_params(bempol_params* p) {
   p->thole_a = 0.39;
   p->refine_scope = BEMPOL_REFINE_EVERY;
   p->thole_perm = 0;
+  p->near_rule = BEMPOL_NEAR_SEMI_ANALYTICAL;
 }
 
 bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out) {
@@ -455,7 +467,7 @@ bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out
     c = new bempol_ctx();
     c->par = *p;
     c->device = device;
-    init_gauss_legendre();
+    init_near_rules();
     c->scal.alloc(16);
     c->dev_err.alloc(1);
     BP_CUDA(cudaMemset(c->dev_err.p, 0, sizeof(int)));
@@ -471,9 +483,11 @@ bempol_status bempol_create(const bempol_params* p, int device, bempol_ctx** out
 bempol_status bempol_set_params(bempol_ctx* c, const bempol_params* p) {
   return guard(c, [&] {
     check_params(p);
-    bool geo = p->gauss_k != c->par.gauss_k || p->near_factor != c->par.near_factor || p->kappa != c->par.kappa;
+    bool geo = p->gauss_k != c->par.gauss_k || p->near_factor != c->par.near_factor || p->kappa != c->par.kappa ||
+               p->near_rule != c->par.near_rule;
     bool tree = p->leaf != c->par.leaf || p->theta != c->par.theta || geo;
-    if (geo && c->have_mesh) fail(BEMPOL_ERR_STATE, "gauss_k, near_factor and kappa are fixed once a mesh is set");
+    if (geo && c->have_mesh)
+      fail(BEMPOL_ERR_STATE, "gauss_k, near_factor, near_rule and kappa are fixed once a mesh is set");
     c->par = *p;
     c->have_solution = false;
     if (tree) c->tree_ready = false;
@@ -501,11 +515,38 @@ bempol_status bempol_set_mesh_systems(bempol_ctx* c, int64_t nv, const double* v
   });
 }
 
+bempol_status bempol_set_mesh_stern(bempol_ctx* c, int64_t nv1, const double* verts1, int64_t nt1,
+                                    const int32_t* tris1, int64_t nv2, const double* verts2, int64_t nt2,
+                                    const int32_t* tris2, int where, void* stream) {
+  return guard(c, [&] {
+    if (where != BEMPOL_HOST) fail(BEMPOL_ERR_ARG, "the Stern-layer surfaces are read from host memory");
+    if (nv1 < 4 || nt1 < 4 || nv2 < 4 || nt2 < 4 || !verts1 || !tris1 || !verts2 || !tris2)
+      fail(BEMPOL_ERR_ARG, "need nv >= 4, nt >= 4 and non-NULL arrays for both surfaces");
+    if (nv1 + nv2 >= (int64_t)1 << 31 || nt1 + nt2 >= (int64_t)1 << 24) fail(BEMPOL_ERR_ARG, "surfaces too large");
+    // one mesh of two bodies: the dielectric boundary (body 0) and the ion-exclusion surface
+    std::vector<double> v(3 * (size_t)(nv1 + nv2));
+    std::copy(verts1, verts1 + 3 * nv1, v.begin());
+    std::copy(verts2, verts2 + 3 * nv2, v.begin() + 3 * nv1);
+    std::vector<int32_t> t(3 * (size_t)(nt1 + nt2)), body(nt1 + nt2, 0);
+    std::copy(tris1, tris1 + 3 * nt1, t.begin());
+    for (int64_t k = 0; k < 3 * nt2; ++k) {
+      if (tris2[k] < 0 || tris2[k] >= nv2) fail(BEMPOL_ERR_MESH, "vertex index out of range in the second surface");
+      t[3 * nt1 + k] = tris2[k] + (int32_t)nv1;
+    }
+    for (int64_t k = 0; k < 3 * nt1; ++k)
+      if (tris1[k] < 0 || tris1[k] >= nv1) fail(BEMPOL_ERR_MESH, "vertex index out of range in the first surface");
+    for (int64_t k = nt1; k < nt1 + nt2; ++k) body[k] = 1;
+    set_mesh_impl(c, nv1 + nv2, v.data(), nt1 + nt2, t.data(), nullptr, body.data(), BEMPOL_HOST,
+                  (cudaStream_t)stream, true);
+  });
+}
+
 bempol_status bempol_set_sites(bempol_ctx* c, int64_t ns, const double* pos, const double* q, const double* d,
                                const double* Q, const double* alpha, const int32_t* group, int where,
                                void* stream) {
   return guard(c, [&] {
-    if (c->ngroup != 1) fail(BEMPOL_ERR_STATE, "the mesh has several bodies: use bempol_set_sites_systems");
+    if (c->ngroup != 1 && !c->stern)
+      fail(BEMPOL_ERR_STATE, "the mesh has several bodies: use bempol_set_sites_systems");
     set_sites_impl(c, ns, pos, q, d, Q, alpha, group, nullptr, nullptr, where, (cudaStream_t)stream);
   });
 }
@@ -1065,6 +1106,7 @@ bempol_status bempol_gradient(bempol_ctx* c, void* stream, double* grad_q, doubl
     if (units != BEMPOL_UNITS_PAPER && units != BEMPOL_UNITS_KCAL) fail(BEMPOL_ERR_ARG, "bad units");
     if (c->par.thole_perm)
       fail(BEMPOL_ERR_ARG, "the adjoint gradient does not differentiate damped permanent fields (thole_perm = 1)");
+    if (c->stern) fail(BEMPOL_ERR_ARG, "the adjoint gradient does not cover the Stern-layer system");
     EventTimer t(s);
     AdjointOut ao = gradient_internal(*c, grad_q, grad_d, grad_Q, grad_pos, s);
     if (units == BEMPOL_UNITS_KCAL) {

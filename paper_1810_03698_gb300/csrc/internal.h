@@ -199,7 +199,8 @@ struct Ctx {
   DBuf<float4> str32;
   DBuf<int> near_ptr;        // [n+1]
   DBuf<int> near_col;        // [nnz]
-  DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections
+  DBuf<double4> near_corr;   // [nnz] VL, KL, VY, KY corrections (Stern layer: a pair across the
+                             // two surfaces holds VL, KL, 0, 0)
   int64_t nnz = 0;
   // the near table by columns: for panel j, entries [near_ptrT[j], near_ptrT[j+1])
   // hold (row i, index into near_corr) of every near pair (i, j)
@@ -211,6 +212,14 @@ struct Ctx {
   Tree tree;
   bool tree_ready = false;
   SiteTree stree;
+
+  // Stern (ion-exclusion) layer: group 0 is the dielectric boundary, group 1 the surface
+  // where the ions begin; the direct blocks' source ranges over their own surface (A) and
+  // over the other one (B), and the second pass's partial sums
+  bool stern = false;
+  DBuf<int4> stern_rngA, stern_rngB;
+  DBuf<double> stern_part;
+  int stern_splits = 0;
 
   // groups (bodies) and systems
   int ngroup = 1, nsys = 1;
@@ -366,7 +375,7 @@ void build_geometry(Ctx& c, const double* d_verts, const int* h_tris, const std:
 void build_blocks(Ctx& c, cudaStream_t s);
 // near.cu
 void build_near(Ctx& c, cudaStream_t s);
-void init_gauss_legendre();
+void init_near_rules();  // Gauss-Legendre nodes and the 19-node triangle rule (constant memory)
 // p2p.cu
 void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s);
 void p2p_direct(Ctx& c, bool fp32, cudaStream_t s);
@@ -407,6 +416,13 @@ std::vector<double> energy_internal(Ctx& c, const double* react10, const double*
 std::vector<double> sor_update(Ctx& c, double* mu, const double* E_react10, const double* E_mult3, bool vacuum,
                                const int* d_active, cudaStream_t s);
 void site_validation(Ctx& c, cudaStream_t s);
+// direct pair sums with the given per-block source ranges into part [S][4][n]
+int p2p_splits(Ctx& c, int max_range);
+void p2p_direct_ranges(Ctx& c, bool fp32, const int4* rng, double* part, int S, cudaStream_t s);
+// Stern layer (stern.cu)
+void build_stern_blocks(Ctx& c, cudaStream_t s);
+void stern_check_nested(Ctx& c, cudaStream_t s);
+void stern_matvec(Ctx& c, const double* x, double* y, bool fp32, cudaStream_t s);
 // sitetree.cu: reaction potential, field and Hessian at the sites by the treecode, FP32
 // terms with FP64 sums or FP64 (out [ns*10] as site_reaction_internal)
 void site_reaction_tree(Ctx& c, const double* x, double* out, bool fp32, cudaStream_t s);

@@ -25,6 +25,15 @@
 //     dpsi = du/cosh(u) and rho_max = d cosh(u); every singularity of the
 //     integrand then lies at |Im u| >= pi/2, and composite 10-node
 //     Gauss-Legendre on pieces of length <= 1 converges to ~1e-16.
+//
+// Optional 19-node rule (near_rule = BEMPOL_NEAR_GAUSS19): near pairs off the self panel
+// take the sums over the fully symmetric 19-node rule of degree 9 instead, as the paper's
+// production runs do ("finer quadrature rules with 19 Gauss nodes" within 1.25 sqrt(A),
+// Sec. "Comparison with Tinker-APBS").  Its 12 orbit parameters (centroid weight; four
+// (a, a, 1-2a) orbits; one (b, c, 1-b-c) orbit) meet the 12 independent moment
+// conditions of degree <= 9 of a symmetric rule, which fix them; they are computed on the
+// host by Gauss-Newton on the monomial moments from Dunavant's table (Int. J. Numer.
+// Meth. Eng. 21, 1985) rounded to 3 digits.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -38,6 +47,114 @@ namespace {
 constexpr int GL_N = 10;
 __constant__ double c_gl_x[GL_N];
 __constant__ double c_gl_w[GL_N];
+constexpr int R19 = 19;
+__constant__ double4 c_r19[R19];  // barycentric (l1, l2, l3) and weight (sum 1); node 0 = centroid
+
+double factorial(int n) {
+  double f = 1.0;
+  for (int k = 2; k <= n; ++k) f *= k;
+  return f;
+}
+
+double ipow(double x, int e) {
+  double r = 1.0;
+  for (int k = 0; k < e; ++k) r *= x;
+  return r;
+}
+
+// x = {w0, a1..a4, W1..W4, b, c, W5} (W = an orbit's total weight) -> the 19 nodes
+void rule19_nodes(const double* x, double4* out) {
+  const double t = 1.0 / 3.0;
+  int n = 0;
+  out[n++] = make_double4(t, t, t, x[0]);
+  for (int o = 0; o < 4; ++o) {
+    const double a = x[1 + o], z = 1.0 - 2.0 * a, w = x[5 + o] / 3.0;
+    out[n++] = make_double4(a, a, z, w);
+    out[n++] = make_double4(a, z, a, w);
+    out[n++] = make_double4(z, a, a, w);
+  }
+  const double b = x[9], c = x[10], d = 1.0 - b - c, w = x[11] / 6.0;
+  const double perm[6][3] = {{b, c, d}, {b, d, c}, {c, b, d}, {c, d, b}, {d, b, c}, {d, c, b}};
+  for (int k = 0; k < 6; ++k) out[n++] = make_double4(perm[k][0], perm[k][1], perm[k][2], w);
+}
+
+// Gauss-Newton on the relative moment residuals of the monomials l1^i l2^j l3^k
+// (i >= j >= k, i + j + k <= 9; the rule is symmetric, so these cover every monomial),
+// F_m(x) = sum_g w_g l1^i l2^j l3^k / mean_ijk - 1 with mean_ijk = 2 i! j! k! / (i+j+k+2)!.
+// The Jacobian is taken by central differences and each step is solved by Householder
+// QR.  Returns the largest |F_m| at the end.
+double solve_rule19(double* x) {
+  constexpr int NM = 53, NX = 12;
+  int I[NM], Jx[NM], Kx[NM], m = 0;
+  for (int i = 0; i <= 9; ++i)
+    for (int j = 0; j <= i; ++j)
+      for (int k = 0; k <= j; ++k)
+        if (i + j + k <= 9) I[m] = i, Jx[m] = j, Kx[m] = k, ++m;
+  if (m != NM) return 1.0;
+  double mean[NM];
+  for (int t = 0; t < NM; ++t)
+    mean[t] = 2.0 * factorial(I[t]) * factorial(Jx[t]) * factorial(Kx[t]) / factorial(I[t] + Jx[t] + Kx[t] + 2);
+  auto resid = [&](const double* xv, double* r) {
+    double4 nd[R19];
+    rule19_nodes(xv, nd);
+    for (int t = 0; t < NM; ++t) {
+      double f = 0.0;
+      for (int g = 0; g < R19; ++g) f += nd[g].w * ipow(nd[g].x, I[t]) * ipow(nd[g].y, Jx[t]) * ipow(nd[g].z, Kx[t]);
+      r[t] = f / mean[t] - 1.0;
+    }
+  };
+  double fmax = 1.0;
+  int polish = 0;  // steps taken after the residual reached rounding level
+  for (int it = 0; it < 60 && polish < 3; ++it) {
+    double A[NM][NX], b[NM], rp[NM], rm[NM];
+    resid(x, b);
+    fmax = 0.0;
+    for (int t = 0; t < NM; ++t) fmax = std::max(fmax, std::fabs(b[t]));
+    if (fmax < 1e-15) ++polish;
+    for (int c = 0; c < NX; ++c) {
+      double xp[NX], xm[NX];
+      const double h = 1e-7;
+      for (int q = 0; q < NX; ++q) xp[q] = xm[q] = x[q];
+      xp[c] += h;
+      xm[c] -= h;
+      resid(xp, rp);
+      resid(xm, rm);
+      for (int t = 0; t < NM; ++t) A[t][c] = (rp[t] - rm[t]) / (2.0 * h);
+    }
+    // Householder QR of A applied to b; then R dx = (Q^T b)[0:NX]
+    for (int c = 0; c < NX; ++c) {
+      double nrm = 0.0;
+      for (int t = c; t < NM; ++t) nrm += A[t][c] * A[t][c];
+      nrm = std::sqrt(nrm);
+      if (nrm == 0.0) return 1.0;
+      const double alpha = A[c][c] > 0 ? -nrm : nrm;
+      double v[NM];
+      for (int t = 0; t < NM; ++t) v[t] = t < c ? 0.0 : A[t][c];
+      v[c] -= alpha;
+      double vv = 0.0;
+      for (int t = c; t < NM; ++t) vv += v[t] * v[t];
+      if (vv == 0.0) continue;
+      for (int q = c; q < NX; ++q) {
+        double d = 0.0;
+        for (int t = c; t < NM; ++t) d += v[t] * A[t][q];
+        d = 2.0 * d / vv;
+        for (int t = c; t < NM; ++t) A[t][q] -= d * v[t];
+      }
+      double d = 0.0;
+      for (int t = c; t < NM; ++t) d += v[t] * b[t];
+      d = 2.0 * d / vv;
+      for (int t = c; t < NM; ++t) b[t] -= d * v[t];
+    }
+    double dx[NX];
+    for (int r = NX - 1; r >= 0; --r) {
+      double v = b[r];
+      for (int q = r + 1; q < NX; ++q) v -= A[r][q] * dx[q];
+      dx[r] = v / A[r][r];
+    }
+    for (int q = 0; q < NX; ++q) x[q] -= dx[q];
+  }
+  return fmax;
+}
 
 // Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n (host).
 void gauss_legendre(int n, double* x, double* w) {
@@ -167,12 +284,48 @@ __device__ void panel_exact(double xx, double xy, double xz, const double* __res
   out[3] = acc3 * inv4pi;
 }
 
+// Sums of the four kernels over the 19-node rule on panel j (vertices v, centroid and area
+// cj, normal nj) for the target x, over 4 pi.  Node 0 is the panel's centroid as computed
+// for its collocation point.
+__device__ void rule19_sums(double xx, double xy, double xz, const double* __restrict__ v, double4 cj, double4 nj,
+                            double kappa, double out[4], int* __restrict__ coincide) {
+  double vl = 0, kl = 0, vy = 0, ky = 0;
+  for (int g = 0; g < R19; ++g) {
+    const double4 L = c_r19[g];
+    double y0 = cj.x, y1 = cj.y, y2 = cj.z;
+    if (g > 0) {
+      y0 = (L.x * v[0] + L.y * v[3]) + L.z * v[6];
+      y1 = (L.x * v[1] + L.y * v[4]) + L.z * v[7];
+      y2 = (L.x * v[2] + L.y * v[5]) + L.z * v[8];
+    }
+    const double w = L.w * cj.w;
+    const double rx = xx - y0, ry = xy - y1, rz = xz - y2;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) {  // a node of another panel on the collocation point: overlapping panels
+      atomicExch(coincide, 1);
+      continue;
+    }
+    const double R = sqrt(r2), inv = 1.0 / R, inv3 = inv * inv * inv;
+    const double nr = nj.x * rx + nj.y * ry + nj.z * rz;
+    const double ek = exp(-kappa * R);
+    vl += w * inv;
+    kl += w * nr * inv3;
+    vy += w * ek * inv;
+    ky += w * nr * (1.0 + kappa * R) * ek * inv3;
+  }
+  const double inv4pi = 0.25 / M_PI;
+  out[0] = vl * inv4pi;
+  out[1] = kl * inv4pi;
+  out[2] = vy * inv4pi;
+  out[3] = ky * inv4pi;
+}
+
 // one thread per near pair k (row found by binary search in the CSR pointers)
 __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restrict__ col, int n, int nnz,
                                  const double4* __restrict__ tgt64, const double* __restrict__ vert9,
                                  const double4* __restrict__ src64, const double4* __restrict__ nrm64, int K,
-                                 double kappa, const int* __restrict__ ptag, double4* __restrict__ corr,
-                                 int* __restrict__ coincide) {
+                                 double kappa, int rule19, int stern, const int* __restrict__ ptag,
+                                 double4* __restrict__ corr, int* __restrict__ coincide) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nnz) return;
   int lo = 0, hi = n - 1;  // largest row i with ptr[i] <= k
@@ -188,8 +341,11 @@ __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restr
   {
     int j = col[k];
     double ex[4];
-    panel_exact(x.x, x.y, x.z, vert9 + 9 * (size_t)j, i == j, kappa, ex);
     double4 nj = nrm64[j];
+    if (rule19 && i != j)
+      rule19_sums(x.x, x.y, x.z, vert9 + 9 * (size_t)j, tgt64[j], nj, kappa, ex, coincide);
+    else
+      panel_exact(x.x, x.y, x.z, vert9 + 9 * (size_t)j, i == j, kappa, ex);
     double vl = 0, kl = 0, vy = 0, ky = 0;
     for (int g = 0; g < K; ++g) {
       double4 y = src64[(size_t)K * j + g];
@@ -212,6 +368,8 @@ __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restr
     const double inv4pi = 0.25 / M_PI;
     if (ptag[i] == ptag[j])
       corr[k] = make_double4(ex[0] - vl * inv4pi, ex[1] - kl * inv4pi, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
+    else if (stern)  // the other surface of a Stern layer: the Laplace layers of the ion-free region
+      corr[k] = make_double4(ex[0] - vl * inv4pi, ex[1] - kl * inv4pi, 0.0, 0.0);
     else  // another body: its Laplace layers do not reach this target
       corr[k] = make_double4(0.0, 0.0, ex[2] - vy * inv4pi, ex[3] - ky * inv4pi);
   }
@@ -219,11 +377,38 @@ __global__ void near_corr_kernel(const int* __restrict__ ptr, const int* __restr
 
 }  // namespace
 
-void init_gauss_legendre() {
+namespace {
+
+// the 19-node rule, solved once per process (host only)
+struct R19Table {
+  double4 node[R19];
+  bool ok;
+  R19Table() {
+    // Dunavant's degree-9 table to 3 digits: centroid weight, the four a's, their orbit
+    // weights, b, c and the six-node orbit's weight
+    double x[12] = {0.0971, 0.490, 0.437, 0.188, 0.0447, 0.094, 0.233, 0.239, 0.0767, 0.0368, 0.222, 0.260};
+    const double f = solve_rule19(x);
+    rule19_nodes(x, node);
+    ok = f < 1e-13;
+    for (int g = 0; g < R19; ++g) ok = ok && node[g].w > 0 && node[g].x > 0 && node[g].y > 0 && node[g].z > 0;
+  }
+};
+
+const R19Table& rule19() {
+  static const R19Table tab;
+  return tab;
+}
+
+}  // namespace
+
+void init_near_rules() {
   double x[GL_N], w[GL_N];
   gauss_legendre(GL_N, x, w);
   BP_CUDA(cudaMemcpyToSymbol(c_gl_x, x, sizeof(x)));
   BP_CUDA(cudaMemcpyToSymbol(c_gl_w, w, sizeof(w)));
+  const R19Table& tab = rule19();
+  if (!tab.ok) fail(BEMPOL_ERR_NOT_CONVERGED, "the 19-node triangle rule did not converge");
+  BP_CUDA(cudaMemcpyToSymbol(c_r19, tab.node, sizeof(tab.node)));
 }
 
 void build_near(Ctx& c, cudaStream_t s) {
@@ -260,7 +445,8 @@ void build_near(Ctx& c, cudaStream_t s) {
   coincide.alloc(1);
   coincide.zero(s);
   launch(near_corr_kernel, cdiv(c.nnz, 128), 128, 0, s, c.near_ptr.p, c.near_col.p, n, (int)c.nnz, c.tgt64.p,
-         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.ptag.p, c.near_corr.p, coincide.p);
+         c.vert9.p, c.src64.p, c.nrm64.p, c.K, c.par.kappa, c.par.near_rule == BEMPOL_NEAR_GAUSS19 ? 1 : 0,
+         c.stern ? 1 : 0, c.ptag.p, c.near_corr.p, coincide.p);
   BP_CHECK_LAUNCH();
   c.nearT_ready = false;  // the table by columns is built on the first transposed product
   int bad = 0;
@@ -274,3 +460,20 @@ void build_near(Ctx& c, cudaStream_t s) {
 }
 
 }  // namespace bp
+
+extern "C" bempol_status bempol_near_rule19(double* nodes) {
+  if (!nodes) return BEMPOL_ERR_ARG;
+  try {
+    const bp::R19Table& tab = bp::rule19();
+    if (!tab.ok) return BEMPOL_ERR_NOT_CONVERGED;
+    for (int g = 0; g < bp::R19; ++g) {
+      nodes[4 * g] = tab.node[g].x;
+      nodes[4 * g + 1] = tab.node[g].y;
+      nodes[4 * g + 2] = tab.node[g].z;
+      nodes[4 * g + 3] = tab.node[g].w;
+    }
+    return BEMPOL_OK;
+  } catch (...) {
+    return BEMPOL_ERR_ARG;
+  }
+}

@@ -293,6 +293,21 @@ void strengths(Ctx& c, const double* x, bool fp32, cudaStream_t s) {
   BP_CHECK_LAUNCH();
 }
 
+int p2p_splits(Ctx& c, int max_range) { return choose_splits(c.ndblk, max_range, c.device); }
+
+void p2p_direct_ranges(Ctx& c, bool fp32, const int4* rng, double* part, int S, cudaStream_t s) {
+  dim3 grid(c.ndblk, S);
+  if (fp32) {
+    const float k = (float)c.par.kappa;
+    launch(p2p_f32_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, c.n, c.dblk.p, rng, c.blk_center.p, c.src64.p,
+           c.str32.p, k, (float)(-c.par.kappa * 1.4426950408889634), c.mv_active, c.grp_sys.p, part);
+  } else {
+    launch(p2p_f64_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, c.n, c.dblk.p, rng, c.src64.p, c.str64.p, c.par.kappa,
+           c.mv_active, c.grp_sys.p, part);
+  }
+  BP_CHECK_LAUNCH();
+}
+
 void p2p_direct(Ctx& c, bool fp32, cudaStream_t s) {
   const int n = c.n;
   int maxr = 0;
@@ -306,20 +321,11 @@ void p2p_direct(Ctx& c, bool fp32, cudaStream_t s) {
   const int S = choose_splits(c.ndblk, maxr, c.device);
   if (c.part.n < (size_t)S * 4 * n) c.part.alloc((size_t)S * 4 * n);
   c.part_splits = S;
-  dim3 grid(c.ndblk, S);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);
   c.stat_pairs += pairs;
-  if (fp32) {
-    const float k = (float)c.par.kappa;
-    launch(p2p_f32_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.dblk.p, c.dblk_rng.p, c.blk_center.p, c.src64.p,
-           c.str32.p, k, (float)(-c.par.kappa * 1.4426950408889634), c.mv_active, c.grp_sys.p, c.part.p);
-  } else {
-    launch(p2p_f64_kernel, grid, P2P_TPB, 0, s, c.tgt64.p, n, c.dblk.p, c.dblk_rng.p, c.src64.p, c.str64.p,
-           c.par.kappa, c.mv_active, c.grp_sys.p, c.part.p);
-  }
+  p2p_direct_ranges(c, fp32, c.dblk_rng.p, c.part.p, S, s);
   c.time_end(s, tm);
-  BP_CHECK_LAUNCH();
 }
 
 void combine(Ctx& c, const double* x, double* y, cudaStream_t s) {
@@ -330,12 +336,18 @@ void combine(Ctx& c, const double* x, double* y, cudaStream_t s) {
 
 void matvec_internal(Ctx& c, const double* x, double* y, int op, cudaStream_t s) {
   bool fp32 = (op == BEMPOL_OP_FP32_DIRECT || op == BEMPOL_OP_FP32_TREE);
+  const bool tree = op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE;
+  if (c.stern) {
+    if (tree || c.transposed) fail(BEMPOL_ERR_ARG, "a Stern-layer mesh takes the direct operator forms only");
+    strengths(c, x, fp32, s);
+    stern_matvec(c, x, y, fp32, s);
+    return;
+  }
   if (c.transposed) {
     matvec_T_internal(c, x, y, op, s);
     return;
   }
   strengths(c, x, fp32, s);
-  const bool tree = op == BEMPOL_OP_FP32_TREE || op == BEMPOL_OP_FP64_TREE;
   if (tree)
     tree_matvec_sums(c, fp32, s);
   else

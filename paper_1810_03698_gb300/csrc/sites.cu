@@ -536,7 +536,11 @@ void site_validation(Ctx& c, cudaStream_t s) {
     if (h[l] == 1)
       fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies within the near-singular radius of a panel");
     if (h[l] == 2) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies outside the surface");
-    if (h[l] == 3) fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies inside the surface of another body");
+    // with a Stern layer the sites lie inside both surfaces; otherwise inside their own only
+    if (h[l] == 3 && !c.stern)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies inside the surface of another body");
+    if (h[l] == 0 && c.stern)
+      fail(BEMPOL_ERR_SITES, "site " + std::to_string(l) + " lies outside the ion-exclusion surface");
   }
 }
 

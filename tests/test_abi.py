@@ -14,7 +14,7 @@ HEADER = os.path.join(ROOT, "include", "bempol.h")
 def _declared():
     src = open(HEADER).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(bempol_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(bempol_[a-z0-9_]+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
@@ -87,3 +87,33 @@ def test_ctypes_structures_match_the_header(tmp_path):
         assert int(got[cname]) == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_library_rule19_is_the_published_degree9_rule(libpath):
+    """bempol_near_rule19 (host only) solves the 19-node rule on its own; it must integrate
+    every monomial of degree <= 9 over the triangle exactly and equal the published 15-digit
+    table (tests/golden/dunavant19_degree9.json)."""
+    import json
+    from math import factorial
+
+    import numpy as np
+
+    import paper_1810_03698_gb300 as bp
+    r = bp.near_rule19()
+    lam, w = r[:, :3], r[:, 3]
+    assert np.all(w > 0) and np.all(lam > 0)
+    assert np.allclose(lam.sum(axis=1), 1.0, rtol=0, atol=1e-15)
+    for i in range(10):
+        for j in range(10 - i):
+            for k in range(10 - i - j):
+                got = np.sum(w * lam[:, 0] ** i * lam[:, 1] ** j * lam[:, 2] ** k)
+                ref = 2.0 * factorial(i) * factorial(j) * factorial(k) / factorial(i + j + k + 2)
+                assert abs(got / ref - 1.0) < 1e-13, (i, j, k)
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "dunavant19_degree9.json")))
+    assert abs(w[0] - gold["centroid_weight"]) < 1e-13
+    want = [np.sort([o["a"], o["a"], 1 - 2 * o["a"]]) for o in gold["orbits_aa"] for _ in range(3)]
+    o = gold["orbit_abc"]
+    want += [np.sort([o["b"], o["c"], 1 - o["b"] - o["c"]])] * 6
+    assert np.allclose(np.sort(lam[1:], axis=1), want, rtol=0, atol=1e-13)
+    ww = [orb["weight_per_node"] for orb in gold["orbits_aa"] for _ in range(3)] + [o["weight_per_node"]] * 6
+    assert np.allclose(w[1:], ww, rtol=0, atol=1e-13)
