@@ -69,25 +69,28 @@ FLOPS_PER_PAIR = 30
 PRODUCTS_PER_DG = 747
 # DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
 # its kernels from one ncu capture of the kernels as committed (set to None when they change).
-TRAFFIC_PER_PRODUCT_BYTES = 47.63e6
-TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels of one FP32 treecode "
-                 "product (leaf moments, 3 M2M levels, far Laplace and Yukawa, pair strengths, near field), "
-                 "cache flushed before each kernel; profiles/tree_product_dram_bumpy81920.md")
+# DRAM bytes of one FP32 treecode product from an ncu capture of the current kernels (None
+# until the capture is taken for them)
+TRAFFIC_PER_PRODUCT_BYTES = None
+TRAFFIC_BASIS = None
 
 
 def far_flops(P):
-    """FP32 flops (FMA = 2) of one (target, cell) Taylor evaluation of order P, counted from
-    the recurrences: per coefficient k with m1 = #{j: k_j >= 1}, m2 = #{j: k_j >= 2}
-    Laplace 2*m1 + m2 + 4 (+4 for the two moment dot products), Yukawa 4*m1 + 2*m2 + 10
-    (+4), plus 20 for Delta, |Delta|, 1/|Delta|^2, the exponential and the order-0 terms."""
-    tot = 20
-    for n in range(1, P + 1):
-        for a in range(n, -1, -1):
-            for b in range(n - a, -1, -1):
-                k = (a, b, n - a - b)
-                m1 = sum(1 for v in k if v >= 1)
-                m2 = sum(1 for v in k if v >= 2)
-                tot += (2 * m1 + m2 + 4 + 4) + (4 * m1 + 2 * m2 + 10 + 4)
+    """FP32 flops (FMA = 2) of one (target, cell) far evaluation of order P, both kernels
+    and both layers, counted from the kernel (`far_eval` in csrc/tree.cu): the three
+    one-dimensional factor tables (powers and constant multiples), per term of the
+    kernel-independent sums S_m the factor products and two FMAs (single and double
+    layer), then Delta and 1/|Delta|^2, the Laplace radial sequence (6 per order), the
+    Yukawa one (exponential set-up, then 8 per order) and the four accumulations."""
+    mons = [(a, b, n - a - b) for n in range(P + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
+    tot = 3 * ((P - 1) + sum(1 for k in range(1, P + 1) for _ in range(k // 2 + 1)))
+    for k0, k1, k2 in mons:
+        for _ in range(k0 // 2 + 1):
+            for _ in range(k1 // 2 + 1):
+                tot += 1 if (k0 > 0 and k1 > 0) else 0
+                for _ in range(k2 // 2 + 1):
+                    tot += 4 + (1 if (k2 > 0 and (k0 > 0 or k1 > 0)) else 0)
+    tot += 9 + (4 + 6 * P) + (13 + 8 * (P - 1)) + 8
     return tot
 
 
@@ -649,7 +652,7 @@ def main():
     pair_launch_ms = stats["pair_ms"] / max(1, stats["pair_launches"])
     pairs_per_launch = stats["pair_interactions"] / max(1, stats["pair_launches"])
     pair_tflops = pairs_per_launch * FLOPS_PER_PAIR / max(pair_launch_ms * 1e-3, 1e-12) / 1e12
-    kernels = {"pair": {"name": "near_kernel<float>" if "tree" in args.op else "p2p_f32_kernel",
+    kernels = {"pair": {"name": "near16_kernel" if "tree" in args.op else "p2p_f32_kernel",
                         "launches": stats["pair_launches"], "total_ms": stats["pair_ms"],
                         "avg_launch_ms": pair_launch_ms, "pairs_per_launch": pairs_per_launch,
                         "flops_per_pair": FLOPS_PER_PAIR, "achieved_tflops": pair_tflops,
@@ -659,7 +662,7 @@ def main():
         far_launch_ms = stats["far_ms"] / stats["far_launches"]
         evals_per_launch = stats["far_evaluations"] / stats["far_launches"]
         far_tflops = evals_per_launch * far_flops(P) / (far_launch_ms * 1e-3) / 1e12
-        kernels["far"] = {"name": f"far_kernel<{P},float> (Laplace + Yukawa)", "launches": stats["far_launches"],
+        kernels["far"] = {"name": f"far16_kernel<{P},float> (Laplace + Yukawa in one pass)", "launches": stats["far_launches"],
                           "total_ms": stats["far_ms"], "avg_launch_ms": far_launch_ms,
                           "evals_per_launch": evals_per_launch, "flops_per_eval": far_flops(P),
                           "achieved_tflops": far_tflops, "frac": far_tflops / fp32_peak}
@@ -671,7 +674,7 @@ def main():
         prod_ms = stats["tree_ms"] / stats["tree_products"]
         flops = (stats["pair_interactions"] * FLOPS_PER_PAIR
                  + stats["far_evaluations"] * far_flops(P)) / stats["tree_products"]
-        kernels["tree"] = {"name": f"FP32 tree product: near_kernel<float> || far_kernel<{P},float> x2",
+        kernels["tree"] = {"name": f"FP32 tree product: near16_kernel || far16_kernel<{P},float>",
                            "launches": stats["tree_products"], "total_ms": stats["tree_ms"],
                            "avg_launch_ms": prod_ms, "flops_per_launch": flops,
                            "achieved_tflops": flops / (prod_ms * 1e-3) / 1e12,

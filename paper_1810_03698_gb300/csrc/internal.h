@@ -121,6 +121,7 @@ struct Tree {
   // blk16 / blk16f; acceptance against each batch's own bounding sphere): far cells of
   // the Yukawa and Laplace kernels and near leaves, CSR by batch id
   DBuf<int> bfar_ptr, bfar_list, bfarL_ptr, bfarL_list, bnear_ptr, bnear_list;
+  DBuf<int> bfar_lap;  // per bfar_list entry: 1 if the cell is in the batch's own body (several bodies only)
   // host copies: the batches (leaf, first, count, id) in id order with their cost (near
   // pairs + far terms weighted by their flops), and the two launch orders
   std::vector<int4> h_batch, h_blk16, h_blk16f;

@@ -14,13 +14,17 @@
 // so  V = sum_k a_k M_k   with M_k = sum_s m_s h_s^k             (single layer),
 //     K = sum_k a_k D_k   with D_k = sum_s sum_j k_j d_sj h_s^(k - e_j)  (double layer:
 //         the moments of the dipole layer, since d . grad_y G = d . grad_h of the series).
-// Coefficients by recurrence in |k| = n, written for f(h) = e^{-kappa r}/r, r = |Delta - h|
-// (kappa = 0 gives Laplace).  From r^2 grad f = (Delta - h)(f + kappa e^{-kappa r}) and
-// grad e^{-kappa r} = kappa (Delta - h) f one gets, with b_k the coefficients of e^{-kappa r},
-//     n |Delta|^2 a_k = (2n - 1) sum_j Delta_j a_{k-e_j} - (n - 1) sum_j a_{k-2e_j}
-//                       + kappa sum_j (Delta_j b_{k-e_j} - b_{k-2e_j}),
-//     n b_k           = kappa sum_j (Delta_j a_{k-e_j} - a_{k-2e_j}),
-// a_0 = e^{-kappa|Delta|}/|Delta|, b_0 = e^{-kappa|Delta|} (terms with a negative index vanish).
+// Coefficients of a radial kernel G(r) = g(r^2/2) (Laplace 1/r; Yukawa e^{-kappa r}/r) in
+// closed form: since d/dx_i acts on g(s), s = |Delta|^2/2, through s alone, each factor
+// splits as a one-dimensional Hermite-type sum,
+//     a_k = sum_{j <= k/2} prod_i u(k_i, j_i; Delta_i) g_{|k| - |j|},
+//     u(k, j; x) = (-1)^k x^(k - 2j) / (2^j j! (k - 2j)!),   g_m = (1/r d/dr)^m G,
+// with the radial sequences  Laplace  g_m = -(2m - 1) g_{m-1} / r^2,  g_0 = 1/r;
+//                            Yukawa   g_0 = e^{-kappa r}/r,  g_1 = -(1 + kappa r) g_0 / r^2,
+//                                     g_{m+1} = (kappa^2 g_{m-1} - (2m + 1) g_m) / r^2.
+// Hence  V = sum_m g_m S_m(M),  K = sum_m g_m S_m(D),  S_m(M) = sum_{|k|-|j| = m} prod_i u M_k:
+// the polynomial sums S_m do not depend on the kernel, so one pass over a cell's moments
+// serves the Laplace and the Yukawa single and double layers together.
 // Moments of a parent follow from its children's by the exact shift
 //     M_k(c_p) = sum_{l <= k} prod_i C(k_i, l_i) (c_c - c_p)_i^(k_i - l_i) M_l(c_c)
 // (and the same for D_k).
@@ -51,113 +55,124 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- far field
-// One (target, cell) interaction of one kernel: the Laplace coefficients a_k, or the
-// Yukawa a_k with their companions b_k, each dotted with the cell's single-layer (M)
-// and double-layer (Dm) moments.  Fully unrolled for a compile-time order, so every
-// table index is a constant; the per-order factors (2n-1)/(n|Delta|^2),
-// (n-1)/(n|Delta|^2), kappa/(n|Delta|^2) and kappa/n are formed once per order.
-// The two kernels run as separate launches so each body stays small.
+// Constants of the one-dimensional factors: c[k][j] = (-1)^k / (2^j j! (k - 2j)!).
+template <int P>
+struct HermU {
+  double c[P + 1][P / 2 + 1];
+  constexpr HermU() : c{} {
+    for (int k = 0; k <= P; ++k)
+      for (int j = 0; 2 * j <= k; ++j) {
+        double d = 1.0;
+        for (int q = 0; q < j; ++q) d *= 2.0 * (q + 1);  // 2^j j!
+        for (int q = 2; q <= k - 2 * j; ++q) d *= q;     // (k - 2j)!
+        c[k][j] = ((k & 1) ? -1.0 : 1.0) / d;
+      }
+  }
+};
+
+// One (target, cell) interaction, both kernels and both layers: the kernel-independent
+// sums S_m of the cell's single-layer (M) and double-layer (Dm) moments, then the Laplace
+// and Yukawa radial sequences.  Fully unrolled for a compile-time order, so every table
+// index is a constant.  lw = 1 adds the Laplace terms (0: a cell of another body).
 template <int P, typename Real>
-__device__ __forceinline__ void far_eval_laplace(const Real D[3], const Real* __restrict__ M,
-                                                 const Real* __restrict__ Dm, Real& v, Real& k) {
+__device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict__ M, const Real* __restrict__ Dm,
+                                         Real kappa, Real kappa2, Real lw, Real& vl, Real& kl, Real& vy, Real& ky) {
   constexpr MI<P> mi{};
+  constexpr HermU<P> hu{};
   constexpr int NC = MI<P>::NC;
+  Real u[3][P + 1][P / 2 + 1];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Real pw[P + 1];
+    pw[0] = (Real)1;
+#pragma unroll
+    for (int e = 1; e <= P; ++e) pw[e] = pw[e - 1] * D[i];
+#pragma unroll
+    for (int k = 0; k <= P; ++k)
+#pragma unroll
+      for (int j = 0; j <= P / 2; ++j)  // fixed trip counts, so every index is a constant
+        if (2 * j <= k) u[i][k][j] = (Real)hu.c[k][j] * pw[k - 2 * j];
+  }
+  Real SM[P + 1], SD[P + 1];
+#pragma unroll
+  for (int m = 0; m <= P; ++m) SM[m] = SD[m] = (Real)0;
+#pragma unroll
+  for (int t = 0; t < NC; ++t) {
+    const int k0 = mi.k[t][0], k1 = mi.k[t][1], k2 = mi.k[t][2], n = mi.ord[t];
+    const Real mt = M[t], dt = Dm[t];
+#pragma unroll
+    for (int j0 = 0; j0 <= P / 2; ++j0)
+#pragma unroll
+      for (int j1 = 0; j1 <= P / 2; ++j1) {
+        if (2 * j0 > k0 || 2 * j1 > k1) continue;
+        const Real w01 = u[0][k0][j0] * u[1][k1][j1];
+#pragma unroll
+        for (int j2 = 0; j2 <= P / 2; ++j2) {
+          if (2 * j2 > k2) continue;
+          const Real w = w01 * u[2][k2][j2];
+          const int m = n - j0 - j1 - j2;
+          SM[m] += w * mt;
+          SD[m] += w * dt;
+        }
+      }
+  }
   const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
   const Real rinv = inv_sqrt(r2);
   const Real ir2 = rinv * rinv;
-  Real q1[P + 1], q2[P + 1];
+  // Laplace
+  Real g = rinv, sV = g * SM[0], sK = g * SD[0];
 #pragma unroll
-  for (int n = 1; n <= P; ++n) {
-    q1[n] = ir2 * (Real)((2.0 * n - 1.0) / n);
-    q2[n] = ir2 * (Real)((n - 1.0) / n);
+  for (int m = 1; m <= P; ++m) {
+    g *= (Real)(-(2.0 * m - 1.0)) * ir2;
+    sV += g * SM[m];
+    sK += g * SD[m];
   }
-  Real a[NC];
-  a[0] = rinv;
-  Real sV = a[0] * M[0], sK = a[0] * Dm[0];
+  vl += lw * sV;
+  kl += lw * sK;
+  // Yukawa
+  const Real kr = kappa * (r2 * rinv);
+  Real g0 = exp_neg(kr) * rinv;
+  Real yV = g0 * SM[0], yK = g0 * SD[0];
+  if constexpr (P >= 1) {
+    Real g1 = -((Real)1 + kr) * g0 * ir2;
+    yV += g1 * SM[1];
+    yK += g1 * SD[1];
 #pragma unroll
-  for (int t = 1; t < NC; ++t) {
-    const int n = mi.ord[t];
-    Real s1 = 0, s2 = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (mi.m1[t][j] >= 0) s1 += D[j] * a[mi.m1[t][j]];
-      if (mi.m2[t][j] >= 0) s2 += a[mi.m2[t][j]];
+    for (int m = 1; m < P; ++m) {
+      const Real g2 = (kappa2 * g0 - (Real)(2.0 * m + 1.0) * g1) * ir2;
+      yV += g2 * SM[m + 1];
+      yK += g2 * SD[m + 1];
+      g0 = g1;
+      g1 = g2;
     }
-    a[t] = q1[n] * s1 - q2[n] * s2;
-    sV += a[t] * M[t];
-    sK += a[t] * Dm[t];
   }
-  v += sV;
-  k += sK;
+  vy += yV;
+  ky += yK;
 }
+
+// Far field, one warp per block of <= 16 targets of one leaf.  Lane l serves target
+// (l & 15); the two half-warps take alternate cells of the batch's far list (half h the
+// cells h, h + 2, ... of every staged group) and their sums are added at the end.  Each
+// warp stages its own groups of FW cells' moments with cp.async, double-buffered, and
+// waits only for its own copies (no block-wide barrier: a warp never waits for another).
+// lap (NULL: every cell) marks the far-list entries whose cell lies in the target's own
+// body, the only ones with Laplace terms.
+constexpr int FW = 8;  // cells per staged group (four per half-warp)
 
 template <int P, typename Real>
-__device__ __forceinline__ void far_eval_yukawa(const Real D[3], const Real* __restrict__ M,
-                                                const Real* __restrict__ Dm, Real kappa, Real& v, Real& k) {
-  constexpr MI<P> mi{};
-  constexpr int NC = MI<P>::NC;
-  const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
-  const Real rinv = inv_sqrt(r2);
-  const Real ir2 = rinv * rinv;
-  Real q1[P + 1], q2[P + 1], q3[P + 1], kn[P + 1];
-#pragma unroll
-  for (int n = 1; n <= P; ++n) {
-    q1[n] = ir2 * (Real)((2.0 * n - 1.0) / n);
-    q2[n] = ir2 * (Real)((n - 1.0) / n);
-    kn[n] = kappa * (Real)(1.0 / n);
-    q3[n] = kn[n] * ir2;
-  }
-  const Real e = exp_neg(kappa * (r2 * rinv));
-  Real A[NC], Bc[NC];
-  A[0] = e * rinv;
-  Bc[0] = e;
-  Real sV = A[0] * M[0], sK = A[0] * Dm[0];
-#pragma unroll
-  for (int t = 1; t < NC; ++t) {
-    const int n = mi.ord[t];
-    Real s1a = 0, s2a = 0, s1b = 0, s2b = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (mi.m1[t][j] >= 0) {
-        s1a += D[j] * A[mi.m1[t][j]];
-        s1b += D[j] * Bc[mi.m1[t][j]];
-      }
-      if (mi.m2[t][j] >= 0) {
-        s2a += A[mi.m2[t][j]];
-        s2b += Bc[mi.m2[t][j]];
-      }
-    }
-    Bc[t] = kn[n] * (s1a - s2a);
-    A[t] = q1[n] * s1a - q2[n] * s2a + q3[n] * (s1b - s2b);
-    sV += A[t] * M[t];
-    sK += A[t] * Dm[t];
-  }
-  v += sV;
-  k += sK;
-}
-
-
-// FP32 far field, one warp per block of <= 16 targets of one leaf.  Lane l serves target
-// (l & 15); the two half-warps take alternate cells of the leaf's far list (half h the
-// cells h, h + 2, ... of every batch) and their sums are added at the end.  Each warp
-// stages its own batches of FW cells' moments with cp.async, double-buffered, and waits
-// only for its own copies (no block-wide barrier: a warp never waits for another).
-constexpr int FW = 8;  // cells per staged batch (four per half-warp)
-
-template <int P, typename Real, int YUK>
 __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                    const int* __restrict__ leaf_cell,
                                                    const double4* __restrict__ center,
                                                    const int* __restrict__ far_ptr, const int* __restrict__ far_list,
-                                                   const Real* __restrict__ mom, Real kappa, int n,
-                                                   const int* __restrict__ active, const int* __restrict__ leaf_sys,
-                                                   double* __restrict__ out) {
+                                                   const int* __restrict__ lap, const Real* __restrict__ mom,
+                                                   Real kappa, int n, const int* __restrict__ active,
+                                                   const int* __restrict__ leaf_sys, double* __restrict__ out) {
   constexpr int NC = MI<P>::NC;
   // cp.async when a cell's moments are a whole number of 16-byte pieces (FP32: every order but 4)
   constexpr bool ASYNC = (2 * NC * sizeof(Real)) % 16 == 0;
   constexpr int CH = (int)(2 * NC * sizeof(Real) / 16);  // 16-byte pieces per cell
   __shared__ __align__(16) Real sm[2][FW][2 * NC];
-  __shared__ Real so[2][FW][3];
+  __shared__ Real so[2][FW][4];
   const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
   const int4 B = blk[blockIdx.x];
   const int leaf = B.x;
@@ -172,7 +187,8 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
     xr[1] = (Real)(x.y - ct.y);
     xr[2] = (Real)(x.z - ct.z);
   }
-  double aV = 0, aK = 0;
+  const Real kappa2 = kappa * kappa;
+  double aVL = 0, aKL = 0, aVY = 0, aKY = 0;
   const int f0 = far_ptr[B.w], f1 = far_ptr[B.w + 1];  // the batch's own far list
   auto stage = [&](int b, int fb) {
     const int cnt = min(FW, f1 - fb);
@@ -192,31 +208,35 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
       so[b][lane][0] = (Real)(ct.x - cc.x);
       so[b][lane][1] = (Real)(ct.y - cc.y);
       so[b][lane][2] = (Real)(ct.z - cc.z);
+      so[b][lane][3] = lap ? (Real)lap[fb + lane] : (Real)1;
     }
   };
   if (f0 < f1) stage(0, f0);
   int b = 0;
   for (int fb = f0; fb < f1; fb += FW, b ^= 1) {
     const int cnt = min(FW, f1 - fb);
-    if constexpr (ASYNC) cp_async_wait_all();  // this lane's pieces of batch b
-    __syncwarp();  // every lane's pieces and offsets of batch b; all done with the other buffer
+    if constexpr (ASYNC) cp_async_wait_all();  // this lane's pieces of group b
+    __syncwarp();  // every lane's pieces and offsets of group b; all done with the other buffer
     if (fb + FW < f1) stage(b ^ 1, fb + FW);
-    Real v = 0, k = 0;
+    Real vl = 0, kl = 0, vy = 0, ky = 0;
     for (int q = h; q < cnt; q += 2) {
       const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
-      if (YUK)
-        far_eval_yukawa<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, v, k);
-      else
-        far_eval_laplace<P, Real>(D, sm[b][q], sm[b][q] + NC, v, k);
+      far_eval<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, kappa2, so[b][q][3], vl, kl, vy, ky);
     }
-    aV += (double)v;
-    aK += (double)k;
+    aVL += (double)vl;
+    aKL += (double)kl;
+    aVY += (double)vy;
+    aKY += (double)ky;
   }
-  aV += __shfl_down_sync(0xffffffffu, aV, 16);
-  aK += __shfl_down_sync(0xffffffffu, aK, 16);
+  aVL += __shfl_down_sync(0xffffffffu, aVL, 16);
+  aKL += __shfl_down_sync(0xffffffffu, aKL, 16);
+  aVY += __shfl_down_sync(0xffffffffu, aVY, 16);
+  aKY += __shfl_down_sync(0xffffffffu, aKY, 16);
   if (h == 0 && act) {
-    out[(2 * YUK) * (size_t)n + i] = aV;
-    out[(2 * YUK + 1) * (size_t)n + i] = aK;
+    out[i] = aVL;
+    out[(size_t)n + i] = aKL;
+    out[2 * (size_t)n + i] = aVY;
+    out[3 * (size_t)n + i] = aKY;
   }
 }
 
@@ -845,8 +865,8 @@ void build_lists(Ctx& c, cudaStream_t s) {
     for (size_t b = 0; b < blk16.size(); ++b) {
       T.h_batch_pairs[b] = bnear[b] * c.K * blk16[b].z;
       T.h_batch_far[b] = bfar[b] * blk16[b].z;
-      // a far term costs about 68 pair terms (2,040 against 30 flops at order 5)
-      T.h_batch_cost[b] = (double)T.h_batch_pairs[b] + 68.0 * (double)T.h_batch_far[b];
+      // a far term costs about 28 pair terms (826 against 30 flops at order 5)
+      T.h_batch_cost[b] = (double)T.h_batch_pairs[b] + 28.0 * (double)T.h_batch_far[b];
     }
     std::vector<int4> bf = blk16;
     // largest blocks first: the grids are a few waves deep, so launching the long blocks
@@ -866,6 +886,14 @@ void build_lists(Ctx& c, cudaStream_t s) {
     if (!T.bfarL_same) {
       upload(T.bfarL_ptr, BL.lptr, s);
       upload(T.bfarL_list, BL.ll, s);
+      // Laplace flag of every far-list entry: the cell lies in the batch's own body
+      std::vector<int> lapf(BL.fl.size());
+      for (size_t bb = 0; bb < blk16.size(); ++bb) {
+        const int gb = T.h_cell_grp[T.h_leaf_cell[blk16[bb].x]];
+        const int w = blk16[bb].w;
+        for (int e = BL.fptr[w]; e < BL.fptr[w + 1]; ++e) lapf[e] = T.h_cell_grp[BL.fl[e]] == gb ? 1 : 0;
+      }
+      upload(T.bfar_lap, lapf, s);
     }
     upload(T.bnear_ptr, BL.nptr, s);
     upload(T.bnear_list, BL.nl, s);
@@ -977,12 +1005,9 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     c.stat_far += sh ? c.sh_far : T.bfar_per_matvec;
   }
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
-  const int* lp = T.bfarL_same ? T.bfar_ptr.p : T.bfarL_ptr.p;
-  const int* ll = T.bfarL_same ? T.bfar_list.p : T.bfarL_list.p;
-  launch(far16_kernel<P, Real, 0>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, lp, ll, mom.p,
-         kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(far16_kernel<P, Real, 1>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, T.bfar_ptr.p,
-         T.bfar_list.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
+  launch(far16_kernel<P, Real>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, T.bfar_ptr.p,
+         T.bfar_list.p, T.bfarL_same ? nullptr : T.bfar_lap.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p,
+         far_out);
   if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
   if (!F64) {
