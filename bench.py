@@ -69,28 +69,26 @@ FLOPS_PER_PAIR = 30
 PRODUCTS_PER_DG = 747
 # DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
 # its kernels from one ncu capture of the kernels as committed (set to None when they change).
-# DRAM bytes of one FP32 treecode product from an ncu capture of the current kernels (None
-# until the capture is taken for them)
-TRAFFIC_PER_PRODUCT_BYTES = None
-TRAFFIC_BASIS = None
+TRAFFIC_PER_PRODUCT_BYTES = 42.57e6
+TRAFFIC_BASIS = ("ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kernels of one FP32 treecode "
+                 "product (leaf moments, 3 M2M levels, far-field coefficients, far field, pair strengths, near "
+                 "field), cache flushed before each kernel, mean of two products; "
+                 "profiles/tree_product_dram_bumpy81920.md")
 
 
 def far_flops(P):
     """FP32 flops (FMA = 2) of one (target, cell) far evaluation of order P, both kernels
-    and both layers, counted from the kernel (`far_eval` in csrc/tree.cu): the three
-    one-dimensional factor tables (powers and constant multiples), per term of the
-    kernel-independent sums S_m the factor products and two FMAs (single and double
-    layer), then Delta and 1/|Delta|^2, the Laplace radial sequence (6 per order), the
-    Yukawa one (exponential set-up, then 8 per order) and the four accumulations."""
-    mons = [(a, b, n - a - b) for n in range(P + 1) for a in range(n, -1, -1) for b in range(n - a, -1, -1)]
-    tot = 3 * ((P - 1) + sum(1 for k in range(1, P + 1) for _ in range(k // 2 + 1)))
-    for k0, k1, k2 in mons:
-        for _ in range(k0 // 2 + 1):
-            for _ in range(k1 // 2 + 1):
-                tot += 1 if (k0 > 0 and k1 > 0) else 0
-                for _ in range(k2 // 2 + 1):
-                    tot += 4 + (1 if (k2 > 0 and (k0 > 0 or k1 > 0)) else 0)
-    tot += 9 + (4 + 6 * P) + (13 + 8 * (P - 1)) + 8
+    and both layers, counted from the kernel (`far_eval` in csrc/tree.cu): Delta (3), the
+    power tables of Delta_y and Delta_z and the running power of Delta_x, one product per
+    monomial Delta^e beyond those (products with a factor 1 are folded away), two FMAs per
+    coefficient B[m, e] (single and double layer), then |Delta|^2 and 1/|Delta|^2, the
+    Laplace radial sequence (6 per order), the Yukawa one (set-up, then 8 per order) and
+    the four accumulations.  The rsqrt and the exponential are counted apart (MUFU)."""
+    nb = sum((d + 1) * (d + 2) // 2 * ((P - d) // 2 + 1) for d in range(P + 1))
+    mono = sum(1 for a in range(P + 1) for b in range(P + 1 - a) for c in range(1, P + 1 - a - b) if a + b >= 1)
+    tot = 3 + 2 * max(P - 1, 0) + max(P - 1, 0) + P * (P - 1) // 2 + mono + 4 * nb
+    tot += 5 + 1 + (2 + 6 * P) + 4                      # |Delta|^2, 1/|Delta|^2, Laplace, accumulate
+    tot += 2 + 1 + 1 + 2 + 3 + 4 + 8 * max(P - 1, 0) + 2  # Yukawa
     return tot
 
 

@@ -103,12 +103,12 @@ struct Tree {
   DBuf<int> leaf_sys;                                    // leaf number -> system
   // group of each cell (-1 for the root when it holds several groups)
   std::vector<int> h_cell_grp;
-  // interaction lists per leaf (CSR): accepted far cells of the Yukawa kernel (every
-  // body of the leaf's system) and of the Laplace kernel (the leaf's own body), and
-  // near (direct) leaves; a near entry with bit 30 set is a leaf of another body
-  // (Yukawa terms only)
-  DBuf<int> far_ptr, far_list, farL_ptr, farL_list, near_ptr, near_list;
-  bool farL_same = true;  // one group: the Laplace lists are the Yukawa lists
+  // interaction lists per leaf (CSR): accepted far cells (every body of the leaf's
+  // system; far_lap flags those of the leaf's own body, the only ones with Laplace
+  // terms) and near (direct) leaves; a near entry with bit 30 set is a leaf of another
+  // body (Yukawa terms only)
+  DBuf<int> far_ptr, far_list, near_ptr, near_list;
+  bool farL_same = true;  // one group: every far cell carries Laplace terms
   // target blocks: (leaf number, first panel, count <= 128) for the far field,
   // (leaf number, first panel, count <= 32) for the FP64 near field and the transposed
   // kernels, and (leaf number, first panel, count <= 16) for the FP32 near field;
@@ -118,10 +118,11 @@ struct Tree {
   DBuf<int4> blk, blk32, blk16;
   DBuf<int4> blk16f;  // the 16-target blocks in the order of the forward far field (most far work first)
   // interaction lists of the 16-target batches of the forward product (batch id = .w of
-  // blk16 / blk16f; acceptance against each batch's own bounding sphere): far cells of
-  // the Yukawa and Laplace kernels and near leaves, CSR by batch id
-  DBuf<int> bfar_ptr, bfar_list, bfarL_ptr, bfarL_list, bnear_ptr, bnear_list;
+  // blk16 / blk16f; acceptance against each batch's own bounding sphere): far cells
+  // (bfar_lap flags those with Laplace terms) and near leaves, CSR by batch id
+  DBuf<int> bfar_ptr, bfar_list, bnear_ptr, bnear_list;
   DBuf<int> bfar_lap;  // per bfar_list entry: 1 if the cell is in the batch's own body (several bodies only)
+  DBuf<int> far_lap;   // per far_list entry: 1 if the cell is in the leaf's own body (several bodies only)
   // host copies: the batches (leaf, first, count, id) in id order with their cost (near
   // pairs + far terms weighted by their flops), and the two launch orders
   std::vector<int4> h_batch, h_blk16, h_blk16f;
@@ -134,6 +135,18 @@ struct Tree {
   DBuf<float> mom32;
   DBuf<double> mom64;
   int mom_order = -1;
+  // far-field coefficients of the cells, [ncell][NB][2] pairs (single, double layer),
+  // formed from the moments in every product, and the table of their terms (entry ->
+  // moment index and constant, CSR) for the product's order; the same for the
+  // transposed product (pairs: Laplace, Yukawa charges)
+  struct BTab {
+    int order = -1;
+    DBuf<int> ptr, k;
+    DBuf<double> c;
+  };
+  DBuf<float> bco32, bcoT32;
+  DBuf<double> bco64, bcoT64;
+  BTab btab, btabT;
   // FP32 Gauss-node positions relative to the centre of their own leaf (x, y, z, 0),
   // and the same for the collocation points
   DBuf<float4> src_rel32, cen_rel32;

@@ -23,8 +23,14 @@
 //                            Yukawa   g_0 = e^{-kappa r}/r,  g_1 = -(1 + kappa r) g_0 / r^2,
 //                                     g_{m+1} = (kappa^2 g_{m-1} - (2m + 1) g_m) / r^2.
 // Hence  V = sum_m g_m S_m(M),  K = sum_m g_m S_m(D),  S_m(M) = sum_{|k|-|j| = m} prod_i u M_k:
-// the polynomial sums S_m do not depend on the kernel, so one pass over a cell's moments
-// serves the Laplace and the Yukawa single and double layers together.
+// the polynomial sums S_m do not depend on the kernel, so one pass over a cell's data
+// serves the Laplace and the Yukawa single and double layers together.  Writing
+// e = k - 2j, S_m is a polynomial in Delta with coefficients fixed per cell,
+//     S_m(M) = sum_{|e| <= m, 2m - |e| <= P} Delta^e B_{m,e}(M),
+//     B_{m,e}(M) = sum_{|j| = m - |e|, |e + 2j| <= P} prod_i c(e_i + 2j_i, j_i) M_{e + 2j},
+// c(k, j) = (-1)^k / (2^j j! (k - 2j)!), so each product forms the B of every cell once
+// from its moments and a (target, cell) term costs one product per monomial Delta^e and
+// two FMAs per coefficient (80 coefficients per layer at P = 5).
 // Moments of a parent follow from its children's by the exact shift
 //     M_k(c_p) = sum_{l <= k} prod_i C(k_i, l_i) (c_c - c_p)_i^(k_i - l_i) M_l(c_c)
 // (and the same for D_k).
@@ -46,75 +52,50 @@ namespace bp {
 
 namespace {
 
-// asynchronous global -> shared copies of 16 bytes (both addresses 16-byte aligned)
-__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // ---------------------------------------------------------------- far field
-// Constants of the one-dimensional factors: c[k][j] = (-1)^k / (2^j j! (k - 2j)!).
-template <int P>
-struct HermU {
-  double c[P + 1][P / 2 + 1];
-  constexpr HermU() : c{} {
-    for (int k = 0; k <= P; ++k)
-      for (int j = 0; 2 * j <= k; ++j) {
-        double d = 1.0;
-        for (int q = 0; q < j; ++q) d *= 2.0 * (q + 1);  // 2^j j!
-        for (int q = 2; q <= k - 2 * j; ++q) d *= q;     // (k - 2j)!
-        c[k][j] = ((k & 1) ? -1.0 : 1.0) / d;
-      }
-  }
-};
-
 // One (target, cell) interaction, both kernels and both layers: the kernel-independent
-// sums S_m of the cell's single-layer (M) and double-layer (Dm) moments, then the Laplace
-// and Yukawa radial sequences.  Fully unrolled for a compile-time order, so every table
-// index is a constant.  lw = 1 adds the Laplace terms (0: a cell of another body).
+// sums S_m = sum_e Delta^e B[m, e] of the cell's coefficients (B interleaved as
+// (single layer, double layer) pairs), then the Laplace and Yukawa radial sequences.
+// Fully unrolled for a compile-time order, so every table index is a constant.  lw = 1
+// adds the Laplace terms (0: a cell of another body).
 template <int P, typename Real>
-__device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict__ M, const Real* __restrict__ Dm,
-                                         Real kappa, Real kappa2, Real lw, Real& vl, Real& kl, Real& vy, Real& ky) {
-  constexpr MI<P> mi{};
-  constexpr HermU<P> hu{};
-  constexpr int NC = MI<P>::NC;
-  Real u[3][P + 1][P / 2 + 1];
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    Real pw[P + 1];
-    pw[0] = (Real)1;
-#pragma unroll
-    for (int e = 1; e <= P; ++e) pw[e] = pw[e - 1] * D[i];
-#pragma unroll
-    for (int k = 0; k <= P; ++k)
-#pragma unroll
-      for (int j = 0; j <= P / 2; ++j)  // fixed trip counts, so every index is a constant
-        if (2 * j <= k) u[i][k][j] = (Real)hu.c[k][j] * pw[k - 2 * j];
-  }
-  Real SM[P + 1], SD[P + 1];
+__device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict__ Bc, Real kappa, Real kappa2,
+                                         Real lw, Real& vl, Real& kl, Real& vy, Real& ky) {
+  constexpr BIdx<P> bi{};
+  Real SM[P + 1], SD[P + 1], py[P + 1], pz[P + 1];
 #pragma unroll
   for (int m = 0; m <= P; ++m) SM[m] = SD[m] = (Real)0;
+  py[0] = pz[0] = (Real)1;
 #pragma unroll
-  for (int t = 0; t < NC; ++t) {
-    const int k0 = mi.k[t][0], k1 = mi.k[t][1], k2 = mi.k[t][2], n = mi.ord[t];
-    const Real mt = M[t], dt = Dm[t];
+  for (int e = 1; e <= P; ++e) {
+    py[e] = py[e - 1] * D[1];
+    pz[e] = pz[e - 1] * D[2];
+  }
+  Real px = (Real)1;
 #pragma unroll
-    for (int j0 = 0; j0 <= P / 2; ++j0)
+  for (int a = 0; a <= P; ++a) {
 #pragma unroll
-      for (int j1 = 0; j1 <= P / 2; ++j1) {
-        if (2 * j0 > k0 || 2 * j1 > k1) continue;
-        const Real w01 = u[0][k0][j0] * u[1][k1][j1];
+    for (int b = 0; b <= P; ++b) {  // fixed trip counts, so every index is a constant
+      if (a + b > P) continue;
+      const Real pab = px * py[b];
 #pragma unroll
-        for (int j2 = 0; j2 <= P / 2; ++j2) {
-          if (2 * j2 > k2) continue;
-          const Real w = w01 * u[2][k2][j2];
-          const int m = n - j0 - j1 - j2;
-          SM[m] += w * mt;
-          SD[m] += w * dt;
+      for (int c = 0; c <= P; ++c) {
+        if (a + b + c > P) continue;
+        const Real w = pab * pz[c];
+        const int d = a + b + c, t0 = bi.t[a][b][c];
+#pragma unroll
+        for (int m = 0; m <= P; ++m) {
+          if (m < d || 2 * m - d > P) continue;
+          const int t = t0 + (m - d);
+          Real bm, bd;
+          ld_entry<Real, (2 * nb_of(P) * sizeof(Real)) % 16 == 0>(Bc, t, bm, bd);
+          SM[m] = fma(w, bm, SM[m]);
+          SD[m] = fma(w, bd, SD[m]);
         }
       }
+    }
+    px *= D[0];
   }
   const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
   const Real rinv = inv_sqrt(r2);
@@ -153,25 +134,24 @@ __device__ __forceinline__ void far_eval(const Real D[3], const Real* __restrict
 // Far field, one warp per block of <= 16 targets of one leaf.  Lane l serves target
 // (l & 15); the two half-warps take alternate cells of the batch's far list (half h the
 // cells h, h + 2, ... of every staged group) and their sums are added at the end.  Each
-// warp stages its own groups of FW cells' moments with cp.async, double-buffered, and
-// waits only for its own copies (no block-wide barrier: a warp never waits for another).
+// warp stages its own groups of cells' coefficients (2 NB values per cell) with
+// cp.async, double-buffered, and waits only for its own copies (no block-wide barrier:
+// a warp never waits for another).  The group size keeps the two buffers near 8 KB.
 // lap (NULL: every cell) marks the far-list entries whose cell lies in the target's own
 // body, the only ones with Laplace terms.
-constexpr int FW = 8;  // cells per staged group (four per half-warp)
-
 template <int P, typename Real>
 __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                    const int* __restrict__ leaf_cell,
                                                    const double4* __restrict__ center,
                                                    const int* __restrict__ far_ptr, const int* __restrict__ far_list,
-                                                   const int* __restrict__ lap, const Real* __restrict__ mom,
+                                                   const int* __restrict__ lap, const Real* __restrict__ bco,
                                                    Real kappa, int n, const int* __restrict__ active,
                                                    const int* __restrict__ leaf_sys, double* __restrict__ out) {
-  constexpr int NC = MI<P>::NC;
-  // cp.async when a cell's moments are a whole number of 16-byte pieces (FP32: every order but 4)
-  constexpr bool ASYNC = (2 * NC * sizeof(Real)) % 16 == 0;
-  constexpr int CH = (int)(2 * NC * sizeof(Real) / 16);  // 16-byte pieces per cell
-  __shared__ __align__(16) Real sm[2][FW][2 * NC];
+  constexpr int NB = FarShape<P, Real>::NB, FW = FarShape<P, Real>::FW;
+  // cp.async when a cell's coefficients are a whole number of 16-byte pieces
+  constexpr bool ASYNC = (2 * NB * sizeof(Real)) % 16 == 0;
+  constexpr int CH = (int)(2 * NB * sizeof(Real) / 16);  // 16-byte pieces per cell
+  __shared__ __align__(16) Real sm[2][FW][2 * NB];
   __shared__ Real so[2][FW][4];
   const int lane = threadIdx.x, h = lane >> 4, tl = lane & 15;
   const int4 B = blk[blockIdx.x];
@@ -195,13 +175,13 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
     if constexpr (ASYNC) {
       for (int q = lane; q < cnt * CH; q += 32) {
         const int cell = q / CH, piece = q - cell * CH;
-        const char* g = reinterpret_cast<const char*>(mom + (size_t)far_list[fb + cell] * 2 * NC) + 16 * piece;
+        const char* g = reinterpret_cast<const char*>(bco + (size_t)far_list[fb + cell] * 2 * NB) + 16 * piece;
         cp_async16(reinterpret_cast<char*>(&sm[b][cell][0]) + 16 * piece, g);
       }
       cp_async_commit();
     } else {
-      for (int q = lane; q < cnt * 2 * NC; q += 32)
-        sm[b][q / (2 * NC)][q % (2 * NC)] = mom[(size_t)far_list[fb + q / (2 * NC)] * 2 * NC + q % (2 * NC)];
+      for (int q = lane; q < cnt * 2 * NB; q += 32)
+        sm[b][q / (2 * NB)][q % (2 * NB)] = bco[(size_t)far_list[fb + q / (2 * NB)] * 2 * NB + q % (2 * NB)];
     }
     if (lane < cnt) {
       const double4 cc = center[far_list[fb + lane]];
@@ -221,7 +201,7 @@ __global__ void __launch_bounds__(32) far16_kernel(const int4* __restrict__ blk,
     Real vl = 0, kl = 0, vy = 0, ky = 0;
     for (int q = h; q < cnt; q += 2) {
       const Real D[3] = {xr[0] + so[b][q][0], xr[1] + so[b][q][1], xr[2] + so[b][q][2]};
-      far_eval<P, Real>(D, sm[b][q], sm[b][q] + NC, kappa, kappa2, so[b][q][3], vl, kl, vy, ky);
+      far_eval<P, Real>(D, sm[b][q], kappa, kappa2, so[b][q][3], vl, kl, vy, ky);
     }
     aVL += (double)vl;
     aKL += (double)kl;
@@ -286,6 +266,8 @@ __device__ __forceinline__ void pair_accum(const double x[3], double4 p, double4
 // (leaf, first, count, batch) takes the near list of its batch, cut into gridDim.y
 // consecutive pieces; piece s writes its partial sums to out + s * 4n (the combine
 // kernel adds the pieces in order).
+// Registers are bounded for 24 resident one-warp blocks per SM (80 per thread, six warps
+// per scheduler), which hides more of the pair formula's dependent latencies.
 constexpr int CP = 64;             // source pairs per staged chunk
 constexpr float FAR_PAD = 1.0e4f;  // leaf-relative position of a padding node (zero strength)
 constexpr int MBAR_SPIN = 1 << 20; // polls of an mbarrier before a wait is declared failed
@@ -385,7 +367,7 @@ __device__ __forceinline__ void chunk_x2(f2 X, f2 Y, f2 Z, const NearChunk& T, i
   }
 }
 
-__global__ void __launch_bounds__(32) near16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
+__global__ void __launch_bounds__(32, 24) near16_kernel(const int4* __restrict__ blk, const double4* __restrict__ tgt64,
                                                     const int* __restrict__ leaf_cell,
                                                     const double4* __restrict__ center,
                                                     const int* __restrict__ near_ptr,
@@ -659,11 +641,6 @@ void build_topology(Ctx& c) {
   T.nleaf = (int)T.h_leaf_cell.size();
 }
 
-template <typename V>
-void upload(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
-  d.alloc(std::max<size_t>(1, h.size()));
-  if (!h.empty()) BP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s));
-}
 
 // Interaction lists of the forward product's target batches (the 16-target blocks of
 // the FP32 and FP64 near and far kernels): batch b holds the targets [first, first +
@@ -865,8 +842,8 @@ void build_lists(Ctx& c, cudaStream_t s) {
     for (size_t b = 0; b < blk16.size(); ++b) {
       T.h_batch_pairs[b] = bnear[b] * c.K * blk16[b].z;
       T.h_batch_far[b] = bfar[b] * blk16[b].z;
-      // a far term costs about 28 pair terms (826 against 30 flops at order 5)
-      T.h_batch_cost[b] = (double)T.h_batch_pairs[b] + 28.0 * (double)T.h_batch_far[b];
+      // a far term costs about 16 pair terms (464 against 30 flops at order 5)
+      T.h_batch_cost[b] = (double)T.h_batch_pairs[b] + 16.0 * (double)T.h_batch_far[b];
     }
     std::vector<int4> bf = blk16;
     // largest blocks first: the grids are a few waves deep, so launching the long blocks
@@ -884,8 +861,6 @@ void build_lists(Ctx& c, cudaStream_t s) {
     upload(T.bfar_list, BL.fl, s);
     T.bfarL_same = BL.ll.size() == BL.fl.size();
     if (!T.bfarL_same) {
-      upload(T.bfarL_ptr, BL.lptr, s);
-      upload(T.bfarL_list, BL.ll, s);
       // Laplace flag of every far-list entry: the cell lies in the batch's own body
       std::vector<int> lapf(BL.fl.size());
       for (size_t bb = 0; bb < blk16.size(); ++bb) {
@@ -941,9 +916,13 @@ void build_lists(Ctx& c, cudaStream_t s) {
   upload(T.far_ptr, fptr, s);
   upload(T.far_list, flist, s);
   T.farL_same = llist.size() == flist.size();
-  if (!T.farL_same) {
-    upload(T.farL_ptr, lptr, s);
-    upload(T.farL_list, llist, s);
+  if (!T.farL_same) {  // Laplace flag of every far-list entry: the cell lies in the leaf's own body
+    std::vector<int> lapf(flist.size());
+    for (int l = 0; l < T.nleaf; ++l) {
+      const int gl = T.h_cell_grp[T.h_leaf_cell[l]];
+      for (int e = fptr[l]; e < fptr[l + 1]; ++e) lapf[e] = T.h_cell_grp[flist[e]] == gl ? 1 : 0;
+    }
+    upload(T.far_lap, lapf, s);
   }
   upload(T.near_ptr, nptr, s);
   upload(T.near_list, nlist, s);
@@ -958,11 +937,18 @@ template <int P, typename Real>
 void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   Tree& T = c.tree;
   constexpr bool F64 = sizeof(Real) == 8;
-  constexpr int NC = MI<P>::NC;
+  constexpr int NC = MI<P>::NC, NB = nb_of(P);
   if (T.mom_order != P || mom.n < (size_t)T.ncell * 2 * NC) {
     mom.alloc((size_t)T.ncell * 2 * NC);
     T.mom_order = P;
   }
+  DBuf<Real>* bco;
+  if constexpr (F64)
+    bco = &T.bco64;
+  else
+    bco = &T.bco32;
+  if (bco->n < (size_t)T.ncell * 2 * NB) bco->alloc((size_t)T.ncell * 2 * NB);
+  build_btab<P>(T.btab, s);
   typedef typename Vec4<Real>::T R4;
   const R4* str = nullptr;
   if (sizeof(Real) == 4)
@@ -999,14 +985,29 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
     const int first = T.h_depth_begin[d], cnt = T.h_depth_begin[d + 1] - first;
     launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, mom.p);
   }
+  {  // far-field coefficients of the cells that far lists can hold
+    const int cb = T.h_depth_begin[T.bm2m_min_depth];
+    if (cb < T.ncell)
+      launch(bcoef_kernel<P, Real>, cdiv((long long)(T.ncell - cb) * NB, 256), 256, 0, sf, cb, T.ncell,
+             T.btab.ptr.p, T.btab.k.p, T.btab.c.p, mom.p, mom.p + NC, bco->p);
+  }
   Ctx::Timed tf;
   if (!F64) {
     c.time_begin(1, sf, tf);
     c.stat_far += sh ? c.sh_far : T.bfar_per_matvec;
   }
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
+  {  // one-warp blocks: the largest shared-memory carveout, so that shared memory does not
+     // cap the resident blocks below the register limit (once per device and instantiation)
+    static bool carve[64] = {};
+    if (c.device >= 0 && c.device < 64 && !carve[c.device]) {
+      BP_CUDA(cudaFuncSetAttribute(far16_kernel<P, Real>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
+      carve[c.device] = true;
+    }
+  }
   launch(far16_kernel<P, Real>, nb16f, 32, 0, sf, b16f, c.tgt64.p, T.leaf_cell.p, T.center.p, T.bfar_ptr.p,
-         T.bfar_list.p, T.bfarL_same ? nullptr : T.bfar_lap.p, mom.p, kappa, c.n, c.mv_active, T.leaf_sys.p,
+         T.bfar_list.p, T.bfarL_same ? nullptr : T.bfar_lap.p, bco->p, kappa, c.n, c.mv_active, T.leaf_sys.p,
          far_out);
   if (!F64) c.time_end(sf, tf);
   Ctx::Timed tm;
@@ -1021,6 +1022,12 @@ void run_tree(Ctx& c, DBuf<Real>& mom, cudaStream_t s) {
   } else {
     launch(pair_str_kernel, cdiv(T.npair, 256), 256, 0, s, T.pair_src.p, T.npair, c.str32.p, T.pairSA.p,
            T.pairSB.p);
+    static bool carve[64] = {};  // as for the far kernel: shared memory must not cap the resident blocks
+    if (c.device >= 0 && c.device < 64 && !carve[c.device]) {
+      BP_CUDA(cudaFuncSetAttribute(near16_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared));
+      carve[c.device] = true;
+    }
     launch(near16_kernel, dim3(nb16, S), 32, 0, s, b16, c.tgt64.p, T.leaf_cell.p, T.center.p,
            T.bnear_ptr.p, T.bnear_list.p, T.pair_ptr.p, T.pairPA.p, T.pairPB.p, T.pairSA.p, T.pairSB.p,
            (float)kappa, nk, c.n, c.mv_active, T.leaf_sys.p, c.part.p, c.dev_err.p);

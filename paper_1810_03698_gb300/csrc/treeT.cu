@@ -10,95 +10,128 @@ namespace {
 // ---------------------------------------------------------------- transposed product
 // A^T puts charges at the collocation points and evaluates at the Gauss nodes: per
 // panel j, sum_g W_g V(y_g) and sum_g W_g n_j . grad V(y_g) with V the potential of the
-// charges u (u1 for the Laplace kernel, u2 for Yukawa).  Far field: V(y) = sum_k a_k(D) M_k
-// with D = y - c_C and M_k the charge moments of cell C; since da_k/dD_j = -(k_j + 1) a_{k+e_j},
-// grad V = -sum_k (k_j + 1) a_{k+e_j} M_k e_j, so the coefficients run to order P + 1.
-template <int P, typename Real, int YUK>
-__device__ __forceinline__ void farT_eval(const Real D[3], const Real* __restrict__ M, Real kappa, Real& V,
-                                          Real G[3]) {
-  constexpr int Q = P + 1;
-  constexpr MI<Q> mi{};
-  constexpr int NCQ = MI<Q>::NC;
-  constexpr int NC = MI<P>::NC;
+// charges u (u1 for the Laplace kernel, u2 for Yukawa).  Far field: with D = y - c_C the
+// potential of a cell's charges is V = sum_m g_m(|D|) S_m(D), S_m = sum_e D^e B[m, e]
+// (the cell's far-field coefficients, as in the product), and since grad g_m = D g_{m+1},
+//     n . grad V = (n . D) sum_m g_{m+1} S_m + sum_m g_m (n . grad S_m).
+// The monomials D^e are carried together with their derivatives along n (first-order
+// dual numbers), so one pass over a cell's interleaved (Laplace, Yukawa) coefficients
+// gives all four rows; the radial sequences run to order P + 1.  lw = 1 adds the
+// Laplace terms (0: a cell of another body).
+template <int P, typename Real>
+__device__ __forceinline__ void farT_eval(const Real D[3], const Real nv[3], const Real* __restrict__ Bc, Real kappa,
+                                          Real kappa2, Real lw, Real& vl, Real& kl, Real& vy, Real& ky) {
+  constexpr BIdx<P> bi{};
+  Real SL[P + 1], TL[P + 1], SY[P + 1], TY[P + 1];  // S_m and n . grad S_m, both charge sets
+  Real py[P + 1], dy[P + 1], pz[P + 1], dz[P + 1];   // powers of D_y, D_z and their n-derivatives
+#pragma unroll
+  for (int m = 0; m <= P; ++m) SL[m] = TL[m] = SY[m] = TY[m] = (Real)0;
+  py[0] = pz[0] = (Real)1;
+  dy[0] = dz[0] = (Real)0;
+#pragma unroll
+  for (int e = 1; e <= P; ++e) {
+    dy[e] = dy[e - 1] * D[1] + py[e - 1] * nv[1];
+    py[e] = py[e - 1] * D[1];
+    dz[e] = dz[e - 1] * D[2] + pz[e - 1] * nv[2];
+    pz[e] = pz[e - 1] * D[2];
+  }
+  Real px = (Real)1, dx = (Real)0;
+#pragma unroll
+  for (int a = 0; a <= P; ++a) {
+#pragma unroll
+    for (int b = 0; b <= P; ++b) {  // fixed trip counts, so every index is a constant
+      if (a + b > P) continue;
+      const Real pab = px * py[b], dab = dx * py[b] + px * dy[b];
+#pragma unroll
+      for (int c = 0; c <= P; ++c) {
+        if (a + b + c > P) continue;
+        const Real w = pab * pz[c], dw = dab * pz[c] + pab * dz[c];
+        const int d = a + b + c, t0 = bi.t[a][b][c];
+#pragma unroll
+        for (int m = 0; m <= P; ++m) {
+          if (m < d || 2 * m - d > P) continue;
+          const int t = t0 + (m - d);
+          Real bl, by;
+          ld_entry<Real, (2 * nb_of(P) * sizeof(Real)) % 16 == 0>(Bc, t, bl, by);
+          SL[m] = fma(w, bl, SL[m]);
+          TL[m] = fma(dw, bl, TL[m]);
+          SY[m] = fma(w, by, SY[m]);
+          TY[m] = fma(dw, by, TY[m]);
+        }
+      }
+    }
+    dx = dx * D[0] + px * nv[0];
+    px *= D[0];
+  }
   const Real r2 = D[0] * D[0] + D[1] * D[1] + D[2] * D[2];
   const Real rinv = inv_sqrt(r2);
   const Real ir2 = rinv * rinv;
-  Real A[NCQ], Bc[YUK ? NCQ : 1];
-  Real q1[Q + 1], q2[Q + 1], q3[Q + 1], kn[Q + 1];
+  const Real nD = nv[0] * D[0] + nv[1] * D[1] + nv[2] * D[2];
+  // Laplace: g_0 = 1/r, g_{m+1} = -(2m + 1) g_m / r^2
+  Real g = rinv, V = 0, K1 = 0, K2 = 0;
 #pragma unroll
-  for (int nn = 1; nn <= Q; ++nn) {
-    q1[nn] = ir2 * (Real)((2.0 * nn - 1.0) / nn);
-    q2[nn] = ir2 * (Real)((nn - 1.0) / nn);
-    kn[nn] = kappa * (Real)(1.0 / nn);
-    q3[nn] = kn[nn] * ir2;
+  for (int m = 0; m <= P; ++m) {
+    const Real gn = g * (Real)(-(2.0 * m + 1.0)) * ir2;
+    V += g * SL[m];
+    K2 += g * TL[m];
+    K1 += gn * SL[m];
+    g = gn;
   }
-  if (YUK) {
-    const Real e = exp_neg(kappa * (r2 * rinv));
-    A[0] = e * rinv;
-    Bc[0] = e;
-  } else {
-    A[0] = rinv;
-  }
+  vl += lw * V;
+  kl += lw * (nD * K1 + K2);
+  // Yukawa: g_0 = e^{-kappa r}/r, g_1 = -(1 + kappa r) g_0 / r^2,
+  // g_{m+1} = (kappa^2 g_{m-1} - (2m + 1) g_m) / r^2
+  const Real kr = kappa * (r2 * rinv);
+  Real g0 = exp_neg(kr) * rinv;
+  Real g1 = -((Real)1 + kr) * g0 * ir2;
+  V = g0 * SY[0];
+  K2 = g0 * TY[0];
+  K1 = g1 * SY[0];
 #pragma unroll
-  for (int t = 1; t < NCQ; ++t) {
-    const int nn = mi.ord[t];
-    Real s1a = 0, s2a = 0, s1b = 0, s2b = 0;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      if (mi.m1[t][j] >= 0) {
-        s1a += D[j] * A[mi.m1[t][j]];
-        if (YUK) s1b += D[j] * Bc[mi.m1[t][j]];
-      }
-      if (mi.m2[t][j] >= 0) {
-        s2a += A[mi.m2[t][j]];
-        if (YUK) s2b += Bc[mi.m2[t][j]];
-      }
-    }
-    if (YUK) {
-      Bc[t] = kn[nn] * (s1a - s2a);
-      A[t] = q1[nn] * s1a - q2[nn] * s2a + q3[nn] * (s1b - s2b);
-    } else {
-      A[t] = q1[nn] * s1a - q2[nn] * s2a;
-    }
+  for (int m = 1; m <= P; ++m) {
+    const Real g2 = (kappa2 * g0 - (Real)(2.0 * m + 1.0) * g1) * ir2;
+    V += g1 * SY[m];
+    K2 += g1 * TY[m];
+    K1 += g2 * SY[m];
+    g0 = g1;
+    g1 = g2;
   }
-  Real v = 0, g0 = 0, g1 = 0, g2 = 0;
-#pragma unroll
-  for (int t = 0; t < NC; ++t) {
-    const Real m = M[t];
-    v += A[t] * m;
-    g0 -= (Real)(mi.k[t][0] + 1) * A[mi.p1[t][0]] * m;
-    g1 -= (Real)(mi.k[t][1] + 1) * A[mi.p1[t][1]] * m;
-    g2 -= (Real)(mi.k[t][2] + 1) * A[mi.p1[t][2]] * m;
-  }
-  V = v;
-  G[0] = g0;
-  G[1] = g1;
-  G[2] = g2;
+  vy += V;
+  ky += nD * K1 + K2;
 }
 
-// Four threads per panel (one per Gauss node, K <= 4) of a target block of <= 32
-// panels of one leaf; loops over the leaf's far cells (Laplace list for YUK = 0,
-// Yukawa list for 1) with the charge moments `mom` ([cell][2][NC], first NC used),
-// then adds the nodes of each panel with shuffles.  Writes rows (2 YUK, 2 YUK + 1) =
-// (sum_g W V, sum_g W n . grad V) of `out` ([4][n]).
-template <int P, typename Real, int YUK>
-__global__ void __launch_bounds__(128) farT_kernel(const int4* __restrict__ blk, const float4* __restrict__ node_rel,
-                                                  const double4* __restrict__ node64, const double4* __restrict__ nrm,
-                                                  int K, const int* __restrict__ leaf_cell,
-                                                  const double4* __restrict__ center, const int* __restrict__ far_ptr,
-                                                  const int* __restrict__ far_list, const Real* __restrict__ mom,
-                                                  Real kappa, int n, const int* __restrict__ active,
-                                                  const int* __restrict__ leaf_sys, double* __restrict__ out) {
-  constexpr int NC = MI<P>::NC;
-  __shared__ Real sm[FCH][NC];
-  __shared__ Real so[FCH][3];
-  const int4 B = blk[blockIdx.x];
+// Far field of the transposed product, one warp per 8 panels of one leaf (half of a
+// 16-panel block; blockIdx.x = 2 * block + half): lane 4p + g serves Gauss node g of
+// panel p.  Every lane takes every cell of the leaf's far list (the acceptance test of
+// the list holds for the leaf's nodes); the warp stages its own groups of cells'
+// coefficients with cp.async, double-buffered, with no block-wide barrier.  The four
+// nodes of a panel are summed with shuffles; rows (V_L, K_L, V_Y, K_Y) go to out
+// ([4][n]).  lap (NULL: every cell) marks the entries with Laplace terms.
+template <int P, typename Real>
+__global__ void __launch_bounds__(32) farT16_kernel(const int4* __restrict__ blk, const float4* __restrict__ node_rel,
+                                                    const double4* __restrict__ node64,
+                                                    const double4* __restrict__ nrm, int K,
+                                                    const int* __restrict__ leaf_cell,
+                                                    const double4* __restrict__ center,
+                                                    const int* __restrict__ far_ptr, const int* __restrict__ far_list,
+                                                    const int* __restrict__ lap, const Real* __restrict__ bco,
+                                                    Real kappa, int n, const int* __restrict__ active,
+                                                    const int* __restrict__ leaf_sys, double* __restrict__ out) {
+  constexpr int NB = FarShape<P, Real>::NB, FW = FarShape<P, Real>::FW;
+  constexpr bool ASYNC = (2 * NB * sizeof(Real)) % 16 == 0;
+  constexpr int CH = (int)(2 * NB * sizeof(Real) / 16);  // 16-byte pieces per cell
+  __shared__ __align__(16) Real sm[2][FW][2 * NB];
+  __shared__ Real so[2][FW][4];
+  const int lane = threadIdx.x;
+  const int4 B = blk[blockIdx.x >> 1];
   const int leaf = B.x;
   if (active && !active[leaf_sys[leaf]]) return;
+  const int first = B.y + 8 * (int)(blockIdx.x & 1), cnt = min(8, B.z - 8 * (int)(blockIdx.x & 1));
+  if (cnt <= 0) return;
   const double4 ct = center[leaf_cell[leaf]];
-  const int pl = threadIdx.x >> 2, g = threadIdx.x & 3;
-  const int i = B.y + pl;
-  const bool act = pl < B.z && g < K;
+  const int pl = lane >> 2, g = lane & 3;
+  const int i = first + pl;
+  const bool act = pl < cnt && g < K;
   Real yr[3] = {0, 0, 0}, w = 0, nv[3] = {0, 0, 0};
   if (act) {
     const size_t q = (size_t)K * i + g;
@@ -119,41 +152,59 @@ __global__ void __launch_bounds__(128) farT_kernel(const int4* __restrict__ blk,
     nv[1] = (Real)nn.y;
     nv[2] = (Real)nn.z;
   }
-  double aV = 0, aK = 0;
+  const Real kappa2 = kappa * kappa;
+  double aVL = 0, aKL = 0, aVY = 0, aKY = 0;
   const int f0 = far_ptr[leaf], f1 = far_ptr[leaf + 1];
-  for (int fb = f0; fb < f1; fb += FCH) {
-    const int cnt = min(FCH, f1 - fb);
-    for (int q = threadIdx.x; q < cnt * NC; q += 128)
-      sm[q / NC][q % NC] = mom[(size_t)far_list[fb + q / NC] * 2 * NC + q % NC];
-    if ((int)threadIdx.x < cnt) {
-      const double4 cc = center[far_list[fb + threadIdx.x]];
-      so[threadIdx.x][0] = (Real)(ct.x - cc.x);
-      so[threadIdx.x][1] = (Real)(ct.y - cc.y);
-      so[threadIdx.x][2] = (Real)(ct.z - cc.z);
-    }
-    __syncthreads();
-    Real v = 0, k = 0;
-    if ((int)(threadIdx.x >> 5) * 8 < B.z) {  // warp holds at least one panel
-      for (int q = 0; q < cnt; ++q) {
-        const Real D[3] = {yr[0] + so[q][0], yr[1] + so[q][1], yr[2] + so[q][2]};
-        Real V, G[3];
-        farT_eval<P, Real, YUK>(D, sm[q], kappa, V, G);
-        v += w * V;
-        k += w * (nv[0] * G[0] + nv[1] * G[1] + nv[2] * G[2]);
+  auto stage = [&](int b, int fb) {
+    const int c = min(FW, f1 - fb);
+    if constexpr (ASYNC) {
+      for (int q = lane; q < c * CH; q += 32) {
+        const int cell = q / CH, piece = q - cell * CH;
+        const char* gp = reinterpret_cast<const char*>(bco + (size_t)far_list[fb + cell] * 2 * NB) + 16 * piece;
+        cp_async16(reinterpret_cast<char*>(&sm[b][cell][0]) + 16 * piece, gp);
       }
+      cp_async_commit();
+    } else {
+      for (int q = lane; q < c * 2 * NB; q += 32)
+        sm[b][q / (2 * NB)][q % (2 * NB)] = bco[(size_t)far_list[fb + q / (2 * NB)] * 2 * NB + q % (2 * NB)];
     }
-    aV += (double)v;
-    aK += (double)k;
-    __syncthreads();
+    if (lane < c) {
+      const double4 cc = center[far_list[fb + lane]];
+      so[b][lane][0] = (Real)(ct.x - cc.x);
+      so[b][lane][1] = (Real)(ct.y - cc.y);
+      so[b][lane][2] = (Real)(ct.z - cc.z);
+      so[b][lane][3] = lap ? (Real)lap[fb + lane] : (Real)1;
+    }
+  };
+  if (f0 < f1) stage(0, f0);
+  int b = 0;
+  for (int fb = f0; fb < f1; fb += FW, b ^= 1) {
+    const int c = min(FW, f1 - fb);
+    if constexpr (ASYNC) cp_async_wait_all();  // this lane's pieces of group b
+    __syncwarp();  // every lane's pieces and offsets of group b; all done with the other buffer
+    if (fb + FW < f1) stage(b ^ 1, fb + FW);
+    Real vl = 0, kl = 0, vy = 0, ky = 0;
+    for (int q = 0; q < c; ++q) {
+      const Real D[3] = {yr[0] + so[b][q][0], yr[1] + so[b][q][1], yr[2] + so[b][q][2]};
+      farT_eval<P, Real>(D, nv, sm[b][q], kappa, kappa2, so[b][q][3], vl, kl, vy, ky);
+    }
+    aVL += (double)(w * vl);
+    aKL += (double)(w * kl);
+    aVY += (double)(w * vy);
+    aKY += (double)(w * ky);
   }
   // the nodes of a panel are four consecutive lanes
   for (int o = 1; o < 4; o <<= 1) {
-    aV += __shfl_xor_sync(0xffffffffu, aV, o);
-    aK += __shfl_xor_sync(0xffffffffu, aK, o);
+    aVL += __shfl_xor_sync(0xffffffffu, aVL, o);
+    aKL += __shfl_xor_sync(0xffffffffu, aKL, o);
+    aVY += __shfl_xor_sync(0xffffffffu, aVY, o);
+    aKY += __shfl_xor_sync(0xffffffffu, aKY, o);
   }
-  if (g == 0 && pl < B.z) {
-    out[(2 * YUK) * (size_t)n + i] = aV;
-    out[(2 * YUK + 1) * (size_t)n + i] = aK;
+  if (g == 0 && pl < cnt) {
+    out[i] = aVL;
+    out[(size_t)n + i] = aKL;
+    out[2 * (size_t)n + i] = aVY;
+    out[3 * (size_t)n + i] = aKY;
   }
 }
 
@@ -349,15 +400,29 @@ DBuf<double>& momT<double>(Tree& T, int w) {
   return T.momT64[w];
 }
 
+template <typename Real>
+DBuf<Real>& bcoT(Tree& T);
+template <>
+DBuf<float>& bcoT<float>(Tree& T) {
+  return T.bcoT32;
+}
+template <>
+DBuf<double>& bcoT<double>(Tree& T) {
+  return T.bcoT64;
+}
+
 template <int P, typename Real>
 void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   Tree& T = c.tree;
-  constexpr int NC = MI<P>::NC;
+  constexpr int NC = MI<P>::NC, NB = nb_of(P);
   typedef typename Vec4<Real>::T R4;
   DBuf<Real>& mL = momT<Real>(T, 0);
   DBuf<Real>& mY = momT<Real>(T, 1);
   if (mL.n < (size_t)T.ncell * 2 * NC) mL.alloc((size_t)T.ncell * 2 * NC);
   if (mY.n < (size_t)T.ncell * 2 * NC) mY.alloc((size_t)T.ncell * 2 * NC);
+  DBuf<Real>& bco = bcoT<Real>(T);
+  if (bco.n < (size_t)T.ncell * 2 * NB) bco.alloc((size_t)T.ncell * 2 * NB);
+  build_btab<P>(T.btabT, s);
   DBuf<R4>& sL = chgT<R4>(T, 0);
   DBuf<R4>& sY = chgT<R4>(T, 1);
   if (sL.n < (size_t)c.n) sL.alloc(c.n);
@@ -366,8 +431,9 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
   const size_t need = (size_t)(S + 1) * 4 * c.n;
   if (c.part.n < need) c.part.alloc(need);
   const Real kappa = (Real)c.par.kappa;
-  // Fork as in the forward product: charges, moments, M2M shifts and far kernels on the
-  // high-priority side stream, the near field (which reads u directly) on `s`.
+  // Fork as in the forward product: charges, moments, M2M shifts, coefficients and the
+  // far kernel on the high-priority side stream, the near field (which reads u
+  // directly) on `s`.
   c.ensure_aux();
   const cudaStream_t sf = c.aux;
   Ctx::Timed tp;
@@ -384,16 +450,18 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
       launch(m2m_kernel<P, Real>, cnt, M2M_TPB, 0, sf, first, T.child0.p, T.nchild.p, T.center.p, m.p);
     }
   }
+  {  // far-field coefficients (Laplace, Yukawa) of the cells that the leaves' far lists can hold
+    const int cb = T.h_depth_begin[T.m2m_min_depth];
+    if (cb < T.ncell)
+      launch(bcoef_kernel<P, Real>, cdiv((long long)(T.ncell - cb) * NB, 256), 256, 0, sf, cb, T.ncell,
+             T.btabT.ptr.p, T.btabT.k.p, T.btabT.c.p, mL.p, mY.p, bco.p);
+  }
   Ctx::Timed tf;
   c.time_begin(1, sf, tf);
   double* far_out = c.part.p + (size_t)S * 4 * c.n;
-  const int* lp = T.farL_same ? T.far_ptr.p : T.farL_ptr.p;
-  const int* ll = T.farL_same ? T.far_list.p : T.farL_list.p;
-  launch(farT_kernel<P, Real, 0>, T.nblk32, 128, 0, sf, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
-         T.leaf_cell.p, T.center.p, lp, ll, mL.p, kappa, c.n, c.mv_active, T.leaf_sys.p, far_out);
-  launch(farT_kernel<P, Real, 1>, T.nblk32, 128, 0, sf, T.blk32.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
-         T.leaf_cell.p, T.center.p, T.far_ptr.p, T.far_list.p, mY.p, kappa, c.n, c.mv_active, T.leaf_sys.p,
-         far_out);
+  launch(farT16_kernel<P, Real>, 2 * T.nblk16f, 32, 0, sf, T.blk16f.p, T.src_rel32.p, c.src64.p, c.nrm64.p, c.K,
+         T.leaf_cell.p, T.center.p, T.far_ptr.p, T.far_list.p, T.farL_same ? nullptr : T.far_lap.p, bco.p, kappa,
+         c.n, c.mv_active, T.leaf_sys.p, far_out);
   c.time_end(sf, tf);
   Ctx::Timed tm;
   c.time_begin(0, s, tm);

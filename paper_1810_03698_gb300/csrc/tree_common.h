@@ -327,7 +327,147 @@ __global__ void __launch_bounds__(M2M_TPB) m2m_kernel(int first_cell, const int*
   }
 }
 
-constexpr int FCH = 32;  // far cells staged in shared memory per pass (fewer barriers)
+// asynchronous global -> shared copies of 16 bytes (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------- far-field coefficients
+// Entries of one cell's far-field coefficients at order P: one per pair (m, e) of a
+// radial index m and a monomial exponent e with |e| <= m and 2m - |e| <= P.
+constexpr int nb_of(int P) {
+  int t = 0;
+  for (int d = 0; d <= P; ++d) t += (d + 1) * (d + 2) / 2 * ((P - d) / 2 + 1);
+  return t;
+}
+
+// Position of the first entry of monomial e = (a, b, c) in a cell's coefficient array
+// (monomials in the order a, then b, then c ascending; within one, m ascending).
+template <int P>
+struct BIdx {
+  static constexpr int NB = nb_of(P);
+  int t[P + 1][P + 1][P + 1];
+  constexpr BIdx() : t{} {
+    int q = 0;
+    for (int a = 0; a <= P; ++a)
+      for (int b = 0; b <= P; ++b)
+        for (int c = 0; c <= P; ++c) {
+          t[a][b][c] = -1;
+          if (a + b + c > P) continue;
+          t[a][b][c] = q;
+          const int d = a + b + c;
+          q += (P - d) / 2 + 1;  // m = d .. floor((P + d) / 2)
+        }
+  }
+};
+
+// Far-field coefficients of a cell from two of its moment sets X and Y (read at the moment
+// layout [cell][2][NC]: the product's single and double layers, or the transposed
+// product's Laplace and Yukawa charges): B[m, e](X) = sum over j with |j| = m - |e| and
+// |e + 2j| <= P of prod_i c(e_i + 2 j_i, j_i) X_{e + 2j}, stored as interleaved pairs
+// (B(X), B(Y)).  One thread per (cell, entry) of the cells [c0, ncell); the entry's terms
+// come from a table built on the host (ptr, moment index, coefficient).
+template <int P, typename Real>
+__global__ void bcoef_kernel(int c0, int ncell, const int* __restrict__ tptr, const int* __restrict__ tk,
+                             const double* __restrict__ tc, const Real* __restrict__ xa, const Real* __restrict__ xb,
+                             Real* __restrict__ bco) {
+  constexpr int NC = MI<P>::NC, NB = nb_of(P);
+  const long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= (long long)(ncell - c0) * NB) return;
+  const int cell = c0 + (int)(g / NB), q = (int)(g - (long long)(cell - c0) * NB);
+  const Real* __restrict__ X = xa + (size_t)cell * 2 * NC;
+  const Real* __restrict__ Y = xb + (size_t)cell * 2 * NC;
+  Real bm = 0, bd = 0;
+  for (int u = tptr[q]; u < tptr[q + 1]; ++u) {
+    const Real cf = (Real)tc[u];
+    bm += cf * X[tk[u]];
+    bd += cf * Y[tk[u]];
+  }
+  Real* o = bco + ((size_t)cell * NB + q) * 2;
+  o[0] = bm;
+  o[1] = bd;
+}
+
+// Entry t of a cell's staged coefficients, the pair (B(X), B(Y)).  When a cell's row is a
+// whole number of 16-byte pieces (VEC) the row is read 16 bytes at a time (FP32: entries
+// t and t + 1 together, so an unrolled pass issues one shared-memory load per two
+// entries); otherwise element by element.
+template <typename Real, bool VEC>
+__device__ __forceinline__ void ld_entry(const Real* __restrict__ Bc, int t, Real& bx, Real& by) {
+  if constexpr (VEC && sizeof(Real) == 4) {
+    const float4 q = reinterpret_cast<const float4*>(Bc)[t >> 1];
+    bx = (t & 1) ? q.z : q.x;
+    by = (t & 1) ? q.w : q.y;
+  } else if constexpr (VEC) {
+    const double2 q = reinterpret_cast<const double2*>(Bc)[t];
+    bx = q.x;
+    by = q.y;
+  } else {
+    bx = Bc[2 * t];
+    by = Bc[2 * t + 1];
+  }
+}
+
+// Staging of the far-field kernels: one cell's coefficients are 2 NB values; groups of
+// FW cells (even, 2..8) keep two staging buffers near 8 KB.
+template <int P, typename Real>
+struct FarShape {
+  static constexpr int NB = nb_of(P);
+  static constexpr int BYTES = 2 * NB * (int)sizeof(Real);  // one cell's coefficients
+  static constexpr int FW0 = 8192 / (2 * BYTES);
+  // cells per staged group: even, 2..8
+  static constexpr int FW = FW0 >= 8 ? 8 : (FW0 < 2 ? 2 : (FW0 & ~1));
+};
+
+template <typename V>
+void upload(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
+  d.alloc(std::max<size_t>(1, h.size()));
+  if (!h.empty()) BP_CUDA(cudaMemcpyAsync(d.p, h.data(), sizeof(V) * h.size(), cudaMemcpyHostToDevice, s));
+}
+
+// Terms of every far-field coefficient at order P (see bcoef_kernel), in the entry order
+// of BIdx: for entry (m, e), the moments X_{e + 2j} with |j| = m - |e| and |e + 2j| <= P,
+// each with the constant prod_i (-1)^{k_i} / (2^{j_i} j_i! (k_i - 2 j_i)!), k = e + 2j.
+template <int P>
+void build_btab(Tree::BTab& T, cudaStream_t s) {
+  if (T.order == P) return;
+  constexpr MI<P> mi{};
+  auto cu = [](int k, int j) {
+    double d = 1.0;
+    for (int q = 0; q < j; ++q) d *= 2.0 * (q + 1);  // 2^j j!
+    for (int q = 2; q <= k - 2 * j; ++q) d *= q;     // (k - 2j)!
+    return ((k & 1) ? -1.0 : 1.0) / d;
+  };
+  std::vector<int> ptr(1, 0), kk;
+  std::vector<double> cf;
+  for (int a = 0; a <= P; ++a)
+    for (int b = 0; b <= P; ++b)
+      for (int c = 0; c <= P; ++c) {
+        const int d = a + b + c;
+        if (d > P) continue;
+        for (int m = d; 2 * m - d <= P; ++m) {
+          const int J = m - d;
+          for (int j0 = 0; j0 <= J; ++j0)
+            for (int j1 = 0; j0 + j1 <= J; ++j1) {
+              const int j2 = J - j0 - j1;
+              const int k0 = a + 2 * j0, k1 = b + 2 * j1, k2 = c + 2 * j2;
+              if (k0 + k1 + k2 > P) continue;
+              kk.push_back(mi.idx[k0][k1][k2]);
+              cf.push_back(cu(k0, j0) * cu(k1, j1) * cu(k2, j2));
+            }
+          ptr.push_back((int)kk.size());
+        }
+      }
+  if ((int)ptr.size() != nb_of(P) + 1) fail(BEMPOL_ERR_ARG, "far-field coefficient table has the wrong size");
+  upload(T.ptr, ptr, s);
+  upload(T.k, kk, s);
+  upload(T.c, cf, s);
+  T.order = P;
+}
+
 constexpr int NTB = 32;  // targets (one warp) per near-field block
 
 }  // namespace
