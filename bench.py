@@ -66,7 +66,7 @@ FLOPS_PER_PAIR = 30
 # induced-dipole iterations and the final solve's inner GMRES, plus its FP64 residuals).
 # The CPU baseline prices one Delta G as this many FP64 matrix-vector products of the
 # oracle in both arms; the native arm also reports its own count beside it.
-PRODUCTS_PER_DG = 747
+PRODUCTS_PER_DG = 754
 # DRAM bytes (read + write) of one FP32 treecode product on this workload, summed over
 # its kernels from one ncu capture of the kernels as committed (set to None when they change).
 TRAFFIC_PER_PRODUCT_BYTES = 42.57e6
