@@ -1,7 +1,10 @@
 // Shared pieces of the treecode (tree.cu: the matrix-vector product; treeT.cu: its
-// transpose): launch constants, the multi-index tables of the Taylor expansions,
-// FP32 approximate rsqrt/exp2, the cell-geometry and leaf-relative position kernels,
-// and the moment kernels (leaf moments from sources, exact M2M shifts).
+// transpose; sitetree.cu: the fields at the sites): launch constants, the multi-index
+// tables of the Taylor expansions, FP32 approximate rsqrt/exp2, the cell-geometry and
+// leaf-relative position kernels, the moment kernels (leaf moments from sources, exact
+// M2M shifts), and the far-field coefficients of the cells (their index table, the
+// host-built table of their terms, the kernel that forms them from two moment sets, and
+// the staging shape and 16-byte reads of the far-field kernels).
 #pragma once
 
 #include <algorithm>
