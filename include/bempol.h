@@ -482,6 +482,20 @@ bempol_status bempol_measure_peaks(int device, int iters, int reps, bempol_peaks
  * BEMPOL_ERR_ARG (NULL) / BEMPOL_ERR_NOT_CONVERGED (the solve failed). */
 bempol_status bempol_near_rule19(double* nodes);
 
+/* The table from which the treecode forms each cell's far-field coefficients at Taylor
+ * order `order` (1..6; Sec. "The treecode algorithm", Cartesian Taylor expansion of the
+ * Laplace and Yukawa kernels about the cell centre).  With a cell's moments X_k in the
+ * order k = (a, b, n - a - b) for n = 0..P, a = n..0, b = n - a..0, its coefficient of
+ * entry q is  B_q = sum_{u = ptr[q]}^{ptr[q+1]-1} coef[u] * X_{moment[u]},  and the far
+ * potential of the cell at Delta = x - c is  sum_m g_m(|Delta|) sum_e Delta^e B_{(m, e)}
+ * with g_m = (1/r d/dr)^m G.  Entries run over the monomial exponents e = (a, b, c) in
+ * the order a, then b, then c ascending, |e| <= P, and within one e over m = |e| ..
+ * floor((P + |e|) / 2).  Call with NULL arrays to get *n_entries (NB) and *n_terms, then
+ * with caller-owned host arrays ptr [NB + 1], moment [n_terms] and coef [n_terms].  Host
+ * only: needs no device or context.  BEMPOL_ERR_ARG: order outside 1..6 or a NULL count. */
+bempol_status bempol_far_coefficients(int order, int64_t* n_entries, int64_t* n_terms, int32_t* ptr,
+                                      int32_t* moment, double* coef);
+
 /* Target sharding over several GPUs (Sec. "The treecode algorithm": the source-target
  * and box-target interactions of different targets are independent).  Each GPU holds
  * the whole mesh, sites and sources in its own context and computes only the rows of

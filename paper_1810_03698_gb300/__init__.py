@@ -130,6 +130,7 @@ def _load():
         "bempol_stats_read": (i32, [vp, C.POINTER(Stats), i32]),
         "bempol_measure_peaks": (i32, [i32, i32, i32, C.POINTER(Peaks)]),
         "bempol_near_rule19": (i32, [vp]),
+        "bempol_far_coefficients": (i32, [i32, vp, vp, vp, vp, vp]),
         "bempol_shard_rows": (i32, [i64, vp, i32, vp]),
         "bempol_set_shard": (i32, [vp, i32, i32, vp, ExchangeFn, vp]),
         "bempol_shard_bounds": (i32, [vp, vp]),
@@ -444,6 +445,24 @@ def near_rule19() -> np.ndarray:
     if st != 0:
         raise BempolError(st, "bempol_near_rule19 failed")
     return out
+
+
+def far_coefficients(order: int):
+    """The treecode's far-field coefficient table at `order` (bempol_far_coefficients, host
+    only): (ptr [NB + 1], moment [terms], coef [terms]), CSR over the NB entries."""
+    ne = C.c_int64(0)
+    nt = C.c_int64(0)
+    st = _lib.bempol_far_coefficients(int(order), C.addressof(ne), C.addressof(nt), None, None, None)
+    if st != 0:
+        raise BempolError(st, "bempol_far_coefficients failed")
+    ptr = np.zeros(ne.value + 1, dtype=np.int32)
+    mom = np.zeros(nt.value, dtype=np.int32)
+    coef = np.zeros(nt.value, dtype=np.float64)
+    st = _lib.bempol_far_coefficients(int(order), C.addressof(ne), C.addressof(nt), ptr.ctypes.data,
+                                      mom.ctypes.data, coef.ctypes.data)
+    if st != 0:
+        raise BempolError(st, "bempol_far_coefficients failed")
+    return ptr, mom, coef
 
 
 def shard_rows(n_units: int, world: int, cost=None):

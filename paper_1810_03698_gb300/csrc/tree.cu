@@ -1208,3 +1208,39 @@ void tree_matvec_sums(Ctx& c, bool fp32, cudaStream_t s) {
 }
 
 }  // namespace bp
+
+namespace {
+
+template <int P>
+bempol_status far_coefficients_copy(int64_t* n_entries, int64_t* n_terms, int32_t* ptr, int32_t* moment,
+                                    double* coef) {
+  std::vector<int> p, k;
+  std::vector<double> c;
+  bp::btab_terms<P>(p, k, c);
+  *n_entries = (int64_t)p.size() - 1;
+  *n_terms = (int64_t)k.size();
+  if (ptr) std::copy(p.begin(), p.end(), ptr);
+  if (moment) std::copy(k.begin(), k.end(), moment);
+  if (coef) std::copy(c.begin(), c.end(), coef);
+  return BEMPOL_OK;
+}
+
+}  // namespace
+
+extern "C" bempol_status bempol_far_coefficients(int order, int64_t* n_entries, int64_t* n_terms, int32_t* ptr,
+                                                 int32_t* moment, double* coef) {
+  if (!n_entries || !n_terms) return BEMPOL_ERR_ARG;
+  try {
+    switch (order) {
+      case 1: return far_coefficients_copy<1>(n_entries, n_terms, ptr, moment, coef);
+      case 2: return far_coefficients_copy<2>(n_entries, n_terms, ptr, moment, coef);
+      case 3: return far_coefficients_copy<3>(n_entries, n_terms, ptr, moment, coef);
+      case 4: return far_coefficients_copy<4>(n_entries, n_terms, ptr, moment, coef);
+      case 5: return far_coefficients_copy<5>(n_entries, n_terms, ptr, moment, coef);
+      case 6: return far_coefficients_copy<6>(n_entries, n_terms, ptr, moment, coef);
+      default: return BEMPOL_ERR_ARG;
+    }
+  } catch (...) {
+    return BEMPOL_ERR_ARG;
+  }
+}

@@ -434,9 +434,9 @@ void upload(DBuf<V>& d, const std::vector<V>& h, cudaStream_t s) {
 // Terms of every far-field coefficient at order P (see bcoef_kernel), in the entry order
 // of BIdx: for entry (m, e), the moments X_{e + 2j} with |j| = m - |e| and |e + 2j| <= P,
 // each with the constant prod_i (-1)^{k_i} / (2^{j_i} j_i! (k_i - 2 j_i)!), k = e + 2j.
+// CSR over the entries: ptr (NB + 1), moment index in the MI<P> order, constant.
 template <int P>
-void build_btab(Tree::BTab& T, cudaStream_t s) {
-  if (T.order == P) return;
+void btab_terms(std::vector<int>& ptr, std::vector<int>& kk, std::vector<double>& cf) {
   constexpr MI<P> mi{};
   auto cu = [](int k, int j) {
     double d = 1.0;
@@ -444,8 +444,9 @@ void build_btab(Tree::BTab& T, cudaStream_t s) {
     for (int q = 2; q <= k - 2 * j; ++q) d *= q;     // (k - 2j)!
     return ((k & 1) ? -1.0 : 1.0) / d;
   };
-  std::vector<int> ptr(1, 0), kk;
-  std::vector<double> cf;
+  ptr.assign(1, 0);
+  kk.clear();
+  cf.clear();
   for (int a = 0; a <= P; ++a)
     for (int b = 0; b <= P; ++b)
       for (int c = 0; c <= P; ++c) {
@@ -464,6 +465,15 @@ void build_btab(Tree::BTab& T, cudaStream_t s) {
           ptr.push_back((int)kk.size());
         }
       }
+}
+
+// The same table on the device, built once per order.
+template <int P>
+void build_btab(Tree::BTab& T, cudaStream_t s) {
+  if (T.order == P) return;
+  std::vector<int> ptr, kk;
+  std::vector<double> cf;
+  btab_terms<P>(ptr, kk, cf);
   if ((int)ptr.size() != nb_of(P) + 1) fail(BEMPOL_ERR_ARG, "far-field coefficient table has the wrong size");
   upload(T.ptr, ptr, s);
   upload(T.k, kk, s);
