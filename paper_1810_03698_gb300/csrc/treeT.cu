@@ -477,8 +477,9 @@ void runT_tree(Ctx& c, const double* u, cudaStream_t s) {
 
 // The transposed far field runs in FP32 at order 4 whatever the forward order: the
 // adjoint needs A^T only to about the accuracy of the forward treecode (theta^(P+1)
-// bounds both), the order-P transposed kernel carries coefficients to order P + 1 at
-// four Gauss nodes per panel, and one compiled order keeps the build short.
+// bounds both), the order-P transposed kernel evaluates four times as many targets (the
+// Gauss nodes) with derivatives along the normal, and one compiled order keeps the build
+// short.
 void dispatchT(Ctx& c, const double* u, cudaStream_t s) { runT_tree<4, float>(c, u, s); }
 
 }  // namespace
